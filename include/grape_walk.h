@@ -1,0 +1,363 @@
+/*
+ * grape_walk.h -- C ABI of libgrape_walk, a GB300 (sm_103a) engine for
+ * node2vec second-order biased random walks over sorted CSR graphs.
+ *
+ * The method is GRAPE's (Cappelletti et al., arXiv 2110.06196), Methods,
+ * "Implementation of second-order RWs":
+ *   a walk at v that arrived from t moves to x in N(v) with un-normalised
+ *   probability pi_vx = alpha_pq(t, x) * w_vx                  (eq. alphaRW)
+ *   alpha = 1/p if x == t, 1 if x in N(t), 1/q otherwise         (eqs. alpha, beta
+ *   and "Efficient computation of the in-out and return bias").
+ *   The first step has no t and is first-order, pi_vx = w_vx ("First and
+ *   second-order RW-based embedding methods").
+ *
+ * Sampling is exact rejection sampling, in place of the paper's per-step
+ * cumulative sum ("Efficient sampling for Node2Vec RWs"):
+ *   - trial k of step s of walk w draws one Philox4x32-10 block (r0, r1, r2, r3),
+ *     with key = seed and counter = (w lo, w hi, s, k);
+ *   - the proposal is x = row_v[floor((r1:r0) * deg_v / 2^64)];
+ *   - it is accepted iff r2 < T_class (unweighted) or
+ *     fl(r2 * wmax_v) < fl(T_class * w_vx) (weighted, IEEE double products).
+ *     Here T_class = floor(alpha_class / max(1/p, 1, 1/q) * 2^32) and wmax_v is
+ *     the largest weight in the row of v;
+ *   - after `trial_cap` rejections the step is drawn by inverse transform over
+ *     the cumulative sum of pi in row order, with the Philox block of trial
+ *     index trial_cap.
+ * A walk is therefore a pure function of (graph, start, walk id, seed, p, q):
+ * the same bytes come out of every entry point below, alone, batched or served.
+ *
+ * Conventions
+ *   - CSR: offsets int64[num_nodes + 1] with offsets[0] = 0 and
+ *     offsets[num_nodes] = num_entries; dsts int32[num_entries], each row
+ *     strictly increasing (sorted, no multi-edges), ids in [0, num_nodes);
+ *     weights fp32[num_entries], finite and > 0, or NULL for unweighted.
+ *     Self-loops are allowed.  N(t) is the out-row of t ("x in N(t)" is read as
+ *     the directed edge t -> x; for undirected graphs, store both directions).
+ *   - Output rows: int32, walk_len entries per walk.  Entry 0 is the start and
+ *     entry s is the node after s transitions.  Once a walk reaches a node
+ *     without out-edges, the rest of its row is -1.  Walk w = r * num_starts + i
+ *     is repetition r of starts[i], and its row is row w.
+ *   - Device pointers are CUDA device (or managed) addresses on the current
+ *     device.  Streams are cudaStream_t values (struct CUstream_st *); NULL is the
+ *     legacy default stream.  Every launch is asynchronous on the given stream.
+ *   - Errors in arguments are returned synchronously, before anything is
+ *     enqueued.  Errors found on the device (a start id out of range) set the
+ *     graph's device status word.  Their rows are filled with -1.
+ *     grape_stream_status reads the word and clears it.  Kernels never trap.
+ *   - Thread safety: a graph is immutable after creation, except through
+ *     grape_graph_set_tuning, and may be used from several host threads and
+ *     streams at once.  Server calls are thread-safe.
+ */
+#ifndef GRAPE_WALK_H
+#define GRAPE_WALK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* grape_stream_t;   /* identical to cudaStream_t */
+
+typedef enum grape_status {
+    GRAPE_OK = 0,
+    GRAPE_ERR_INVALID_ARG = 1,    /* bad argument; nothing was enqueued */
+    GRAPE_ERR_INVALID_GRAPH = 2,  /* CSR failed validation */
+    GRAPE_ERR_NOMEM = 3,          /* device or host allocation failed, or request above the server cap */
+    GRAPE_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    GRAPE_ERR_TIMEOUT = 5,        /* a bounded wait ran out */
+    GRAPE_ERR_BUSY = 6,           /* server queue full (try again) */
+    GRAPE_ERR_CANCELLED = 7,      /* request cancelled or server shut down */
+    GRAPE_ERR_DEVICE = 8,         /* the device status word was set (bad start id) */
+    GRAPE_ERR_NOT_FOUND = 9       /* unknown ticket */
+} grape_status_t;
+
+/* Message for a status code (static storage). */
+const char* grape_status_string(grape_status_t status);
+
+/* ------------------------------------------------------------------------ */
+/* Graphs                                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct grape_graph grape_graph_t;
+
+#define GRAPE_UNDIRECTED 1u  /* caller asserts every row pair is symmetric (with equal weights);
+                                membership may then search whichever of N(t), N(x) is shorter */
+#define GRAPE_VALIDATE   2u  /* check the CSR on the device before accepting it */
+
+/*
+ * Copy a CSR graph into library-owned device memory and build the per-node
+ * records the walks read (row offset, degree, largest row weight).  The layout
+ * follows GRAPE, Methods, "Graph data structures" (CSR with sorted adjacency).
+ *   offsets, dsts, weights: device pointers laid out as in Conventions.  The
+ *       caller keeps ownership; they may be freed once `stream` has reached
+ *       this call's work (the copies are enqueued on it).
+ *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62].
+ *   flags: GRAPE_UNDIRECTED | GRAPE_VALIDATE.  With GRAPE_VALIDATE the call
+ *       synchronises `stream` and returns GRAPE_ERR_INVALID_GRAPH for:
+ *       non-monotone offsets, wrong first or last offset, ids out of range,
+ *       rows not strictly increasing, weights not finite or <= 0, or (with
+ *       GRAPE_UNDIRECTED) a missing or unequal reverse entry.
+ *   *out receives the graph on GRAPE_OK, and NULL otherwise.
+ */
+grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
+                                  const float* weights, int64_t num_nodes,
+                                  int64_t num_entries, uint32_t flags,
+                                  grape_stream_t stream, grape_graph_t** out);
+
+/* Free the graph's device memory (synchronises the device first). NULL is a no-op. */
+void grape_graph_destroy(grape_graph_t* graph);
+
+typedef struct grape_graph_info {
+    int64_t num_nodes;
+    int64_t num_entries;
+    int32_t max_degree;
+    int32_t weighted;        /* 1 when weights were given */
+    int32_t undirected;      /* 1 when GRAPE_UNDIRECTED was given */
+    int32_t pad;
+    int64_t device_bytes;    /* device memory held by the graph */
+} grape_graph_info_t;
+
+grape_status_t grape_graph_info(const grape_graph_t* graph, grape_graph_info_t* info);
+
+/*
+ * Launch and search policy.  None of these change any output byte; they only
+ * change how the work is spread over the GPU.
+ */
+typedef struct grape_tuning {
+    int64_t trial_cap;        /* rejection trials before the exact fallback (default 4096; 0 = always fall back) */
+    int32_t warp_search_min;  /* membership lists at least this long are searched by the whole warp
+                                 (32-ary, one probe per lane); shorter ones by the lane alone */
+    int32_t block_threads;    /* threads per block for walk kernels (multiple of 32, <= 1024) */
+    int32_t blocks_per_sm;    /* resident blocks per SM for the grid size; 0 = occupancy maximum */
+    int32_t chunk_walks;      /* batched and served queues: walks per queue entry */
+    int32_t shorter_list;     /* undirected graphs: 1 = search whichever of N(t), N(x) is shorter */
+    int32_t pad;
+} grape_tuning_t;
+
+grape_status_t grape_graph_get_tuning(const grape_graph_t* graph, grape_tuning_t* tuning);
+grape_status_t grape_graph_set_tuning(grape_graph_t* graph, const grape_tuning_t* tuning);
+
+/* ------------------------------------------------------------------------ */
+/* Walks                                                                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * walks_per_node * num_starts walks of walk_len entries each, into
+ * out[walks_per_node * num_starts][walk_len] (device, caller-owned, int32).
+ * This is the per-call path (GRAPE, "Implementation of second-order RWs"),
+ * with the p == 1 / q == 1 / unweighted specialisations of that section
+ * picked automatically.
+ *   starts: device int32[num_starts], or NULL for 0, 1, ..., num_starts - 1
+ *           (then num_starts <= num_nodes).
+ *   walk_len >= 1; walks_per_node >= 1; p, q finite and > 0; seed any value.
+ *   Starts out of range produce -1 rows and set the device status word.
+ * Returns after enqueueing on `stream`.
+ */
+grape_status_t grape_walks(const grape_graph_t* graph, const int32_t* starts,
+                           int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                           double p, double q, uint64_t seed, int32_t* out,
+                           grape_stream_t stream);
+
+/*
+ * A contiguous shard of a grape_walks job: the walks with ids
+ * [walk_begin, walk_begin + walk_count) of the job (starts, num_starts,
+ * walks_per_node, ...), written to out[walk_count][walk_len] (row j = walk id
+ * walk_begin + j).  The rows are byte-identical to the same rows of the whole
+ * job, so a job split over several GPUs (one shard each, no communication)
+ * reassembles exactly.
+ */
+grape_status_t grape_walks_range(const grape_graph_t* graph, const int32_t* starts,
+                                 int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                                 double p, double q, uint64_t seed, int64_t walk_begin,
+                                 int64_t walk_count, int32_t* out, grape_stream_t stream);
+
+/*
+ * The same walks as grape_walks, with `starts` and `out` in HOST memory
+ * (pageable or pinned).  The call copies the starts in, runs the walks and
+ * copies the rows out, and returns once `out` holds them (it synchronises
+ * `stream`).  Device scratch for the starts and rows is taken from, and given
+ * back to, the device's default stream-ordered memory pool inside the call.
+ * Pinned host buffers let both copies run at full link speed.
+ */
+grape_status_t grape_walks_host(const grape_graph_t* graph, const int32_t* starts,
+                                int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                                double p, double q, uint64_t seed, int32_t* out,
+                                grape_stream_t stream);
+
+/* One walk request: rows as in grape_walks. */
+typedef struct grape_walk_request {
+    const int32_t* starts;    /* device int32[num_starts] for batched calls; HOST for the server */
+    int64_t num_starts;       /* >= 1 (NULL starts: 0..num_starts-1) */
+    int32_t walk_len;         /* >= 1 */
+    int32_t walks_per_node;   /* >= 1 */
+    double p, q;              /* finite, > 0 */
+    uint64_t seed;
+    int32_t* out;             /* device rows (batched); HOST rows or NULL (server) */
+} grape_walk_request_t;
+
+/*
+ * Batched walks: all requests in one persistent launch, replayed from a CUDA
+ * graph.  Each request's rows are byte-identical to a grape_walks call with
+ * the same arguments.  Workers take `chunk_walks` walks at a time from one
+ * queue that spans the requests, so requests of uneven size, length and
+ * (p, q) share the GPU without a launch per request.
+ * A plan uploads the request table once and can be launched many times; the
+ * request arrays must stay valid while the plan is in use.
+ */
+typedef struct grape_batch_plan grape_batch_plan_t;
+
+grape_status_t grape_batch_plan_create(const grape_graph_t* graph,
+                                       const grape_walk_request_t* requests,
+                                       int32_t num_requests, grape_stream_t stream,
+                                       grape_batch_plan_t** out);
+grape_status_t grape_batch_plan_launch(grape_batch_plan_t* plan, grape_stream_t stream);
+void grape_batch_plan_destroy(grape_batch_plan_t* plan);
+
+/* Plan, launch and free in one call (the plan is freed after the launch is enqueued). */
+grape_status_t grape_walks_batched(const grape_graph_t* graph,
+                                   const grape_walk_request_t* requests,
+                                   int32_t num_requests, grape_stream_t stream);
+
+/*
+ * Autotune the batched path for this graph: times a grid of (chunk_walks,
+ * warp_search_min) on the given requests with CUDA events, and stores the
+ * fastest pair in the graph's tuning (also returned in *best when not NULL).
+ * Writes into the requests' out buffers.  Synchronises `stream`.
+ */
+grape_status_t grape_autotune_batched(grape_graph_t* graph,
+                                      const grape_walk_request_t* requests,
+                                      int32_t num_requests, grape_stream_t stream,
+                                      grape_tuning_t* best);
+
+/*
+ * Synchronise `stream`, then read and clear the graph's device status word:
+ * GRAPE_OK, or GRAPE_ERR_DEVICE when a kernel saw a start id out of range.
+ */
+grape_status_t grape_stream_status(const grape_graph_t* graph, grape_stream_t stream);
+
+/*
+ * Work counters, summed over every walk kernel that ran on this graph while
+ * counting was on (off by default; enabling costs one atomic per warp per
+ * kernel).  Used for the bytes-per-step roofline accounting.
+ */
+typedef struct grape_walk_counters {
+    int64_t steps;        /* transitions taken */
+    int64_t trials;       /* proposals drawn */
+    int64_t searches;     /* membership tests whose outcome decided acceptance */
+    int64_t warp_searches;/* of which warp-cooperative */
+    int64_t fallbacks;    /* steps drawn by the exact inverse-transform fallback */
+    int64_t walks;        /* rows written */
+} grape_walk_counters_t;
+
+grape_status_t grape_counters_enable(grape_graph_t* graph, int32_t enable);
+/* Synchronises the device, copies the counters out and resets them. */
+grape_status_t grape_counters_read(grape_graph_t* graph, grape_walk_counters_t* out);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching with the graph resident on the device         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct grape_server grape_server_t;
+
+typedef struct grape_server_config {
+    int64_t output_cap_bytes;   /* device bytes for admitted requests' rows and starts (e.g. 40 GB) */
+    int32_t max_inflight;       /* requests admitted at once (ring slots), <= 65536 */
+    int32_t chunk_walks;        /* walks per work-queue entry (0 = graph tuning) */
+    int64_t max_chunks;         /* capacity of the device work queue, in entries */
+    int64_t idle_exit_us;       /* the resident kernel exits after this long without work */
+    int32_t admit_timeout_ms;   /* submit waits this long for memory/slots, then GRAPE_ERR_BUSY */
+    int32_t pad;
+} grape_server_config_t;
+
+typedef struct grape_server_stats {
+    int64_t submitted, admitted, completed, cancelled, rejected;
+    int64_t inflight;            /* admitted, not yet complete */
+    int64_t bytes_reserved;      /* output arena bytes in use */
+    int64_t kernel_launches;     /* resident-kernel launches so far */
+    int64_t steps;               /* transitions of completed requests (from row contents) */
+} grape_server_stats_t;
+
+/*
+ * Create a server on `graph` (which must outlive it).  The server owns a
+ * device arena of output_cap_bytes, a device request ring and work queue, a
+ * compute and a copy stream, and two host threads (scheduler, completion).
+ * Requests are admitted while arena bytes and ring slots allow; each is cut
+ * into queue entries of chunk_walks walks, appended to the queue that a
+ * resident kernel is draining.  Work that arrives while other requests run is
+ * picked up by the running kernel.  Finished rows are copied to the host on the
+ * copy stream while the kernel keeps running.  The resident kernel's waits are
+ * bounded (idle_exit_us); it is relaunched when new work arrives.
+ */
+grape_status_t grape_walk_server_create(const grape_graph_t* graph,
+                                        const grape_server_config_t* config,
+                                        grape_server_t** out);
+
+/*
+ * Submit a request.  req->starts is HOST memory (copied before return, so it
+ * may be reused at once).  req->out is the HOST destination of the rows
+ * (walks_per_node * num_starts * walk_len int32).  It must stay valid until
+ * grape_walk_server_wait returns for this ticket.  It may be NULL, and then
+ * the rows are handed over by wait's host_out.
+ * Returns GRAPE_ERR_NOMEM for a request larger than the whole cap, and
+ * GRAPE_ERR_BUSY when admission did not succeed within admit_timeout_ms.
+ */
+grape_status_t grape_walk_server_submit(grape_server_t* server,
+                                        const grape_walk_request_t* req,
+                                        uint64_t* ticket);
+
+/*
+ * Wait up to timeout_ms (< 0: no limit) for a ticket.  On GRAPE_OK the rows
+ * are in the host buffer given at submit, or in host_out when that was NULL.
+ * Once wait has returned GRAPE_OK, GRAPE_ERR_CANCELLED or a device error,
+ * the ticket is retired.  GRAPE_ERR_TIMEOUT leaves it pending.
+ */
+grape_status_t grape_walk_server_wait(grape_server_t* server, uint64_t ticket,
+                                      int64_t timeout_ms, int32_t* host_out);
+
+/*
+ * Wait up to timeout_ms (< 0: no limit) for ANY submitted ticket to finish,
+ * retire it and return it in *ticket.  *latency_ns (if not NULL) gets the time
+ * from submit to the rows being in host memory.  host_out is used as in
+ * grape_walk_server_wait.  Returns the ticket's status, or GRAPE_ERR_TIMEOUT.
+ */
+grape_status_t grape_walk_server_wait_any(grape_server_t* server, int64_t timeout_ms,
+                                          uint64_t* ticket, int64_t* latency_ns,
+                                          int32_t* host_out);
+
+/* Cancel a pending ticket (its rows are not delivered; wait returns GRAPE_ERR_CANCELLED). */
+grape_status_t grape_walk_server_cancel(grape_server_t* server, uint64_t ticket);
+
+grape_status_t grape_walk_server_stats(grape_server_t* server, grape_server_stats_t* stats);
+
+/* Stop admitting, let admitted work finish (bounded), cancel the rest, free everything. */
+void grape_walk_server_destroy(grape_server_t* server);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The device Philox4x32-10 generator the walks use (Salmon et al., SC 2011),
+ * evaluated on n counter/key pairs: ctr_key is device uint32[n][6]
+ * (c0 c1 c2 c3 k0 k1), out is device uint32[n][4].  Enqueued on `stream`.
+ */
+grape_status_t grape_philox4x32_10(const uint32_t* ctr_key, int64_t n, uint32_t* out,
+                                   grape_stream_t stream);
+
+/*
+ * Random 32-byte-sector gather probe (HBM random-access calibration): each of
+ * `n_reads` reads fetches one aligned 32-byte sector of `buf` (device,
+ * `buf_bytes` long, 32-byte aligned) at a position drawn by Philox from `seed`.
+ * The XOR of what was read lands in *sink (device uint32) so nothing is
+ * optimised away.
+ */
+grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_reads,
+                                  uint64_t seed, uint32_t* sink, grape_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPE_WALK_H */

@@ -1,0 +1,323 @@
+// graph.cu -- graph residency and preparation: CSR checks, node records, status
+// word, tuning and counters.
+//
+// The graph is stored as GRAPE stores it (Methods, "Graph data structures":
+// CSR with each adjacency list sorted), re-laid out for the walk kernels:
+//   rec[v]   16-byte record {row offset (int64), degree (int32), max row weight (fp32)}
+//            so that one aligned 16-byte load gives everything a step needs about v;
+//   dsts[e]  int32 sorted rows, read by the membership searches;
+//   pairs[e] int2 {dst, weight bits} (weighted graphs), so a weighted proposal
+//            reads its candidate and its weight from one 32-byte sector.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using grape::NodeRec;
+
+namespace {
+
+enum : int {
+    BAD_OFFSETS = 1,
+    BAD_IDS = 2,
+    BAD_ORDER = 4,
+    BAD_WEIGHTS = 8,
+    BAD_SYMMETRY = 16,
+};
+
+__global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, long long n,
+                                     long long m, int* bad) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v <= n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long a = offsets[v];
+        bool ok = (a >= 0 && a <= m);
+        if (v == 0) ok = ok && (a == 0);
+        if (v == n) ok = ok && (a == m);
+        if (v < n) {
+            const long long b = offsets[v + 1];
+            ok = ok && (b >= a) && (b <= m);
+        }
+        if (!ok) atomicOr(bad, BAD_OFFSETS);
+    }
+}
+
+// One warp per row: ids in range (always, so no later kernel can read out of
+// bounds), strict order and weights (when validating), the node record and
+// the weighted pair array.
+__global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
+                                  const int32_t* __restrict__ dsts,
+                                  const float* __restrict__ weights, long long n, int validate,
+                                  int4* __restrict__ rec, int2* __restrict__ pairs, int* bad,
+                                  int* max_deg) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
+         v += warps) {
+        const long long a = offsets[v], b = offsets[v + 1];
+        float wmax = 0.0f;
+        int flags = 0;
+        for (long long e = a + lane; e < b; e += 32) {
+            const int x = dsts[e];
+            if (x < 0 || x >= n) flags |= BAD_IDS;
+            if (validate && e > a && dsts[e - 1] >= x) flags |= BAD_ORDER;
+            if (weights) {
+                const float w = weights[e];
+                if (validate && !(isfinite(w) && w > 0.0f)) flags |= BAD_WEIGHTS;
+                wmax = fmaxf(wmax, w);
+                pairs[e] = make_int2(x, __float_as_int(w));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wmax = fmaxf(wmax, __shfl_xor_sync(grape::FULL, wmax, o));
+            flags |= __shfl_xor_sync(grape::FULL, flags, o);
+        }
+        if (lane == 0) {
+            const unsigned long long off = (unsigned long long)a;
+            const int deg = (int)(b - a);
+            rec[v] = make_int4((int)(unsigned)off, (int)(unsigned)(off >> 32), deg,
+                               __float_as_int(wmax));
+            if (flags) atomicOr(bad, flags);
+            atomicMax(max_deg, deg);
+        }
+    }
+}
+
+// Undirected graphs: every entry v -> x has a reverse entry x -> v with the same weight.
+__global__ void check_symmetry_kernel(const int4* __restrict__ rec, const int32_t* __restrict__ dsts,
+                                      const int2* __restrict__ pairs, long long n, int* bad) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
+         v += warps) {
+        const int4 rv = rec[v];
+        const long long a = (long long)(((unsigned long long)(unsigned)rv.y << 32) | (unsigned)rv.x);
+        const long long b = a + rv.z;
+        int flags = 0;
+        for (long long e = a + lane; e < b; e += 32) {
+            const int x = dsts[e];
+            const int4 rx = rec[x];
+            const long long xa = (long long)(((unsigned long long)(unsigned)rx.y << 32) | (unsigned)rx.x);
+            // lower bound of v in row x
+            long long lo = xa, hi = xa + rx.z;
+            while (lo < hi) {
+                const long long mid = lo + (hi - lo) / 2;
+                if (dsts[mid] < v) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= xa + rx.z || dsts[lo] != v) {
+                flags |= BAD_SYMMETRY;
+            } else if (pairs && pairs[lo].y != pairs[e].y) {
+                flags |= BAD_SYMMETRY;
+            }
+        }
+        flags = __reduce_or_sync(grape::FULL, flags);
+        if (lane == 0 && flags) atomicOr(bad, flags);
+    }
+}
+
+void free_graph(grape_graph* g) {
+    if (!g) return;
+    cudaFree(g->rec);
+    cudaFree(g->dsts);
+    cudaFree(g->pairs);
+    cudaFree(g->status);
+    cudaFree(g->counters);
+    delete g;
+}
+
+int grid_for(int num_sms, long long items, int per_block) {
+    long long b = (items + per_block - 1) / per_block;
+    long long cap = (long long)num_sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grape_status_string(grape_status_t s) {
+    switch (s) {
+        case GRAPE_OK: return "ok";
+        case GRAPE_ERR_INVALID_ARG: return "invalid argument";
+        case GRAPE_ERR_INVALID_GRAPH: return "invalid graph";
+        case GRAPE_ERR_NOMEM: return "out of memory";
+        case GRAPE_ERR_CUDA: return "CUDA runtime error";
+        case GRAPE_ERR_TIMEOUT: return "timed out";
+        case GRAPE_ERR_BUSY: return "busy";
+        case GRAPE_ERR_CANCELLED: return "cancelled";
+        case GRAPE_ERR_DEVICE: return "device reported an error (start id out of range)";
+        case GRAPE_ERR_NOT_FOUND: return "unknown ticket";
+    }
+    return "unknown status";
+}
+
+grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
+                                  const float* weights, int64_t num_nodes,
+                                  int64_t num_entries, uint32_t flags,
+                                  grape_stream_t stream_, grape_graph_t** out) {
+    if (!out) return GRAPE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!offsets || num_nodes < 1 || num_nodes > 0x7fffffffLL || num_entries < 0 ||
+        num_entries > (1LL << 62) || (num_entries > 0 && !dsts) ||
+        (flags & ~(GRAPE_UNDIRECTED | GRAPE_VALIDATE)))
+        return GRAPE_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+
+    grape_graph* g = new (std::nothrow) grape_graph();
+    if (!g) return GRAPE_ERR_NOMEM;
+    g->n = num_nodes;
+    g->m = num_entries;
+    g->weighted = (weights != nullptr);
+    g->undirected = (flags & GRAPE_UNDIRECTED) != 0;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    const size_t m_alloc = (size_t)(num_entries > 0 ? num_entries : 1);
+    if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
+    if (e == cudaSuccess && g->weighted) e = cudaMalloc(&g->pairs, sizeof(int2) * m_alloc);
+    if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * 6);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return grape::cuda_status(e);
+    }
+    g->device_bytes = (int64_t)(sizeof(int4) * num_nodes + sizeof(int32_t) * m_alloc +
+                                (g->weighted ? sizeof(int2) * m_alloc : 0));
+    int* scratch = g->status;   // [0] status word, [1] bad flags, [2] max degree
+    int host[4] = {0, 0, 0, 0};
+    e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * 6, stream);
+
+    // 1. Offsets first: nothing reads a row before its bounds are known good.
+    if (e == cudaSuccess) {
+        check_offsets_kernel<<<grid_for(g->num_sms, num_nodes + 1, 256), 256, 0, stream>>>(
+            offsets, num_nodes, num_entries, scratch + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess || host[1] != 0) {
+        free_graph(g);
+        return e != cudaSuccess ? grape::cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
+    }
+    // 2. Rows: copy, ids, order, weights, records.
+    if (num_entries > 0)
+        e = cudaMemcpyAsync(g->dsts, dsts, sizeof(int32_t) * (size_t)num_entries,
+                            cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) {
+        build_rows_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+            offsets, dsts, weights, num_nodes, (flags & GRAPE_VALIDATE) ? 1 : 0, g->rec,
+            g->pairs, scratch + 1, scratch + 2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess || host[1] != 0) {
+        free_graph(g);
+        return e != cudaSuccess ? grape::cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
+    }
+    // 3. Symmetry (ids are known in range now).
+    if ((flags & GRAPE_VALIDATE) && g->undirected) {
+        check_symmetry_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+            g->rec, g->dsts, g->pairs, num_nodes, scratch + 1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess || host[1] != 0) {
+            free_graph(g);
+            return e != cudaSuccess ? grape::cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
+        }
+    }
+    g->max_degree = host[2];
+    e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        free_graph(g);
+        return grape::cuda_status(e);
+    }
+
+    g->tuning.trial_cap = 4096;
+    g->tuning.warp_search_min = 512;
+    g->tuning.block_threads = 256;
+    g->tuning.blocks_per_sm = 0;
+    g->tuning.chunk_walks = 64;
+    g->tuning.shorter_list = 1;
+    *out = g;
+    return GRAPE_OK;
+}
+
+void grape_graph_destroy(grape_graph_t* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    free_graph(g);
+}
+
+grape_status_t grape_graph_info(const grape_graph_t* g, grape_graph_info_t* info) {
+    if (!g || !info) return GRAPE_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->num_nodes = g->n;
+    info->num_entries = g->m;
+    info->max_degree = g->max_degree;
+    info->weighted = g->weighted ? 1 : 0;
+    info->undirected = g->undirected ? 1 : 0;
+    info->device_bytes = g->device_bytes;
+    return GRAPE_OK;
+}
+
+grape_status_t grape_graph_get_tuning(const grape_graph_t* g, grape_tuning_t* t) {
+    if (!g || !t) return GRAPE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(const_cast<grape_graph*>(g)->mu);
+    *t = g->tuning;
+    return GRAPE_OK;
+}
+
+grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t) {
+    if (!g || !t) return GRAPE_ERR_INVALID_ARG;
+    if (t->trial_cap < 0 || t->trial_cap > 0xffffffffLL || t->warp_search_min < 1 ||
+        t->block_threads < 32 || t->block_threads > 1024 || (t->block_threads % 32) ||
+        t->blocks_per_sm < 0 || t->chunk_walks < 1)
+        return GRAPE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tuning = *t;
+    return GRAPE_OK;
+}
+
+grape_status_t grape_stream_status(const grape_graph_t* g, grape_stream_t stream_) {
+    if (!g) return GRAPE_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    int word = 0;
+    GRAPE_CUDA_TRY(cudaStreamSynchronize(stream));
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(&word, g->status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    GRAPE_CUDA_TRY(cudaMemsetAsync(g->status, 0, sizeof(int), stream));
+    GRAPE_CUDA_TRY(cudaStreamSynchronize(stream));
+    return word ? GRAPE_ERR_DEVICE : GRAPE_OK;
+}
+
+grape_status_t grape_counters_enable(grape_graph_t* g, int32_t enable) {
+    if (!g) return GRAPE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->counting = enable != 0;
+    return GRAPE_OK;
+}
+
+grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out) {
+    if (!g || !out) return GRAPE_ERR_INVALID_ARG;
+    unsigned long long c[6];
+    GRAPE_CUDA_TRY(cudaDeviceSynchronize());
+    GRAPE_CUDA_TRY(cudaMemcpy(c, g->counters, sizeof(c), cudaMemcpyDeviceToHost));
+    GRAPE_CUDA_TRY(cudaMemset(g->counters, 0, sizeof(c)));
+    GRAPE_CUDA_TRY(cudaDeviceSynchronize());
+    out->steps = (int64_t)c[0];
+    out->trials = (int64_t)c[1];
+    out->searches = (int64_t)c[2];
+    out->warp_searches = (int64_t)c[3];
+    out->fallbacks = (int64_t)c[4];
+    out->walks = (int64_t)c[5];
+    return GRAPE_OK;
+}
+
+}  // extern "C"

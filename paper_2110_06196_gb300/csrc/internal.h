@@ -1,0 +1,81 @@
+// internal.h -- host-side definitions shared by the library's translation units.
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "../../include/grape_walk.h"
+#include "walk_device.cuh"
+
+struct grape_graph {
+    int64_t n = 0;
+    int64_t m = 0;
+    int32_t max_degree = 0;
+    bool weighted = false;
+    bool undirected = false;
+    int device = 0;
+    int num_sms = 0;
+    int4* rec = nullptr;          // NodeRec[n]
+    int32_t* dsts = nullptr;      // [m]
+    int2* pairs = nullptr;        // [m] weighted only
+    int* status = nullptr;        // device status word
+    unsigned long long* counters = nullptr;  // [6]
+    bool counting = false;
+    int64_t device_bytes = 0;
+    grape_tuning_t tuning{};
+    std::mutex mu;                // guards tuning / counting updates
+
+    grape::GraphDev dev() const {
+        grape::GraphDev g;
+        g.rec = rec;
+        g.dsts = dsts;
+        g.pairs = pairs;
+        g.n = n;
+        g.status = status;
+        g.counters = counting ? counters : nullptr;
+        g.undirected = undirected ? 1 : 0;
+        return g;
+    }
+};
+
+namespace grape {
+
+// Fill the per-request constants from (p, q, seed, ...): the three class
+// thresholds T = floor(alpha / max(1/p, 1, 1/q) * 2^32), stored as T - 1.
+grape_status_t make_walk_const(const grape_graph* g, const int32_t* starts, int64_t num_starts,
+                               int32_t walk_len, int32_t walks_per_node, double p, double q,
+                               uint64_t seed, int32_t* out, WalkConst* wc);
+
+// Restrict wc to the walk ids [walk_begin, walk_begin + walk_count).
+grape_status_t restrict_walks(WalkConst* wc, int64_t walk_begin, int64_t walk_count);
+
+// Launch configuration of the walk kernels for this graph's tuning.
+struct LaunchShape {
+    int threads;
+    int blocks;
+};
+
+LaunchShape queue_launch_shape(const grape_graph* g, const grape_tuning_t& t, int weighted);
+
+// Launch the queue (batched / served) kernel.
+cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
+                                const WalkConst* reqs, const Chunk* chunks,
+                                unsigned long long* head, const unsigned long long* tail,
+                                unsigned long long ring, long long idle_spins, int* exit_flag,
+                                int blocks, cudaStream_t stream);
+
+inline grape_status_t cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GRAPE_OK;
+    if (e == cudaErrorMemoryAllocation) return GRAPE_ERR_NOMEM;
+    return GRAPE_ERR_CUDA;
+}
+
+}  // namespace grape
+
+#define GRAPE_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return grape::cuda_status(_e);  \
+    } while (0)

@@ -1,0 +1,593 @@
+// server.cu -- continuous-batching walk server.
+//
+// The graph stays resident.  Requests are admitted while output-arena bytes,
+// request slots and queue entries allow (FIFO, no overtaking).  An admitted
+// request is cut into queue entries of `chunk_walks` walks, and those are
+// appended to a device ring that a resident queue kernel is draining.  The
+// kernel's workers take entries with a compare-and-swap that never passes the
+// published tail, so work that is admitted while the kernel runs joins it at
+// once.  Each finished walk bumps its request's counter.  The last one raises a
+// completion flag in mapped host memory.  The driver thread then copies the
+// rows to the caller's host buffer on a separate copy stream while the kernel
+// keeps working, and frees the arena bytes.
+//
+// Waits are bounded on both sides.  An idle kernel polls the tail for at most
+// `idle_exit_us` and then exits.  The driver relaunches it when work is queued
+// and no kernel is running.  Shutdown raises an exit flag that the kernel reads
+// before taking each entry.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+using namespace grape;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch())
+        .count();
+}
+
+// First-fit allocator over [0, cap) with coalescing; 256-byte granules.
+class Arena {
+  public:
+    explicit Arena(int64_t cap) : cap_(cap) { free_[0] = cap; }
+    static int64_t round(int64_t b) { return (b + 255) & ~int64_t(255); }
+    bool alloc(int64_t bytes, int64_t* off) {
+        bytes = round(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const int64_t rest = it->second - bytes;
+                const int64_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest > 0) free_[start] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(int64_t off, int64_t bytes) {
+        bytes = round(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    int64_t used() const { return used_; }
+
+  private:
+    int64_t cap_;
+    int64_t used_ = 0;
+    std::map<int64_t, int64_t> free_;
+};
+
+enum class St { Pending, Admitted, Copying, Done, Cancelled, Failed };
+
+struct Req {
+    uint64_t ticket = 0;
+    grape_walk_request_t r{};
+    std::vector<int32_t> starts;   // host copy (empty when r.starts == NULL)
+    int32_t* host_out = nullptr;
+    int64_t num_walks = 0;
+    int64_t out_bytes = 0;
+    int64_t starts_bytes = 0;
+    int64_t alloc_bytes = 0;
+    int64_t arena_off = -1;
+    int slot = -1;
+    uint64_t first_chunk = 0;
+    uint64_t num_chunks = 0;
+    St st = St::Pending;
+    bool cancel = false;
+    bool retired = false;
+    bool inflight = false;          // counted in stats.inflight (admitted, not complete)
+    grape_status_t result = GRAPE_OK;
+    cudaEvent_t copied = nullptr;
+    int64_t t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct grape_server {
+    const grape_graph* g = nullptr;
+    grape_server_config_t cfg{};
+    grape_tuning_t tuning{};
+    int chunk_walks = 64;
+
+    // device state
+    char* arena_base = nullptr;
+    WalkConst* d_reqs = nullptr;
+    unsigned long long* d_done = nullptr;
+    Chunk* d_chunks = nullptr;
+    unsigned long long* d_ctl = nullptr;   // [0] head, [1] tail
+    int* d_exit = nullptr;
+    unsigned* h_flags = nullptr;           // mapped host memory
+    unsigned* d_flags = nullptr;           // its device address
+    cudaStream_t compute = nullptr, copy = nullptr, ctl = nullptr;
+    cudaEvent_t kernel_done = nullptr;
+    bool kernel_launched = false;
+
+    // host state
+    std::unique_ptr<Arena> arena;
+    std::mutex mu;
+    std::condition_variable cv;       // signalled on every state change
+    std::deque<std::shared_ptr<Req>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Req>> live;   // not yet retired
+    std::vector<std::shared_ptr<Req>> by_slot;
+    std::vector<int> free_slots;
+    std::deque<uint64_t> finished;    // completed, not retired (for wait_any)
+    uint64_t next_ticket = 1;
+    uint64_t tail = 0;                // queue entries published
+    bool stop = false;
+    bool accepting = true;
+    grape_server_stats_t stats{};
+    std::thread driver;
+
+    void run();
+    bool admit_locked(const std::shared_ptr<Req>& q);
+    grape_status_t publish(const std::vector<std::shared_ptr<Req>>& reqs);
+    uint64_t oldest_live_chunk_locked() const;
+    void finish_locked(const std::shared_ptr<Req>& q, St st, grape_status_t res);
+};
+
+uint64_t grape_server::oldest_live_chunk_locked() const {
+    uint64_t oldest = tail;
+    for (const auto& q : by_slot)
+        if (q && q->first_chunk < oldest) oldest = q->first_chunk;
+    return oldest;
+}
+
+bool grape_server::admit_locked(const std::shared_ptr<Req>& q) {
+    if (free_slots.empty()) return false;
+    const uint64_t nch = (uint64_t)((q->num_walks + chunk_walks - 1) / chunk_walks);
+    const uint64_t used = tail - oldest_live_chunk_locked();
+    if (used + nch > (uint64_t)cfg.max_chunks) return false;
+    int64_t off = 0;
+    if (!arena->alloc(q->alloc_bytes, &off)) return false;
+    q->arena_off = off;
+    q->slot = free_slots.back();
+    free_slots.pop_back();
+    q->first_chunk = tail;
+    q->num_chunks = nch;
+    tail += nch;
+    by_slot[q->slot] = q;
+    q->st = St::Admitted;
+    q->t_admit = now_ns();
+    q->inflight = true;
+    stats.admitted++;
+    stats.inflight++;
+    stats.bytes_reserved = arena->used();
+    return true;
+}
+
+grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& reqs) {
+    // Descriptors, starts and queue entries first, the new tail last, all on one
+    // stream, so a worker that sees the tail also sees what it covers.
+    std::vector<Chunk> chunks;
+    cudaError_t e = cudaSuccess;
+    uint64_t new_tail = 0;
+    for (const auto& q : reqs) {
+        char* base = arena_base + q->arena_off;
+        int32_t* d_starts = nullptr;
+        if (!q->starts.empty()) {
+            d_starts = reinterpret_cast<int32_t*>(base + Arena::round(q->out_bytes));
+            e = cudaMemcpyAsync(d_starts, q->starts.data(), (size_t)q->starts_bytes,
+                                cudaMemcpyHostToDevice, ctl);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        WalkConst wc;
+        grape_status_t st = make_walk_const(g, d_starts, q->r.num_starts, q->r.walk_len,
+                                            q->r.walks_per_node, q->r.p, q->r.q, q->r.seed,
+                                            reinterpret_cast<int32_t*>(base), &wc);
+        if (st != GRAPE_OK) return st;
+        wc.done = d_done + q->slot;
+        wc.done_flag = d_flags + q->slot;
+        h_flags[q->slot] = 0u;
+        e = cudaMemcpyAsync(d_reqs + q->slot, &wc, sizeof(wc), cudaMemcpyHostToDevice, ctl);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_done + q->slot, 0, sizeof(unsigned long long), ctl);
+        if (e != cudaSuccess) return cuda_status(e);
+        // the WalkConst lives on this stack frame: wait for it before reuse
+        e = cudaStreamSynchronize(ctl);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (uint64_t c = 0; c < q->num_chunks; ++c) {
+            Chunk ch;
+            ch.walk_lo = (long long)(c * (uint64_t)chunk_walks);
+            ch.count = (int)std::min<int64_t>(chunk_walks, q->num_walks - ch.walk_lo);
+            ch.req = q->slot;
+            chunks.push_back(ch);
+        }
+        new_tail = q->first_chunk + q->num_chunks;
+    }
+    if (reqs.empty()) return GRAPE_OK;
+    // Copy entries into the ring (possibly wrapping).
+    const uint64_t ring = (uint64_t)cfg.max_chunks;
+    uint64_t pos = reqs.front()->first_chunk;
+    size_t i = 0;
+    while (i < chunks.size()) {
+        const uint64_t slot = pos % ring;
+        const size_t n = (size_t)std::min<uint64_t>(chunks.size() - i, ring - slot);
+        e = cudaMemcpyAsync(d_chunks + slot, chunks.data() + i, sizeof(Chunk) * n,
+                            cudaMemcpyHostToDevice, ctl);
+        if (e != cudaSuccess) return cuda_status(e);
+        i += n;
+        pos += n;
+    }
+    static thread_local unsigned long long tail_host;
+    tail_host = new_tail;
+    e = cudaMemcpyAsync(d_ctl + 1, &tail_host, sizeof(tail_host), cudaMemcpyHostToDevice, ctl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
+    return cuda_status(e);
+}
+
+void grape_server::finish_locked(const std::shared_ptr<Req>& q, St st, grape_status_t res) {
+    if (q->arena_off >= 0) {
+        arena->release(q->arena_off, q->alloc_bytes);
+        q->arena_off = -1;
+    }
+    if (q->slot >= 0) {
+        by_slot[q->slot].reset();
+        free_slots.push_back(q->slot);
+        q->slot = -1;
+    }
+    if (q->inflight) {
+        q->inflight = false;
+        stats.inflight--;
+    }
+    if (q->copied) {
+        cudaEventDestroy(q->copied);
+        q->copied = nullptr;
+    }
+    q->st = st;
+    q->result = res;
+    q->t_done = now_ns();
+    if (st == St::Done) stats.completed++;
+    if (st == St::Cancelled) stats.cancelled++;
+    if (st == St::Failed) stats.rejected++;
+    stats.bytes_reserved = arena->used();
+    finished.push_back(q->ticket);
+    cv.notify_all();
+}
+
+void grape_server::run() {
+    const long long idle_spins = std::max<long long>(1, cfg.idle_exit_us);
+    while (true) {
+        bool busy = false;
+        std::vector<std::shared_ptr<Req>> admitted;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) break;
+            while (!pending.empty()) {
+                auto q = pending.front();
+                if (q->cancel) {
+                    pending.pop_front();
+                    finish_locked(q, St::Cancelled, GRAPE_ERR_CANCELLED);
+                    continue;
+                }
+                if (!accepting) {
+                    pending.pop_front();
+                    finish_locked(q, St::Cancelled, GRAPE_ERR_CANCELLED);
+                    continue;
+                }
+                if (admit_locked(q)) {
+                    pending.pop_front();
+                    admitted.push_back(q);
+                    continue;
+                }
+                if (cfg.admit_timeout_ms > 0 &&
+                    now_ns() - q->t_submit > (int64_t)cfg.admit_timeout_ms * 1000000) {
+                    pending.pop_front();
+                    finish_locked(q, St::Failed, GRAPE_ERR_BUSY);
+                    continue;
+                }
+                break;
+            }
+        }
+        if (!admitted.empty()) {
+            busy = true;
+            grape_status_t st = publish(admitted);
+            if (st != GRAPE_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                for (auto& q : admitted) finish_locked(q, St::Failed, st);
+            }
+        }
+        // Keep a resident kernel running while admitted work remains.
+        bool inflight;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            inflight = stats.inflight > 0;
+        }
+        if (inflight) {
+            const bool running = kernel_launched && cudaEventQuery(kernel_done) == cudaErrorNotReady;
+            if (!running) {
+                cudaError_t e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl, d_ctl + 1,
+                                                    (unsigned long long)cfg.max_chunks, idle_spins,
+                                                    d_exit, 0, compute);
+                if (e == cudaSuccess) e = cudaEventRecord(kernel_done, compute);
+                std::lock_guard<std::mutex> lk(mu);
+                if (e == cudaSuccess) {
+                    kernel_launched = true;
+                    stats.kernel_launches++;
+                } else {
+                    for (auto& q : by_slot)
+                        if (q) finish_locked(q, St::Failed, GRAPE_ERR_CUDA);
+                }
+            }
+        }
+        // Completions: flag -> copy out -> done.
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto& q : by_slot) {
+                if (!q) continue;
+                if (q->st == St::Admitted && ((volatile unsigned*)h_flags)[q->slot] != 0u) {
+                    busy = true;
+                    if (q->cancel) {
+                        finish_locked(q, St::Cancelled, GRAPE_ERR_CANCELLED);
+                        continue;
+                    }
+                    if (q->host_out) {
+                        cudaError_t e = cudaEventCreateWithFlags(&q->copied, cudaEventDisableTiming);
+                        if (e == cudaSuccess)
+                            e = cudaMemcpyAsync(q->host_out, arena_base + q->arena_off,
+                                                (size_t)q->out_bytes, cudaMemcpyDeviceToHost, copy);
+                        if (e == cudaSuccess) e = cudaEventRecord(q->copied, copy);
+                        if (e != cudaSuccess) {
+                            finish_locked(q, St::Failed, cuda_status(e));
+                            continue;
+                        }
+                        q->st = St::Copying;
+                    } else {
+                        // rows stay in the arena until wait() hands them over
+                        q->st = St::Done;
+                        q->t_done = now_ns();
+                        q->inflight = false;
+                        stats.inflight--;
+                        stats.completed++;
+                        finished.push_back(q->ticket);
+                        cv.notify_all();
+                    }
+                } else if (q->st == St::Copying) {
+                    const cudaError_t e = cudaEventQuery(q->copied);
+                    if (e == cudaSuccess) {
+                        busy = true;
+                        finish_locked(q, q->cancel ? St::Cancelled : St::Done,
+                                      q->cancel ? GRAPE_ERR_CANCELLED : GRAPE_OK);
+                    } else if (e != cudaErrorNotReady) {
+                        finish_locked(q, St::Failed, cuda_status(e));
+                    }
+                }
+            }
+        }
+        if (!busy) {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stats.inflight > 0)
+                cv.wait_for(lk, std::chrono::microseconds(20));
+            else if (!stop)
+                cv.wait_for(lk, std::chrono::milliseconds(2),
+                            [&] { return stop || !pending.empty(); });
+        }
+    }
+}
+
+extern "C" {
+
+grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_server_config_t* cfg,
+                                        grape_server_t** out) {
+    if (!out) return GRAPE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!g || !cfg || cfg->output_cap_bytes < 4096 || cfg->max_inflight < 1 ||
+        cfg->max_inflight > 65536 || cfg->chunk_walks < 0 || cfg->max_chunks < 1 ||
+        cfg->idle_exit_us < 1 || cfg->admit_timeout_ms < 0)
+        return GRAPE_ERR_INVALID_ARG;
+    grape_server* s = new (std::nothrow) grape_server();
+    if (!s) return GRAPE_ERR_NOMEM;
+    s->g = g;
+    s->cfg = *cfg;
+    grape_graph_get_tuning(g, &s->tuning);
+    s->chunk_walks = cfg->chunk_walks > 0 ? cfg->chunk_walks : s->tuning.chunk_walks;
+    s->arena.reset(new Arena(cfg->output_cap_bytes));
+    const int slots = cfg->max_inflight;
+    s->by_slot.resize((size_t)slots);
+    for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    cudaError_t e = cudaMalloc(&s->arena_base, (size_t)cfg->output_cap_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_reqs, sizeof(WalkConst) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_done, sizeof(unsigned long long) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_chunks, sizeof(Chunk) * (size_t)cfg->max_chunks);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ctl, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_exit, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&s->h_flags, sizeof(unsigned) * (size_t)slots, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->d_flags, s->h_flags, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemset(s->d_ctl, 0, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMemset(s->d_exit, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        grape_walk_server_destroy(s);
+        return cuda_status(e);
+    }
+    std::memset(s->h_flags, 0, sizeof(unsigned) * (size_t)slots);
+    s->driver = std::thread([s] { s->run(); });
+    *out = s;
+    return GRAPE_OK;
+}
+
+grape_status_t grape_walk_server_submit(grape_server_t* s, const grape_walk_request_t* r,
+                                        uint64_t* ticket) {
+    if (!s || !r || !ticket) return GRAPE_ERR_INVALID_ARG;
+    WalkConst probe;
+    grape_status_t st = make_walk_const(s->g, r->starts, r->num_starts, r->walk_len,
+                                        r->walks_per_node, r->p, r->q, r->seed,
+                                        reinterpret_cast<int32_t*>(alignof(int4)), &probe);
+    if (st != GRAPE_OK) return st;
+    auto q = std::make_shared<Req>();
+    q->r = *r;
+    q->host_out = r->out;
+    q->num_walks = probe.num_walks;
+    q->out_bytes = (int64_t)sizeof(int32_t) * probe.num_walks * r->walk_len;
+    q->starts_bytes = r->starts ? (int64_t)sizeof(int32_t) * r->num_starts : 0;
+    q->alloc_bytes = Arena::round(q->out_bytes) + Arena::round(q->starts_bytes);
+    if (q->alloc_bytes > s->cfg.output_cap_bytes) return GRAPE_ERR_NOMEM;
+    if (r->starts) q->starts.assign(r->starts, r->starts + r->num_starts);
+    q->r.starts = nullptr;
+    q->t_submit = now_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->accepting) return GRAPE_ERR_CANCELLED;
+    if ((int64_t)s->pending.size() >= 4LL * s->cfg.max_inflight + 1024) return GRAPE_ERR_BUSY;
+    q->ticket = s->next_ticket++;
+    s->pending.push_back(q);
+    s->live[q->ticket] = q;
+    s->stats.submitted++;
+    *ticket = q->ticket;
+    s->cv.notify_all();
+    return GRAPE_OK;
+}
+
+static bool terminal(St st) {
+    return st == St::Done || st == St::Cancelled || st == St::Failed;
+}
+
+static grape_status_t retire_locked(grape_server* s, const std::shared_ptr<Req>& q,
+                                    int32_t* host_out, std::unique_lock<std::mutex>& lk) {
+    grape_status_t res = q->result;
+    if (q->st == St::Done && q->arena_off >= 0) {
+        // rows held in the arena: hand them over now
+        if (!host_out) {
+            res = GRAPE_ERR_INVALID_ARG;
+        } else {
+            const void* src = s->arena_base + q->arena_off;
+            lk.unlock();
+            cudaError_t e = cudaMemcpy(host_out, src, (size_t)q->out_bytes, cudaMemcpyDeviceToHost);
+            lk.lock();
+            res = cuda_status(e);
+        }
+        if (q->arena_off >= 0) {
+            s->arena->release(q->arena_off, q->alloc_bytes);
+            q->arena_off = -1;
+        }
+        if (q->slot >= 0) {
+            s->by_slot[q->slot].reset();
+            s->free_slots.push_back(q->slot);
+            q->slot = -1;
+        }
+        s->stats.bytes_reserved = s->arena->used();
+        s->cv.notify_all();
+    }
+    q->retired = true;
+    s->live.erase(q->ticket);
+    return res;
+}
+
+grape_status_t grape_walk_server_wait(grape_server_t* s, uint64_t ticket, int64_t timeout_ms,
+                                      int32_t* host_out) {
+    if (!s) return GRAPE_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->live.find(ticket);
+    if (it == s->live.end()) return GRAPE_ERR_NOT_FOUND;
+    auto q = it->second;
+    auto ready = [&] { return terminal(q->st); };
+    if (timeout_ms < 0) s->cv.wait(lk, ready);
+    else if (!s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return GRAPE_ERR_TIMEOUT;
+    return retire_locked(s, q, host_out, lk);
+}
+
+grape_status_t grape_walk_server_wait_any(grape_server_t* s, int64_t timeout_ms,
+                                          uint64_t* ticket, int64_t* latency_ns,
+                                          int32_t* host_out) {
+    if (!s || !ticket) return GRAPE_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] {
+        while (!s->finished.empty() && !s->live.count(s->finished.front())) s->finished.pop_front();
+        return !s->finished.empty();
+    };
+    if (timeout_ms < 0) s->cv.wait(lk, ready);
+    else if (!s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return GRAPE_ERR_TIMEOUT;
+    const uint64_t t = s->finished.front();
+    s->finished.pop_front();
+    auto q = s->live[t];
+    *ticket = t;
+    if (latency_ns) *latency_ns = q->t_done - q->t_submit;
+    return retire_locked(s, q, host_out, lk);
+}
+
+grape_status_t grape_walk_server_cancel(grape_server_t* s, uint64_t ticket) {
+    if (!s) return GRAPE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->live.find(ticket);
+    if (it == s->live.end()) return GRAPE_ERR_NOT_FOUND;
+    it->second->cancel = true;
+    s->cv.notify_all();
+    return GRAPE_OK;
+}
+
+grape_status_t grape_walk_server_stats(grape_server_t* s, grape_server_stats_t* out) {
+    if (!s || !out) return GRAPE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    return GRAPE_OK;
+}
+
+void grape_walk_server_destroy(grape_server_t* s) {
+    if (!s) return;
+    if (s->driver.joinable()) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->accepting = false;
+            for (auto& q : s->pending) q->cancel = true;
+            s->cv.notify_all();
+            // admitted work gets a bounded time to finish
+            s->cv.wait_for(lk, std::chrono::seconds(60), [&] { return s->stats.inflight == 0; });
+            s->stop = true;
+            s->cv.notify_all();
+        }
+        int one = 1;
+        cudaMemcpyAsync(s->d_exit, &one, sizeof(int), cudaMemcpyHostToDevice, s->ctl);
+        cudaStreamSynchronize(s->ctl);
+        s->driver.join();
+    }
+    if (s->compute) cudaStreamSynchronize(s->compute);
+    if (s->copy) cudaStreamSynchronize(s->copy);
+    for (auto& kv : s->live)
+        if (kv.second->copied) cudaEventDestroy(kv.second->copied);
+    if (s->kernel_done) cudaEventDestroy(s->kernel_done);
+    if (s->compute) cudaStreamDestroy(s->compute);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->ctl) cudaStreamDestroy(s->ctl);
+    if (s->h_flags) cudaFreeHost(s->h_flags);
+    cudaFree(s->arena_base);
+    cudaFree(s->d_reqs);
+    cudaFree(s->d_done);
+    cudaFree(s->d_chunks);
+    cudaFree(s->d_ctl);
+    cudaFree(s->d_exit);
+    delete s;
+}
+
+}  // extern "C"

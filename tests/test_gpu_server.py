@@ -1,0 +1,154 @@
+"""Continuous-batching server: every request's rows equal the same request run
+alone through grape_walks (and the oracle on samples), whatever else is in
+flight; admission by output bytes queues requests that do not fit yet; the
+resident kernel's bounded idle wait runs out and it is relaunched; cancel,
+timeouts, oversize requests and shutdown with work in flight."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_06196_gb300 import GrapeError, Graph, Server, synth, walks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def graph():
+    csr = synth.rmat(14, 120000, seed=41, weighted=False)
+    return csr, Graph.from_csr(csr)
+
+
+def _alone(g, starts, L, p, q, seed, wpn=1):
+    return walks(g, torch.from_numpy(starts).cuda(), L, wpn, p, q, seed).cpu().numpy()
+
+
+def test_mixed_stream_equals_alone_and_oracle(graph):
+    csr, g = graph
+    mix = synth.request_mix(csr.num_nodes, 120, gen_seed=3, max_starts=20000, len_lo=5,
+                            len_hi=90)
+    srv = Server(g, output_cap_bytes=256 << 20, max_inflight=64, chunk_walks=32,
+                 idle_exit_us=500)
+    arrivals = synth.poisson_arrivals(2000.0, len(mix), seed=9)
+    tickets = {}
+    t0 = time.perf_counter()
+    for j, r in enumerate(mix):
+        while time.perf_counter() - t0 < arrivals[j]:
+            time.sleep(0.0002)
+        tickets[srv.submit(r.starts, r.walk_len, r.p, r.q, r.seed)] = j
+    got = {}
+    lat = []
+    while len(got) < len(mix):
+        t, l, rows = srv.wait_any(timeout_ms=60000)
+        got[tickets[t]] = rows
+        lat.append(l)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(mix) and st["inflight"] == 0
+    og = oracle.Graph(*csr.numpy())
+    for j, r in enumerate(mix):
+        assert np.array_equal(got[j], _alone(g, r.starts, r.walk_len, r.p, r.q, r.seed)), j
+        if j % 10 == 0:
+            ids = np.arange(min(3, len(r.starts)))
+            want = oracle.walk_rows(og, r.starts, r.walk_len, 1, r.p, r.q, r.seed, ids)
+            assert np.array_equal(got[j][ids], want)
+    assert all(x > 0 for x in lat)
+
+
+def test_admission_by_output_bytes(graph):
+    csr, g = graph
+    L = 50
+    per = 20000 * L * 4                       # 4 MB of rows per request
+    srv = Server(g, output_cap_bytes=3 * per, max_inflight=16, chunk_walks=64)
+    rng = np.random.default_rng(1)
+    reqs = [rng.integers(0, csr.num_nodes, 20000).astype(np.int32) for _ in range(12)]
+    ts = [srv.submit(s, L, 0.5, 2.0, 100 + j) for j, s in enumerate(reqs)]
+    peak = 0
+    for _ in range(2000):
+        st = srv.stats()
+        peak = max(peak, st["bytes_reserved"])
+        if st["completed"] == len(reqs):
+            break
+        time.sleep(0.001)
+    outs = [srv.wait(t, timeout_ms=60000) for t in ts]
+    srv.close()
+    assert peak <= 3 * per + 3 * 256 * 4
+    for j, (s, o) in enumerate(zip(reqs, outs)):
+        assert np.array_equal(o, _alone(g, s, L, 0.5, 2.0, 100 + j))
+
+
+def test_oversize_request_is_rejected(graph):
+    csr, g = graph
+    srv = Server(g, output_cap_bytes=1 << 20, max_inflight=4)
+    with pytest.raises(GrapeError) as ei:
+        srv.submit(np.zeros(100000, np.int32), 10, 1.0, 1.0, 0)
+    assert ei.value.name == "GRAPE_ERR_NOMEM"
+    srv.close()
+
+
+def test_idle_exit_and_relaunch(graph):
+    csr, g = graph
+    srv = Server(g, output_cap_bytes=64 << 20, max_inflight=8, idle_exit_us=200)
+    s = np.arange(500, dtype=np.int32)
+    a = srv.wait(srv.submit(s, 20, 2.0, 0.5, 1), timeout_ms=30000)
+    time.sleep(0.05)                     # the resident kernel's idle wait runs out
+    b = srv.wait(srv.submit(s, 20, 2.0, 0.5, 2), timeout_ms=30000)
+    st = srv.stats()
+    srv.close()
+    assert st["kernel_launches"] >= 2
+    assert np.array_equal(a, _alone(g, s, 20, 2.0, 0.5, 1))
+    assert np.array_equal(b, _alone(g, s, 20, 2.0, 0.5, 2))
+
+
+def test_cancel_timeout_and_shutdown(graph):
+    csr, g = graph
+    srv = Server(g, output_cap_bytes=8 << 20, max_inflight=2, chunk_walks=16)
+    big = np.random.default_rng(2).integers(0, csr.num_nodes, 30000).astype(np.int32)
+    t1 = srv.submit(big, 60, 0.25, 4.0, 5)
+    t2 = srv.submit(big, 60, 0.25, 4.0, 6)      # waits for memory behind t1
+    t3 = srv.submit(big[:10], 5, 1.0, 1.0, 7)
+    srv.cancel(t2)
+    with pytest.raises(GrapeError) as ei:
+        srv.wait(t2, timeout_ms=60000)
+    assert ei.value.name == "GRAPE_ERR_CANCELLED"
+    with pytest.raises(GrapeError) as ei:
+        srv.wait(999999, timeout_ms=0)
+    assert ei.value.name == "GRAPE_ERR_NOT_FOUND"
+    r1 = srv.wait(t1, timeout_ms=60000)
+    assert np.array_equal(r1, _alone(g, big, 60, 0.25, 4.0, 5))
+    r3 = srv.wait(t3, timeout_ms=60000)
+    assert np.array_equal(r3, _alone(g, big[:10], 5, 1.0, 1.0, 7))
+    # shutdown with work still queued and running
+    for j in range(6):
+        srv.submit(big, 60, 0.5, 2.0, 50 + j)
+    srv.close()
+
+
+def test_concurrent_submitters(graph):
+    csr, g = graph
+    srv = Server(g, output_cap_bytes=128 << 20, max_inflight=32, chunk_walks=32)
+    results = {}
+    errors = []
+
+    def client(k):
+        try:
+            rng = np.random.default_rng(k)
+            for j in range(6):
+                s = rng.integers(0, csr.num_nodes, int(rng.integers(1, 4000))).astype(np.int32)
+                t = srv.submit(s, 25, 1.0, 0.5, 1000 * k + j)
+                results[(k, j)] = (s, srv.wait(t, timeout_ms=60000))
+        except Exception as e:  # pragma: no cover
+            errors.append(e)
+
+    th = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    srv.close()
+    assert not errors
+    for (k, j), (s, rows) in results.items():
+        assert np.array_equal(rows, _alone(g, s, 25, 1.0, 0.5, 1000 * k + j))

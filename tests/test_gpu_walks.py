@@ -1,0 +1,281 @@
+"""GPU parity of the per-call path (grape_walks through the C ABI) against the
+CPU oracle: bit-exact int32 rows.
+
+Coverage: the eight p == 1 / q == 1 / weighted specialisations over a (p, q)
+grid; lane-only, mixed and warp-only membership search; the exact fallback
+(trial caps 0 and 2); tiny and structured graphs (house with a self-loop,
+directed with a dead end, star, path, K_n); ragged walk counts and lengths,
+unaligned output, explicit start lists, out-of-range starts, shards of a job,
+host-buffer calls; the 1,000-node ER workload in full; and the R-MAT scale-20
+weighted and scale-24 hub-heavy workloads at full size, checked on sampled walk
+ids and on every walk that starts at a top hub.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import _law
+from paper_2110_06196_gb300 import Graph, GrapeError, synth, walks, walks_host
+from paper_2110_06196_gb300 import walk as W
+
+pytestmark = pytest.mark.gpu
+
+PQ5 = (0.25, 0.5, 1.0, 2.0, 4.0)
+
+
+def csr_from_np(off, dst, w=None, n=None):
+    return synth.CSRGraph(torch.from_numpy(off), torch.from_numpy(dst),
+                          None if w is None else torch.from_numpy(w), len(off) - 1)
+
+
+def small_graphs():
+    out = {}
+    n, e = _law.graph_house()
+    out["house"] = (csr_from_np(*_law.csr_from_edges(n, e, None, True)), True)
+    wts = [0.1 + 0.9 * ((7 * k + 3) % 11) / 10 for k in range(len(e))]
+    out["house_w"] = (csr_from_np(*_law.csr_from_edges(n, e, wts, True)), True)
+    n, e = _law.graph_directed()
+    out["directed"] = (csr_from_np(*_law.csr_from_edges(n, e, None, False)), False)
+    wd = [0.2 + 0.15 * (k % 6) for k in range(len(e))]
+    out["directed_w"] = (csr_from_np(*_law.csr_from_edges(n, e, wd, False)), False)
+    out["star"] = (csr_from_np(*_law.csr_from_edges(9, [(0, i) for i in range(1, 9)])), True)
+    out["path"] = (csr_from_np(*_law.csr_from_edges(12, [(i, i + 1) for i in range(11)])), True)
+    kn = [(i, j) for i in range(8) for j in range(i + 1, 8)]
+    out["k8"] = (csr_from_np(*_law.csr_from_edges(8, kn)), True)
+    return out
+
+
+_RMAT12 = {}
+
+
+def rmat12(weighted):
+    if weighted not in _RMAT12:
+        _RMAT12[weighted] = synth.rmat(12, 40000, seed=21, weighted=weighted)
+    return _RMAT12[weighted]
+
+
+def check_parity(csr, starts, walk_len, wpn, p, q, seed, undirected=True, tuning=None,
+                 graph=None, out=None):
+    g = graph or Graph.from_csr(csr, undirected=undirected)
+    if tuning:
+        g.set_tuning(**tuning)
+    got = walks(g, starts, walk_len, wpn, p, q, seed, out=out)
+    torch.cuda.synchronize()
+    g.stream_status()
+    got = got.cpu().numpy()
+    og = oracle.Graph(*csr.numpy())
+    cap = g.get_tuning().trial_cap
+    want, rc = oracle.walks(og, None if starts is None else np.asarray(starts), walk_len, wpn,
+                            p, q, seed, trial_cap=cap)
+    assert rc == 0
+    if not np.array_equal(got, want):
+        bad = np.argwhere((got != want).any(axis=1))[:, 0]
+        raise AssertionError(f"{len(bad)} rows differ, first {bad[:5].tolist()}:\n"
+                             f"gpu    {got[bad[0]].tolist()}\noracle {want[bad[0]].tolist()}")
+    return got
+
+
+def test_device_philox_matches_published_vectors_and_oracle():
+    import os
+    kat = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [[int(x, 16) for x in l.split()] for l in open(kat)
+            if l.strip() and not l.startswith("#")]
+    rng = np.random.default_rng(5)
+    rnd = rng.integers(0, 2**32, size=(4096, 6), dtype=np.uint64)
+    ck = np.concatenate([np.array([r[:6] for r in rows], np.uint64), rnd]).astype(np.uint32)
+    got = W.philox4x32_10(torch.from_numpy(ck.view(np.int32)).cuda()).cpu().numpy().view(np.uint32)
+    for j, r in enumerate(rows):
+        assert got[j].tolist() == r[6:10]
+    for j in range(len(rows), len(ck)):
+        assert got[j].tolist() == oracle.philox4x32_10(ck[j, :4], ck[j, 4:6]).tolist()
+
+
+@pytest.mark.parametrize("name", sorted(small_graphs()))
+def test_small_graphs_all_pq(name):
+    csr, und = small_graphs()[name]
+    g = Graph.from_csr(csr, undirected=und)
+    for p in PQ5:
+        for q in PQ5:
+            check_parity(csr, None, 17, 9, p, q, seed=int(p * 100 + q * 10), undirected=und,
+                         graph=g)
+
+
+@pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
+@pytest.mark.parametrize("warp_min", [1, 32, 1 << 30], ids=["warp", "mixed", "lane"])
+def test_rmat12_specialisations_and_search_paths(weighted, warp_min):
+    csr = rmat12(weighted)
+    g = Graph.from_csr(csr)
+    g.set_tuning(warp_search_min=warp_min)
+    for (p, q) in [(1.0, 1.0), (2.0, 1.0), (1.0, 0.5), (0.5, 2.0), (4.0, 0.25), (0.25, 4.0)]:
+        check_parity(csr, None, 24, 2, p, q, seed=99, graph=g)
+
+
+@pytest.mark.parametrize("cap", [0, 2])
+def test_exact_fallback_paths(cap):
+    for weighted in (False, True):
+        csr = rmat12(weighted)
+        g = Graph.from_csr(csr)
+        g.set_tuning(trial_cap=cap)
+        for (p, q) in [(0.25, 4.0), (2.0, 0.5), (1.0, 1.0)]:
+            check_parity(csr, None, 12, 1, p, q, seed=3, graph=g)
+    n, e = _law.graph_directed()
+    csr = csr_from_np(*_law.csr_from_edges(n, e, [0.3 + 0.1 * k for k in range(len(e))], False))
+    g = Graph.from_csr(csr, undirected=False)
+    g.set_tuning(trial_cap=cap)
+    check_parity(csr, None, 15, 20, 0.5, 2.0, seed=4, undirected=False, graph=g)
+
+
+@pytest.mark.parametrize("walk_len", [1, 2, 3, 5, 33])
+@pytest.mark.parametrize("wpn", [1, 3])
+def test_ragged_lengths_and_counts(walk_len, wpn):
+    csr = rmat12(True)
+    starts = np.random.default_rng(walk_len).integers(0, csr.num_nodes, 1000 + walk_len)
+    check_parity(csr, starts.astype(np.int32), walk_len, wpn, 0.5, 2.0, seed=walk_len)
+
+
+def test_unaligned_output_buffer():
+    csr = rmat12(False)
+    g = Graph.from_csr(csr)
+    rows, L = 777, 13
+    buf = torch.empty(rows * L + 1, dtype=torch.int32, device="cuda")
+    out = buf[1:].view(rows, L)
+    assert out.data_ptr() % 16 != 0
+    starts = np.arange(rows, dtype=np.int32) % csr.num_nodes
+    check_parity(csr, starts, L, 1, 2.0, 0.5, seed=8, graph=g, out=out)
+
+
+def test_out_of_range_starts_set_status_and_fill_minus_one():
+    csr = rmat12(False)
+    g = Graph.from_csr(csr)
+    starts = torch.tensor([0, -1, 5, csr.num_nodes, 7], dtype=torch.int32, device="cuda")
+    out = walks(g, starts, 6, 1, 1.0, 1.0, seed=1)
+    with pytest.raises(GrapeError) as ei:
+        g.stream_status()
+    assert ei.value.name == "GRAPE_ERR_DEVICE"
+    o = out.cpu().numpy()
+    assert (o[1] == -1).all() and (o[3] == -1).all()
+    assert o[0, 0] == 0 and o[2, 0] == 5 and o[4, 0] == 7
+    g.stream_status()          # cleared
+
+
+def test_argument_errors():
+    csr = rmat12(False)
+    g = Graph.from_csr(csr)
+    for bad in [dict(p=0.0), dict(q=-1.0), dict(p=float("nan")), dict(walk_len=0),
+                dict(walks_per_node=0)]:
+        kw = dict(walk_len=4, walks_per_node=1, p=1.0, q=1.0)
+        kw.update(bad)
+        with pytest.raises(GrapeError) as ei:
+            walks(g, None, kw["walk_len"], kw["walks_per_node"], kw["p"], kw["q"], 0,
+                  out=torch.empty((csr.num_nodes, 4), dtype=torch.int32, device="cuda"))
+        assert ei.value.name == "GRAPE_ERR_INVALID_ARG"
+
+
+def test_invalid_graphs_are_rejected():
+    off = torch.tensor([0, 2, 3, 4], dtype=torch.int64)
+    cases = {
+        "unsorted": (off, torch.tensor([2, 1, 0, 0], dtype=torch.int32), None),
+        "id_range": (off, torch.tensor([1, 7, 0, 0], dtype=torch.int32), None),
+        "offsets": (torch.tensor([0, 3, 2, 4]), torch.tensor([1, 2, 0, 0], dtype=torch.int32), None),
+        "weights": (off, torch.tensor([1, 2, 0, 0], dtype=torch.int32),
+                    torch.tensor([1.0, -1.0, 1.0, 1.0])),
+        "asymmetric": (off, torch.tensor([1, 2, 0, 1], dtype=torch.int32), None),
+    }
+    for name, (o, d, w) in cases.items():
+        with pytest.raises(GrapeError) as ei:
+            Graph(o, d, w, undirected=True, validate=True)
+        assert ei.value.name == "GRAPE_ERR_INVALID_GRAPH", name
+
+
+def test_shards_reassemble_the_job():
+    csr = rmat12(True)
+    g = Graph.from_csr(csr)
+    full = walks(g, None, 20, 3, 0.5, 2.0, seed=17).cpu().numpy()
+    lib = g._lib
+    total = csr.num_nodes * 3
+    bounds = [0, 1, 4097, 9000, total]
+    for b, e in zip(bounds[:-1], bounds[1:]):
+        out = torch.empty((e - b, 20), dtype=torch.int32, device="cuda")
+        import ctypes
+        code = lib.grape_walks_range(g.handle, None, csr.num_nodes, 20, 3, 0.5, 2.0, 17, b, e - b,
+                                     ctypes.c_void_p(out.data_ptr()), W._stream_ptr())
+        assert code == 0
+        assert np.array_equal(out.cpu().numpy(), full[b:e])
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    csr = rmat12(True)
+    g = Graph.from_csr(csr)
+    starts = np.random.default_rng(1).integers(0, csr.num_nodes, 3001).astype(np.int32)
+    dev = walks(g, torch.from_numpy(starts).cuda(), 31, 2, 2.0, 0.5, seed=5).cpu().numpy()
+    host = walks_host(g, starts, 31, 2, 2.0, 0.5, seed=5)
+    assert np.array_equal(dev, host)
+
+
+def test_er1k_workload_full_parity():
+    csr = synth.workload_graph("er1k")
+    job = synth.WORKLOADS["er1k"]["job"]
+    check_parity(csr, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed)
+
+
+def _sampled_parity(name, n_sample, hubs=64, threads=None):
+    spec = synth.WORKLOADS[name]
+    job = spec["job"]
+    csr = synth.workload_graph(name, device="cuda")
+    g = Graph.from_csr(csr, validate=False)
+    out = walks(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed)
+    torch.cuda.synchronize()
+    g.stream_status()
+    n = csr.num_nodes
+    total = n * job.walks_per_node
+    rng = np.random.default_rng(2024)
+    ids = rng.choice(total, size=n_sample, replace=False)
+    deg = csr.degrees()
+    top = torch.topk(deg, hubs).indices.cpu().numpy()
+    hub_ids = (top[None, :] + n * np.arange(job.walks_per_node)[:, None]).ravel()
+    ids = np.unique(np.concatenate([ids, hub_ids, [0, total - 1]]))
+    ids_t = torch.from_numpy(ids).cuda()
+    got = out[ids_t].cpu().numpy()
+    # every step follows an edge: checked on the device for a block of rows
+    blk = out[: min(total, 200_000)].to(torch.int64)
+    a, b = blk[:, :-1], blk[:, 1:]
+    valid = b >= 0
+    keys = csr.offsets.new_zeros(0)
+    row_off = csr.offsets
+    lo = row_off[a.clamp(min=0)]
+    hi = row_off[a.clamp(min=0) + 1]
+    # membership of b in row a by searchsorted over the global (row, dst) key space
+    gkeys = torch.repeat_interleave(torch.arange(n, device="cuda"), (row_off[1:] - row_off[:-1])) * n \
+        + csr.dsts.to(torch.int64)
+    q = a.clamp(min=0) * n + b.clamp(min=0)
+    pos = torch.searchsorted(gkeys, q[valid])
+    ok = gkeys[pos.clamp(max=gkeys.numel() - 1)] == q[valid]
+    assert bool(ok.all()), "a GPU step left the edge set"
+    del gkeys, keys, lo, hi, blk, a, b, q, pos, ok
+    del out
+    torch.cuda.empty_cache()
+    og = oracle.Graph(*csr.numpy())
+    want = np.empty_like(got)
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    parts = np.array_split(np.arange(len(ids)), threads or os.cpu_count() or 4)
+
+    def run(part):
+        want[part] = oracle.walk_rows(og, None, job.walk_len, job.walks_per_node, job.p, job.q,
+                                      job.seed, ids[part])
+
+    with ThreadPoolExecutor(len(parts)) as ex:
+        list(ex.map(run, parts))
+    bad = np.argwhere((got != want).any(axis=1))[:, 0]
+    assert len(bad) == 0, f"{len(bad)} of {len(ids)} sampled rows differ, first id {ids[bad[0]]}"
+    return len(ids)
+
+
+def test_rmat20_weighted_workload_sampled_parity():
+    assert _sampled_parity("rmat20w", 20000) > 20000
+
+
+@pytest.mark.slow
+def test_rmat24_workload_sampled_parity():
+    assert _sampled_parity("rmat24", 20000) > 20000
