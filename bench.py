@@ -352,7 +352,8 @@ def run_ours(args, dist):
                      "algorithmic_bytes_per_launch": alg},
         "counters": {"trials_per_step": cnt["trials"] / max(1, cnt["steps"]),
                      "searches_per_step": cnt["searches"] / max(1, cnt["steps"]),
-                     "warp_searches": cnt["warp_searches"], "fallbacks": cnt["fallbacks"]},
+                     "probes_per_search": cnt["probes"] / max(1, cnt["searches"]),
+                     "fallbacks": cnt["fallbacks"]},
         "clocks": clk,
     }
     if not args.no_batched and dist.rank == 0 and args.workload == "rmat20w":
@@ -405,7 +406,7 @@ def bench_batched(g, csr, dev):
             "speedup_vs_per_request": t_seq / t_batch, "requests": 512, "steps": steps,
             "ms_batched": t_batch * 1e3, "ms_sequential": t_seq * 1e3,
             "tuning": {"chunk_walks": best["chunk_walks"],
-                       "warp_search_min": best["warp_search_min"]}}
+                       "shorter_min": best["shorter_min"]}}
 
 
 # ---------------------------------------------------------------------------

@@ -127,13 +127,12 @@ grape_status_t grape_graph_info(const grape_graph_t* graph, grape_graph_info_t* 
  */
 typedef struct grape_tuning {
     int64_t trial_cap;        /* rejection trials before the exact fallback (default 4096; 0 = always fall back) */
-    int32_t warp_search_min;  /* membership lists at least this long are searched by the whole warp
-                                 (32-ary, one probe per lane); shorter ones by the lane alone */
-    int32_t block_threads;    /* threads per block for walk kernels (multiple of 32, <= 1024) */
+    int32_t shorter_min;      /* undirected graphs: when deg(t) exceeds this, the record of x is
+                                 loaded first and the shorter of N(t), N(x) is searched; otherwise
+                                 N(t) is searched at once (INT32_MAX: always N(t)) */
+    int32_t block_threads;    /* threads per block for walk kernels (multiple of 32, <= 256) */
     int32_t blocks_per_sm;    /* resident blocks per SM for the grid size; 0 = occupancy maximum */
     int32_t chunk_walks;      /* batched and served queues: walks per queue entry */
-    int32_t shorter_list;     /* undirected graphs: 1 = search whichever of N(t), N(x) is shorter */
-    int32_t pad;
 } grape_tuning_t;
 
 grape_status_t grape_graph_get_tuning(const grape_graph_t* graph, grape_tuning_t* tuning);
@@ -222,7 +221,7 @@ grape_status_t grape_walks_batched(const grape_graph_t* graph,
 
 /*
  * Autotune the batched path for this graph: times a grid of (chunk_walks,
- * warp_search_min) on the given requests with CUDA events, and stores the
+ * shorter_min) on the given requests with CUDA events, and stores the
  * fastest pair in the graph's tuning (also returned in *best when not NULL).
  * Writes into the requests' out buffers.  Synchronises `stream`.
  */
@@ -240,13 +239,13 @@ grape_status_t grape_stream_status(const grape_graph_t* graph, grape_stream_t st
 /*
  * Work counters, summed over every walk kernel that ran on this graph while
  * counting was on (off by default; enabling costs one atomic per warp per
- * kernel).  Used for the bytes-per-step roofline accounting.
+ * counter per kernel).  Used for the bytes-per-step roofline accounting.
  */
 typedef struct grape_walk_counters {
     int64_t steps;        /* transitions taken */
     int64_t trials;       /* proposals drawn */
     int64_t searches;     /* membership tests whose outcome decided acceptance */
-    int64_t warp_searches;/* of which warp-cooperative */
+    int64_t probes;       /* list entries loaded by those tests */
     int64_t fallbacks;    /* steps drawn by the exact inverse-transform fallback */
     int64_t walks;        /* rows written */
 } grape_walk_counters_t;

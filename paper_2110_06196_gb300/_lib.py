@@ -37,9 +37,8 @@ class GraphInfo(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("trial_cap", c_i64), ("warp_search_min", c_i32), ("block_threads", c_i32),
-                ("blocks_per_sm", c_i32), ("chunk_walks", c_i32), ("shorter_list", c_i32),
-                ("pad", c_i32)]
+    _fields_ = [("trial_cap", c_i64), ("shorter_min", c_i32), ("block_threads", c_i32),
+                ("blocks_per_sm", c_i32), ("chunk_walks", c_i32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
@@ -53,7 +52,7 @@ class WalkRequest(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [("steps", c_i64), ("trials", c_i64), ("searches", c_i64),
-                ("warp_searches", c_i64), ("fallbacks", c_i64), ("walks", c_i64)]
+                ("probes", c_i64), ("fallbacks", c_i64), ("walks", c_i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -180,7 +180,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
     if (e == cudaSuccess && g->weighted) e = cudaMalloc(&g->pairs, sizeof(int2) * m_alloc);
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * 6);
+    if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * grape::C_COUNT);
     if (e != cudaSuccess) {
         free_graph(g);
         return grape::cuda_status(e);
@@ -190,7 +190,8 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     int* scratch = g->status;   // [0] status word, [1] bad flags, [2] max degree
     int host[4] = {0, 0, 0, 0};
     e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * 6, stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * grape::C_COUNT, stream);
 
     // 1. Offsets first: nothing reads a row before its bounds are known good.
     if (e == cudaSuccess) {
@@ -241,11 +242,10 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     }
 
     g->tuning.trial_cap = 4096;
-    g->tuning.warp_search_min = 512;
+    g->tuning.shorter_min = 8;
     g->tuning.block_threads = 256;
     g->tuning.blocks_per_sm = 0;
     g->tuning.chunk_walks = 64;
-    g->tuning.shorter_list = 1;
     *out = g;
     return GRAPE_OK;
 }
@@ -277,8 +277,8 @@ grape_status_t grape_graph_get_tuning(const grape_graph_t* g, grape_tuning_t* t)
 
 grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t) {
     if (!g || !t) return GRAPE_ERR_INVALID_ARG;
-    if (t->trial_cap < 0 || t->trial_cap > 0xffffffffLL || t->warp_search_min < 1 ||
-        t->block_threads < 32 || t->block_threads > 1024 || (t->block_threads % 32) ||
+    if (t->trial_cap < 0 || t->trial_cap > 0xffffffffLL || t->shorter_min < 0 ||
+        t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
         t->blocks_per_sm < 0 || t->chunk_walks < 1)
         return GRAPE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g->mu);
@@ -306,7 +306,7 @@ grape_status_t grape_counters_enable(grape_graph_t* g, int32_t enable) {
 
 grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out) {
     if (!g || !out) return GRAPE_ERR_INVALID_ARG;
-    unsigned long long c[6];
+    unsigned long long c[grape::C_COUNT];
     GRAPE_CUDA_TRY(cudaDeviceSynchronize());
     GRAPE_CUDA_TRY(cudaMemcpy(c, g->counters, sizeof(c), cudaMemcpyDeviceToHost));
     GRAPE_CUDA_TRY(cudaMemset(g->counters, 0, sizeof(c)));
@@ -314,7 +314,7 @@ grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out)
     out->steps = (int64_t)c[0];
     out->trials = (int64_t)c[1];
     out->searches = (int64_t)c[2];
-    out->warp_searches = (int64_t)c[3];
+    out->probes = (int64_t)c[3];
     out->fallbacks = (int64_t)c[4];
     out->walks = (int64_t)c[5];
     return GRAPE_OK;

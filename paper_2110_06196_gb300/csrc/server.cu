@@ -150,7 +150,8 @@ struct grape_server {
     bool admit_locked(const std::shared_ptr<Req>& q);
     grape_status_t publish(const std::vector<std::shared_ptr<Req>>& reqs);
     uint64_t oldest_live_chunk_locked() const;
-    void finish_locked(const std::shared_ptr<Req>& q, St st, grape_status_t res);
+    // q is taken by value: callers may pass an element of by_slot, which this resets.
+    void finish_locked(std::shared_ptr<Req> q, St st, grape_status_t res);
 };
 
 uint64_t grape_server::oldest_live_chunk_locked() const {
@@ -242,7 +243,7 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
     return cuda_status(e);
 }
 
-void grape_server::finish_locked(const std::shared_ptr<Req>& q, St st, grape_status_t res) {
+void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t res) {
     if (q->arena_off >= 0) {
         arena->release(q->arena_off, q->alloc_bytes);
         q->arena_off = -1;
@@ -331,7 +332,8 @@ void grape_server::run() {
                     kernel_launched = true;
                     stats.kernel_launches++;
                 } else {
-                    for (auto& q : by_slot)
+                    const auto snapshot = by_slot;
+                    for (const auto& q : snapshot)
                         if (q) finish_locked(q, St::Failed, GRAPE_ERR_CUDA);
                 }
             }
@@ -339,7 +341,8 @@ void grape_server::run() {
         // Completions: flag -> copy out -> done.
         {
             std::lock_guard<std::mutex> lk(mu);
-            for (auto& q : by_slot) {
+            const auto snapshot = by_slot;       // finish_locked edits by_slot
+            for (const auto& q : snapshot) {
                 if (!q) continue;
                 if (q->st == St::Admitted && ((volatile unsigned*)h_flags)[q->slot] != 0u) {
                     busy = true;

@@ -3,9 +3,20 @@
 // One lane owns one walk at a time.  All three launch shapes share the engine
 // `walk_loop`: per call (grid-stride over walk ids), batched (a queue of
 // (request, walk range) entries), and served (the same queue, fed while the
-// kernel runs).  Each loop iteration makes ONE rejection trial for every lane
-// that holds a walk, so lanes whose trial counts differ do not serialise the
-// warp on nested loops.  A lane that finishes a walk takes the next one.
+// kernel runs).
+//
+// The engine is a per-lane state machine that issues at most ONE dependent
+// global load per lane per loop iteration and consumes it in the next
+// iteration.  A lane deep in a membership search on a hub list therefore does
+// not hold up the other 31 lanes of its warp; they keep drawing proposals and
+// loading records, so every iteration keeps up to 32 independent gathers per
+// warp in flight.  Phases:
+//   CAND    a proposal's (dst[, weight]) arrived: classify and decide, or
+//           start a membership search
+//   REC     the record of an accepted x arrived: emit x, move, start the next step
+//   RECS    the record of x arrived before a search: pick the shorter of N(t)
+//           and N(x) (undirected graphs) and issue the first probe
+//   SEARCH  one probe of a binary search arrived: narrow or finish
 //
 // Per trial (GRAPE, Methods, eq. alphaRW with the beta/gamma split of eqs. alpha, beta):
 //   Philox4x32-10(key = seed, ctr = (w, s, k)) -> r0..r3
@@ -31,19 +42,21 @@ struct __align__(16) NodeRec {
     float wmax;
 };
 
+enum Counter : int { C_STEPS = 0, C_TRIALS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_COUNT };
+
 struct GraphDev {
     const int4* rec;            // [n] NodeRec viewed as int4
     const int* dsts;            // [m] sorted rows
     const int2* pairs;          // [m] (dst, weight bits) for weighted graphs, else nullptr
     long long n;
     int* status;                // device status word (1 = bad start id)
-    unsigned long long* counters;  // [6] or nullptr
+    unsigned long long* counters;  // [C_COUNT] or nullptr
     int undirected;
 };
 
 // Per-request constants.  Thresholds are stored as T - 1 (T in [1, 2^32]):
 // r2 < T  <=>  r2 <= T - 1.
-struct WalkConst {
+struct __align__(16) WalkConst {
     const int* starts;          // nullptr: start i is node i
     int* out;                   // rows [num_walks][walk_len]
     long long num_starts;
@@ -53,11 +66,12 @@ struct WalkConst {
     unsigned tm1_ret, tm1_in, tm1_out;
     int walk_len;
     double a_ret, a_out;        // 1/p and 1/q for the exact fallback
-    int out_vec;                // 1 when out is 16-byte aligned
+    int out_vec;                // 1 when out is 32-byte aligned (whole-sector row stores)
     int pad;
     unsigned long long* done;   // served requests: finished-walk counter, else nullptr
     unsigned* done_flag;        // served requests: host-mapped completion flag, else nullptr
 };
+static_assert(sizeof(WalkConst) % 16 == 0, "WalkConst is loaded as int4 words");
 
 // Queue entry for batched and served launches: walks [walk_lo, walk_lo + count)
 // of request `req`.
@@ -95,11 +109,8 @@ __device__ __forceinline__ uint4 trial_block(unsigned long long seed, long long 
                          make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
 }
 
-// ---------------------------------------------------------------------------
-// Membership: is key in the sorted list a[0, n)?
-// ---------------------------------------------------------------------------
-
-// Lane-local branchless binary search: ceil(log2 n) + 1 dependent loads.
+// Is key in the sorted list a[0, n)?  Lane-local binary search (used by the
+// exact fallback, which runs outside the pipelined state machine).
 __device__ __forceinline__ bool lane_search(const int* __restrict__ a, int n, int key) {
     if (n <= 0) return false;
     const int* b = a;
@@ -111,35 +122,15 @@ __device__ __forceinline__ bool lane_search(const int* __restrict__ a, int n, in
     return __ldg(b) == key;
 }
 
-// Warp-cooperative 33-ary search for one query (all 32 lanes call it with the
-// same a, n, key): each round every lane loads one pivot, a ballot locates the
-// segment, and the range shrinks 33x; the last <= 32 entries are read as one
-// coalesced segment.  ~log33(n) + 1 round trips instead of log2(n) + 1.
-__device__ __forceinline__ bool warp_search(const int* __restrict__ a, long long n, int key,
-                                            int lane) {
-    long long lo = 0;
-    while (n > 32) {
-        const long long pj = lo + ((long long)(lane + 1) * n) / 33;
-        const int val = __ldg(a + pj);
-        const unsigned m = __ballot_sync(FULL, val <= key);
-        const int c = __popc(m);
-        const long long nlo = (c == 0) ? lo : lo + ((long long)c * n) / 33;
-        const long long nhi = (c == 32) ? lo + n : lo + ((long long)(c + 1) * n) / 33;
-        lo = nlo;
-        n = nhi - nlo;
-    }
-    const bool hit = (lane < n) && (__ldg(a + lo + lane) == key);
-    return __any_sync(FULL, hit);
-}
-
 // ---------------------------------------------------------------------------
 // Lane state
 // ---------------------------------------------------------------------------
+enum Phase : int { PH_START = 0, PH_CAND = 1, PH_REC = 2, PH_RECS = 3, PH_SEARCH = 4 };
+
 struct Lane {
-    long long w;          // walk id within its request
-    long long e0;         // element index of the row start in `out`
+    long long w;          // walk id (Philox counter words 0-1)
     long long off_v, off_t;
-    int* out;
+    int* row;             // this walk's output row
     unsigned long long seed;
     unsigned tm1_ret, tm1_in, tm1_out;
     unsigned k;           // trial index within the step
@@ -149,26 +140,56 @@ struct Lane {
     int deg_v, deg_t;
     float wmax_v;
     int req;              // request index (batched / served), -1 for per-call
-    int out_vec;
-    int b0, b1, b2, b3;   // last four entries written (16-byte store buffer)
+    // the trial in flight
+    int phase;
+    unsigned r2;          // acceptance uniform
+    int x;                // proposal
+    unsigned flags;       // F_* bits below
+    // membership search over sb[0, sn) for skey
+    const int* sb;
+    int sn;
+    int skey;
+};
+
+enum : unsigned {
+    F_ACC_IN = 1u,        // accept if x is in N(t)
+    F_ACC_OUT = 2u,       // accept if x is not in N(t)
+    F_HAVE_RX = 4u,       // the pending record load holds x's record
+    F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
 };
 
 struct LaneCounts {
-    unsigned steps, trials, searches, warp_searches, fallbacks, walks;
+    unsigned c[C_COUNT];
 };
 
-// Row writer: entries that fill an aligned 16-byte group lying inside the row
-// leave as one streaming 16-byte store when the group's last entry arrives;
-// the (at most 3 + 3) entries at the ragged row ends are stored singly.
+// Row writer.  Each lane stages its row's entries in its own 32-byte slot of
+// shared memory; when an entry completes a 32-byte sector that lies inside the
+// row, the sector leaves as two 16-byte stores, so DRAM sees whole sectors.
+// Entries in the (at most two) sectors a row shares with its neighbours are
+// stored singly.
+__device__ __forceinline__ int* out_stage() {
+    extern __shared__ int4 stage_words[];
+    return reinterpret_cast<int*>(stage_words) + 8 * threadIdx.x;
+}
+
 __device__ __forceinline__ void put(Lane& L, int s, int val) {
-    L.b0 = L.b1; L.b1 = L.b2; L.b2 = L.b3; L.b3 = val;
-    const long long e = L.e0 + s;
-    const long long gs = e & ~3LL;
-    const bool full = L.out_vec && (gs >= L.e0) && (gs + 3 < L.e0 + L.len);
-    if (!full) {
-        __stcs(L.out + e, val);
-    } else if ((e & 3) == 3) {
-        __stcs(reinterpret_cast<int4*>(L.out + gs), make_int4(L.b0, L.b1, L.b2, L.b3));
+    int* const p = L.row + s;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t sec = a & ~uintptr_t(31);
+    const bool inside = (L.flags & F_VEC) && sec >= reinterpret_cast<uintptr_t>(L.row) &&
+                        sec + 32 <= reinterpret_cast<uintptr_t>(L.row + L.len);
+    if (!inside) {
+        *p = val;
+        return;
+    }
+    int* st = out_stage();
+    const int j = (int)((a >> 2) & 7);
+    st[j] = val;
+    if (j == 7) {
+        const int4* s4 = reinterpret_cast<const int4*>(st);
+        int4* g4 = reinterpret_cast<int4*>(sec);
+        g4[0] = s4[0];
+        g4[1] = s4[1];
     }
 }
 
@@ -176,13 +197,16 @@ __device__ __forceinline__ void fill_dead(Lane& L, int from) {
     for (int j = from; j < L.len; ++j) put(L, j, -1);
 }
 
-__device__ __forceinline__ NodeRec load_rec(const GraphDev& g, int x) {
-    const int4 r = __ldg(g.rec + x);
+__device__ __forceinline__ NodeRec decode_rec(int4 r) {
     NodeRec n;
     n.off = (long long)(((unsigned long long)(unsigned)r.y << 32) | (unsigned)r.x);
     n.deg = r.z;
     n.wmax = __int_as_float(r.w);
     return n;
+}
+
+__device__ __forceinline__ NodeRec load_rec(const GraphDev& g, int x) {
+    return decode_rec(__ldg(g.rec + x));
 }
 
 // fl(r2 * wmax) < fl(T * w) with both products rounded once (no FMA).
@@ -236,42 +260,27 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, double a_ret, do
     return __ldg(g.dsts + L.off_v + L.deg_v - 1);
 }
 
-// A finished walk: served requests count it and, on the last walk of the
-// request, publish completion to the host.
-__device__ __forceinline__ void finish_walk(const WalkConst& wc, LaneCounts& cnt) {
-    cnt.walks++;
-    if (wc.done != nullptr) {
-        __threadfence();   // this walk's rows are visible before it is counted
-        const unsigned long long prev = atomicAdd(wc.done, 1ull);
-        if (prev + 1 == (unsigned long long)wc.num_walks) {
-            __threadfence_system();
-            *(volatile unsigned*)wc.done_flag = 1u;
-        }
-    }
-}
-
-// Start the walk of row `row` (walk id walk_base + row) of request wc on this lane.  Returns true when the walk needs
-// transitions; false when it is already complete (length 1, dead start, or a
-// start id out of range, whose row is all -1 and which sets the status word).
+// Start the walk of row `row` (walk id walk_base + row) of request wc on this
+// lane.  Returns true when the walk needs transitions (phase PH_START); false
+// when it is already complete (length 1, dead start, or a start id out of
+// range, whose row is all -1 and which sets the status word).
 __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& wc, int req,
-                                           long long row, Lane& L, LaneCounts& cnt) {
+                                           long long row, Lane& L) {
     const long long w = wc.walk_base + row;
     L.w = w;
     L.req = req;
-    L.out = wc.out;
+    L.row = wc.out + row * (long long)wc.walk_len;
     L.len = wc.walk_len;
-    L.e0 = row * (long long)wc.walk_len;
     L.seed = wc.seed;
     L.tm1_ret = wc.tm1_ret;
     L.tm1_in = wc.tm1_in;
     L.tm1_out = wc.tm1_out;
-    L.out_vec = wc.out_vec;
+    L.flags = wc.out_vec ? F_VEC : 0u;
     const long long i = w % wc.num_starts;
     const long long v0 = wc.starts ? (long long)__ldg(wc.starts + i) : i;
     if (v0 < 0 || v0 >= g.n) {
         atomicOr(g.status, 1);
         fill_dead(L, 0);
-        finish_walk(wc, cnt);
         return false;
     }
     put(L, 0, (int)v0);
@@ -283,39 +292,10 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.wmax_v = r.wmax;
     L.s = 1;
     L.k = 0;
-    if (L.len <= 1) {
-        finish_walk(wc, cnt);
-        return false;
-    }
+    L.phase = PH_START;
+    if (L.len <= 1) return false;
     if (r.deg == 0) {
         fill_dead(L, 1);
-        finish_walk(wc, cnt);
-        return false;
-    }
-    return true;
-}
-
-// Move to x.  Returns true while the walk continues.
-__device__ __forceinline__ bool advance(const WalkConst& wc, Lane& L, int x, const NodeRec& rx,
-                                        LaneCounts& cnt) {
-    put(L, L.s, x);
-    cnt.steps++;
-    L.t = L.v;
-    L.off_t = L.off_v;
-    L.deg_t = L.deg_v;
-    L.v = x;
-    L.off_v = rx.off;
-    L.deg_v = rx.deg;
-    L.wmax_v = rx.wmax;
-    L.s++;
-    L.k = 0;
-    if (L.s >= L.len) {
-        finish_walk(wc, cnt);
-        return false;
-    }
-    if (rx.deg == 0) {
-        fill_dead(L, L.s);
-        finish_walk(wc, cnt);
         return false;
     }
     return true;
@@ -323,11 +303,9 @@ __device__ __forceinline__ bool advance(const WalkConst& wc, Lane& L, int x, con
 
 __device__ __forceinline__ void flush_counts(const GraphDev& g, LaneCounts& c) {
     if (g.counters == nullptr) return;
-    unsigned long long v[6] = {c.steps, c.trials, c.searches, c.warp_searches, c.fallbacks,
-                               c.walks};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        unsigned long long x = v[i];
+    for (int i = 0; i < C_COUNT; ++i) {
+        unsigned long long x = c.c[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
         if ((threadIdx.x & 31) == 0 && x) atomicAdd(g.counters + i, x);
@@ -343,30 +321,48 @@ struct GridFeed {
     const WalkConst* wc;     // kernel-parameter copy
     long long next;
     long long stride;
-    __device__ __forceinline__ const WalkConst& req(int) const { return *wc; }
+
+    __device__ __forceinline__ void finish(int, LaneCounts& cnt) { cnt.c[C_WALKS]++; }
+    __device__ __forceinline__ void alphas(int, double& a_ret, double& a_out) const {
+        a_ret = wc->a_ret;
+        a_out = wc->a_out;
+    }
     // Not warp-collective; every lane calls it.
     __device__ __forceinline__ bool refill(const GraphDev& g, Lane& L, bool have,
                                            LaneCounts& cnt) {
         while (!have && next < wc->num_walks) {
-            const long long w = next;
+            const long long row = next;
             next += stride;
-            have = begin_walk(g, *wc, -1, w, L, cnt);
+            have = begin_walk(g, *wc, -1, row, L);
+            if (!have) finish(-1, cnt);
         }
         return have;
     }
 };
 
+// 16-byte loads through L2 only: queue entries and request descriptors of a
+// served queue are rewritten by the host while the kernel runs, so no copy of
+// them may come from an SM's L1.
+__device__ __forceinline__ WalkConst load_walkconst(const WalkConst* p) {
+    WalkConst w;
+    const int4* src = reinterpret_cast<const int4*>(p);
+    int4* dst = reinterpret_cast<int4*>(&w);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(WalkConst) / 16); ++i) dst[i] = __ldcg(src + i);
+    return w;
+}
+
 // Batched and served: a warp takes queue entries (one request's walk range) and
-// deals their walks to its lanes as lanes free up.  The queue head is advanced
-// with a bounded compare-and-swap loop that never passes the published tail,
-// so a served queue can keep growing while the kernel runs.
+// deals their walks to its lanes as lanes free up.  Served queues advance the
+// head with a compare-and-swap that never passes the published tail, so the
+// queue can keep growing while the kernel runs.
 struct QueueFeed {
     const WalkConst* reqs;       // request table (device)
     const Chunk* chunks;         // queue entries (device ring of `ring` entries)
     unsigned long long* head;    // next entry to take
     const volatile unsigned long long* tail;  // entries published so far
     unsigned long long ring;     // ring capacity (entries)
-    long long idle_spins;        // served: polls of an empty queue before giving up
+    long long idle_spins;        // served: polls of an empty queue before giving up; 0 batched
     int* exit_flag;              // served: set when the kernel should stop
     // warp-uniform state
     long long cur_lo;
@@ -374,7 +370,27 @@ struct QueueFeed {
     int cur_req;
     bool drained;
 
-    __device__ __forceinline__ const WalkConst& req(int r) const { return reqs[r]; }
+    __device__ __forceinline__ void finish(int req, LaneCounts& cnt) {
+        cnt.c[C_WALKS]++;
+        if (idle_spins <= 0) return;                 // batched: nothing to publish
+        const WalkConst* r = reqs + req;
+        unsigned long long* done =
+            reinterpret_cast<unsigned long long*>(__ldcg(reinterpret_cast<const long long*>(&r->done)));
+        if (done == nullptr) return;
+        const long long nw = __ldcg(&r->num_walks);
+        unsigned* flag =
+            reinterpret_cast<unsigned*>(__ldcg(reinterpret_cast<const long long*>(&r->done_flag)));
+        __threadfence();   // this walk's rows are visible before it is counted
+        const unsigned long long prev = atomicAdd(done, 1ull);
+        if (prev + 1 == (unsigned long long)nw) {
+            __threadfence_system();
+            *(volatile unsigned*)flag = 1u;
+        }
+    }
+    __device__ __forceinline__ void alphas(int req, double& a_ret, double& a_out) const {
+        a_ret = __ldcg(&reqs[req].a_ret);
+        a_out = __ldcg(&reqs[req].a_out);
+    }
 
     // Take one queue entry for the warp (lane 0 decides, then broadcast).
     // Returns false when the queue is drained (batched) or idle too long (served).
@@ -406,10 +422,11 @@ struct QueueFeed {
                     }
                 }
                 if (got) {
-                    const Chunk c = chunks[h % ring];
-                    lo = c.walk_lo;
-                    cnt = c.count;
-                    rq = c.req;
+                    __threadfence();     // the entry is read after the tail that covers it
+                    const int4 c = __ldcg(reinterpret_cast<const int4*>(chunks + (h % ring)));
+                    lo = (long long)(((unsigned long long)(unsigned)c.y << 32) | (unsigned)c.x);
+                    cnt = c.z;
+                    rq = c.w;
                     ok = 1;
                     break;
                 }
@@ -443,8 +460,9 @@ struct QueueFeed {
             const int n_need = __popc(need);
             const int give = n_need < cur_left ? n_need : cur_left;
             if (!have && rank < give) {
-                const WalkConst& wc = reqs[cur_req];
-                have = begin_walk(g, wc, cur_req, cur_lo + rank, L, cnt);
+                const WalkConst wc = load_walkconst(reqs + cur_req);
+                have = begin_walk(g, wc, cur_req, cur_lo + rank, L);
+                if (!have) finish(cur_req, cnt);
             }
             cur_lo += give;
             cur_left -= give;
@@ -457,107 +475,189 @@ struct QueueFeed {
 // The engine
 // ---------------------------------------------------------------------------
 template <bool WEIGHTED, bool HAS_P, bool HAS_Q, class Feed>
+struct Engine {
+    const GraphDev& g;
+    Feed& feed;
+    unsigned trial_cap;
+    int shorter_min;             // undirected: load rec[x] first to pick the shorter list
+                                 // when deg_t exceeds this
+    LaneCounts& cnt;
+    int2& ld_cand;               // loads in flight (consumed next iteration)
+    int4& ld_rec;
+    int& ld_probe;
+
+    // Emit x and move to it.  Returns true while the walk continues.
+    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg, float wmax) {
+        put(L, L.s, x);
+        cnt.c[C_STEPS]++;
+        L.t = L.v;
+        L.off_t = L.off_v;
+        L.deg_t = L.deg_v;
+        L.v = x;
+        L.off_v = off;
+        L.deg_v = deg;
+        L.wmax_v = wmax;
+        L.s++;
+        L.k = 0;
+        L.flags &= ~F_HAVE_RX;
+        if (L.s >= L.len) {
+            feed.finish(L.req, cnt);
+            return false;
+        }
+        if (deg == 0) {
+            fill_dead(L, L.s);
+            feed.finish(L.req, cnt);
+            return false;
+        }
+        return true;
+    }
+
+    // Issue the next proposal of the current step.  While the trial cap is
+    // spent, steps are drawn by the exact fallback instead.  Returns have.
+    __device__ __forceinline__ bool start_trial(Lane& L) {
+        while (L.k >= trial_cap) {
+            cnt.c[C_FALLBACKS]++;
+            double a_ret, a_out;
+            feed.alphas(L.req, a_ret, a_out);
+            const int xf = exact_fallback<WEIGHTED>(g, L, a_ret, a_out, trial_cap);
+            const NodeRec rf = load_rec(g, xf);
+            if (!advance(L, xf, rf.off, rf.deg, rf.wmax)) return false;
+        }
+        cnt.c[C_TRIALS]++;
+        const uint4 r = trial_block(L.seed, L.w, L.s, L.k);
+        L.r2 = r.z;
+        const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+        const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
+        if (WEIGHTED) ld_cand = __ldg(g.pairs + e);
+        else ld_cand = make_int2(__ldg(g.dsts + e), 0);
+        L.phase = PH_CAND;
+        return true;
+    }
+
+    __device__ __forceinline__ bool reject(Lane& L) {
+        L.k++;
+        return start_trial(L);
+    }
+
+    __device__ __forceinline__ void issue_probe(Lane& L) {
+        cnt.c[C_PROBES]++;
+        ld_probe = __ldg(L.sb + (L.sn > 1 ? (L.sn >> 1) : 0));
+        L.phase = PH_SEARCH;
+    }
+
+    // The membership outcome is known: accept or reject the proposal.
+    __device__ __forceinline__ bool decide(Lane& L, bool found) {
+        const bool accept = (L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0;
+        if (!accept) return reject(L);
+        if (L.flags & F_HAVE_RX) {
+            const NodeRec rx = decode_rec(ld_rec);
+            if (!advance(L, L.x, rx.off, rx.deg, rx.wmax)) return false;
+            return start_trial(L);
+        }
+        ld_rec = __ldg(g.rec + L.x);
+        L.phase = PH_REC;
+        return true;
+    }
+
+    __device__ __forceinline__ bool begin_search(Lane& L, const int* base, int n, int key) {
+        L.sb = base;
+        L.sn = n;
+        L.skey = key;
+        if (n <= 0) return decide(L, false);
+        issue_probe(L);
+        return true;
+    }
+
+    // One state-machine step for a lane that holds a walk.  Returns have.
+    __device__ __forceinline__ bool step(Lane& L) {
+        switch (L.phase) {
+            case PH_START:
+                return start_trial(L);
+            case PH_CAND: {
+                const int x = ld_cand.x;
+                const float wx = __int_as_float(ld_cand.y);
+                L.x = x;
+                bool accept = false, decided = true;
+                if (L.t < 0) {
+                    accept = WEIGHTED ? weighted_accept(L.r2, L.wmax_v, 0xffffffffu, wx) : true;
+                } else if ((HAS_P || HAS_Q) && x == L.t) {
+                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_ret, wx);
+                } else if (!HAS_Q) {
+                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_in, wx);
+                } else {
+                    const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_in, wx);
+                    const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_out, wx);
+                    if (ai == ao) {
+                        accept = ai;
+                    } else {
+                        decided = false;
+                        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT)) | (ai ? F_ACC_IN : 0u) |
+                                  (ao ? F_ACC_OUT : 0u);
+                    }
+                }
+                if (decided) {
+                    if (!accept) return reject(L);
+                    ld_rec = __ldg(g.rec + x);
+                    L.phase = PH_REC;
+                    return true;
+                }
+                cnt.c[C_SEARCHES]++;
+                if (g.undirected && L.deg_t > shorter_min) {
+                    ld_rec = __ldg(g.rec + x);       // needed anyway if accepted
+                    L.phase = PH_RECS;
+                    return true;
+                }
+                return begin_search(L, g.dsts + L.off_t, L.deg_t, x);
+            }
+            case PH_REC: {
+                const NodeRec rx = decode_rec(ld_rec);
+                if (!advance(L, L.x, rx.off, rx.deg, rx.wmax)) return false;
+                return start_trial(L);
+            }
+            case PH_RECS: {
+                // ld_rec keeps x's record until the decision (no other record
+                // load is issued during a search).
+                const NodeRec rx = decode_rec(ld_rec);
+                L.flags |= F_HAVE_RX;
+                // x in N(t)  <=>  t in N(x) for symmetric graphs: search the shorter row.
+                if (rx.deg < L.deg_t) return begin_search(L, g.dsts + rx.off, rx.deg, L.t);
+                return begin_search(L, g.dsts + L.off_t, L.deg_t, L.x);
+            }
+            case PH_SEARCH:
+            default: {
+                const int val = ld_probe;
+                if (val == L.skey) return decide(L, true);
+                if (L.sn <= 1) return decide(L, false);
+                const int half = L.sn >> 1;
+                if (val < L.skey) L.sb += half;
+                L.sn -= half;
+                issue_probe(L);
+                return true;
+            }
+        }
+    }
+};
+
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
-                                          int warp_min, int shorter_list) {
-    const int lane = threadIdx.x & 31;
+                                          int shorter_min) {
     Lane L;
     L.t = -1;
     L.req = -1;
-    LaneCounts cnt = {0, 0, 0, 0, 0, 0};
+    L.phase = PH_START;
+    LaneCounts cnt;
+#pragma unroll
+    for (int i = 0; i < C_COUNT; ++i) cnt.c[i] = 0;
+    int2 ld_cand = make_int2(0, 0);
+    int4 ld_rec = make_int4(0, 0, 0, 0);
+    int ld_probe = 0;
+    Engine<WEIGHTED, HAS_P, HAS_Q, Feed> eng{g, feed, trial_cap, shorter_min, cnt,
+                                             ld_cand, ld_rec, ld_probe};
     bool have = false;
-
     while (true) {
         have = feed.refill(g, L, have, cnt);
         if (!__any_sync(FULL, have)) break;
-
-        const WalkConst& wc = feed.req(L.req < 0 ? 0 : L.req);
-        bool fallback = have && (L.k >= trial_cap);
-        bool trial = have && !fallback;
-        bool need = false, accept = false, acc_in = false, acc_out = false;
-        int x = 0;
-        float wx = 1.0f;
-        NodeRec rx;
-        rx.off = 0; rx.deg = 0; rx.wmax = 0.0f;
-        bool have_rx = false;
-        long long s_off = 0;
-        int s_len = 0, s_key = 0;
-
-        if (trial) {
-            cnt.trials++;
-            const uint4 r = trial_block(L.seed, L.w, L.s, L.k);
-            const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
-            const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-            if (WEIGHTED) {
-                const int2 pr = __ldg(g.pairs + e);
-                x = pr.x;
-                wx = __int_as_float(pr.y);
-            } else {
-                x = __ldg(g.dsts + e);
-            }
-            const unsigned r2 = r.z;
-            if (L.t < 0) {
-                accept = WEIGHTED ? weighted_accept(r2, L.wmax_v, 0xffffffffu, wx) : true;
-            } else if ((HAS_P || HAS_Q) && x == L.t) {
-                accept = accept_test<WEIGHTED>(r2, L.wmax_v, L.tm1_ret, wx);
-            } else if (!HAS_Q) {
-                accept = accept_test<WEIGHTED>(r2, L.wmax_v, L.tm1_in, wx);
-            } else {
-                acc_in = accept_test<WEIGHTED>(r2, L.wmax_v, L.tm1_in, wx);
-                acc_out = accept_test<WEIGHTED>(r2, L.wmax_v, L.tm1_out, wx);
-                if (acc_in == acc_out) accept = acc_in;
-                else need = true;
-            }
-            if (accept || need) {
-                rx = load_rec(g, x);
-                have_rx = true;
-            }
-            if (need) {
-                cnt.searches++;
-                s_off = L.off_t;
-                s_len = L.deg_t;
-                s_key = x;
-                if (shorter_list && g.undirected && rx.deg < L.deg_t) {
-                    s_off = rx.off;
-                    s_len = rx.deg;
-                    s_key = L.t;
-                }
-            }
-        }
-
-        if (HAS_Q) {
-            // Membership phase: short lists by the lane, long ones by the warp.
-            bool found = false;
-            if (need && s_len < warp_min) found = lane_search(g.dsts + s_off, s_len, s_key);
-            unsigned wm = __ballot_sync(FULL, need && s_len >= warp_min);
-            while (wm) {
-                const int leader = __ffs(wm) - 1;
-                wm &= wm - 1;
-                const long long b = __shfl_sync(FULL, s_off, leader);
-                const int n = __shfl_sync(FULL, s_len, leader);
-                const int key = __shfl_sync(FULL, s_key, leader);
-                const bool f = warp_search(g.dsts + b, n, key, lane);
-                if (lane == leader) {
-                    found = f;
-                    cnt.warp_searches++;
-                }
-            }
-            if (need) accept = found ? acc_in : acc_out;
-        }
-
-        if (trial) {
-            if (accept) {
-                have = advance(wc, L, x, rx, cnt);
-            } else if (++L.k >= trial_cap) {
-                fallback = true;
-            }
-        }
-        if (fallback) {
-            cnt.fallbacks++;
-            const int xf = exact_fallback<WEIGHTED>(g, L, wc.a_ret, wc.a_out, trial_cap);
-            const NodeRec rf = load_rec(g, xf);
-            have = advance(wc, L, xf, rf, cnt);
-        }
-        (void)have_rx;
+        if (have) have = eng.step(L);
     }
     flush_counts(g, cnt);
 }

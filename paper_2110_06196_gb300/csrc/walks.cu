@@ -15,6 +15,11 @@ using namespace grape;
 namespace {
 
 constexpr int kMaxThreads = 256;
+// Resident blocks per SM the register allocation is held to: more warps keep
+// more independent gathers in flight, which is what this latency-bound loop
+// needs (4 x 256 threads -> at most 64 registers per thread).
+constexpr int kMinBlocksWalk = 4;
+constexpr int kMinBlocksQueue = 3;
 
 // ---------------------------------------------------------------------------
 // Kernels
@@ -23,21 +28,21 @@ constexpr int kMaxThreads = 256;
 // Per-call walk kernel: the eight specialisations of GRAPE ("Implementation of
 // second-order RWs": p == 1, q == 1, weighted or not) as template arguments.
 template <bool W, bool P, bool Q>
-__global__ void __launch_bounds__(kMaxThreads)
-walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int warp_min, int shorter) {
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
+walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min) {
     GridFeed f;
     f.wc = &wc;
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
-    walk_loop<W, P, Q>(g, f, trial_cap, warp_min, shorter);
+    walk_loop<W, P, Q>(g, f, trial_cap, shorter_min);
 }
 
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
 template <bool W>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocksQueue)
 queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* head,
              const unsigned long long* tail, unsigned long long ring, long long idle_spins,
-             int* exit_flag, unsigned trial_cap, int warp_min, int shorter) {
+             int* exit_flag, unsigned trial_cap, int shorter_min) {
     QueueFeed f;
     f.reqs = reqs;
     f.chunks = chunks;
@@ -50,7 +55,7 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true>(g, f, trial_cap, warp_min, shorter);
+    walk_loop<W, true, true>(g, f, trial_cap, shorter_min);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint32_t* __restrict__ out) {
@@ -93,10 +98,14 @@ sector_probe_kernel(const int4* __restrict__ buf, unsigned long long nsec, long 
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
+// Dynamic shared memory of the walk kernels: one 32-byte output staging slot per thread.
+inline size_t stage_bytes(int threads) { return (size_t)threads * 32; }
+
 template <class K>
 int occupancy_blocks(K kernel, int threads) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, stage_bytes(threads)) !=
+            cudaSuccess ||
         nb < 1)
         nb = 1;
     return nb;
@@ -112,8 +121,8 @@ cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const Wal
     const long long cap = (long long)g->num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    walk_kernel<W, P, Q><<<(unsigned)blocks, threads, 0, stream>>>(
-        g->dev(), wc, (unsigned)t.trial_cap, t.warp_search_min, t.shorter_list);
+    walk_kernel<W, P, Q><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
+        g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min);
     return cudaGetLastError();
 }
 
@@ -175,7 +184,7 @@ grape_status_t make_walk_const(const grape_graph* g, const int32_t* starts, int6
     wc->tm1_out = tm1[2];
     wc->a_ret = alpha[0];
     wc->a_out = alpha[2];
-    wc->out_vec = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0) ? 1 : 0;
+    wc->out_vec = ((reinterpret_cast<uintptr_t>(out) & 31u) == 0) ? 1 : 0;
     wc->done = nullptr;
     wc->done_flag = nullptr;
     return GRAPE_OK;
@@ -209,15 +218,13 @@ cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
     const LaunchShape s = queue_launch_shape(g, t, g->weighted);
     const int nb = blocks > 0 ? blocks : s.blocks;
     if (g->weighted)
-        queue_kernel<true><<<nb, s.threads, 0, stream>>>(g->dev(), reqs, chunks, head, tail, ring,
+        queue_kernel<true><<<nb, s.threads, stage_bytes(s.threads), stream>>>(g->dev(), reqs, chunks, head, tail, ring,
                                                          idle_spins, exit_flag,
-                                                         (unsigned)t.trial_cap,
-                                                         t.warp_search_min, t.shorter_list);
+                                                         (unsigned)t.trial_cap, t.shorter_min);
     else
-        queue_kernel<false><<<nb, s.threads, 0, stream>>>(g->dev(), reqs, chunks, head, tail, ring,
+        queue_kernel<false><<<nb, s.threads, stage_bytes(s.threads), stream>>>(g->dev(), reqs, chunks, head, tail, ring,
                                                           idle_spins, exit_flag,
-                                                          (unsigned)t.trial_cap,
-                                                          t.warp_search_min, t.shorter_list);
+                                                          (unsigned)t.trial_cap, t.shorter_min);
     return cudaGetLastError();
 }
 
@@ -422,7 +429,7 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     const grape_tuning_t base = tuning_of(g);
     const int chunk_grid[] = {16, 32, 64, 128, 256};
-    const int warp_grid[] = {64, 256, 1024, 1 << 30};
+    const int shorter_grid[] = {0, 8, 32, 0x7fffffff};
     cudaEvent_t e0, e1;
     GRAPE_CUDA_TRY(cudaEventCreate(&e0));
     GRAPE_CUDA_TRY(cudaEventCreate(&e1));
@@ -430,10 +437,10 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
     grape_tuning_t best_t = base;
     grape_status_t result = GRAPE_OK;
     for (int cw : chunk_grid) {
-        for (int wm : warp_grid) {
+        for (int sm : shorter_grid) {
             grape_tuning_t t = base;
             t.chunk_walks = cw;
-            t.warp_search_min = wm;
+            t.shorter_min = sm;
             grape_batch_plan* p = nullptr;
             grape_status_t st = build_plan(g, reqs, n, t, &p);
             if (st != GRAPE_OK) { result = st; break; }
@@ -459,7 +466,7 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
     {
         std::lock_guard<std::mutex> lk(g->mu);
         g->tuning.chunk_walks = best_t.chunk_walks;
-        g->tuning.warp_search_min = best_t.warp_search_min;
+        g->tuning.shorter_min = best_t.shorter_min;
     }
     if (best) *best = best_t;
     return GRAPE_OK;

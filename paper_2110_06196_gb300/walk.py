@@ -6,7 +6,9 @@ Every walk step runs in the library's kernels.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
+import weakref
 
 import numpy as np
 import torch
@@ -217,6 +219,20 @@ def autotune_batched(graph: Graph, reqs, stream=None) -> dict:
     return best.as_dict()
 
 
+_live_servers = weakref.WeakSet()
+
+
+@atexit.register
+def _close_servers():
+    # A process must not exit while a resident kernel may still write to the
+    # server's mapped host memory: shut every live server down first.
+    for s in list(_live_servers):
+        try:
+            s.close()
+        except Exception:
+            pass
+
+
 class Server:
     """grape_walk_server_*: continuous batching with the graph resident."""
 
@@ -231,6 +247,7 @@ class Server:
         self._h = h
         self._lib = graph._lib
         self._outs = {}
+        _live_servers.add(self)
 
     def submit(self, starts, walk_len, p, q, seed, walks_per_node=1, out=None):
         """Host starts (copied at once); `out` a host int32 buffer (numpy or pinned

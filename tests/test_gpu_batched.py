@@ -47,12 +47,12 @@ def test_batched_equals_per_call_and_oracle(small):
 
 
 @pytest.mark.parametrize("chunk", [1, 7, 64, 1000])
-@pytest.mark.parametrize("warp_min", [1, 64, 1 << 30])
-def test_batched_independent_of_granularity(small, chunk, warp_min):
+@pytest.mark.parametrize("shorter_min", [0, 16, 0x7fffffff])
+def test_batched_independent_of_granularity(small, chunk, shorter_min):
     csr, g = small
     mix = synth.request_mix(csr.num_nodes, 16, gen_seed=6, max_starts=2000, len_lo=5, len_hi=40)
     ref = [_per_call(g, r) for r in _reqs_from_mix(mix)]
-    g.set_tuning(chunk_walks=chunk, warp_search_min=warp_min)
+    g.set_tuning(chunk_walks=chunk, shorter_min=shorter_min)
     try:
         reqs = _reqs_from_mix(mix)
         plan = BatchPlan(g, reqs)
@@ -65,7 +65,7 @@ def test_batched_independent_of_granularity(small, chunk, warp_min):
                 assert torch.equal(a, b)
         plan.close()
     finally:
-        g.set_tuning(chunk_walks=64, warp_search_min=512)
+        g.set_tuning(chunk_walks=64, shorter_min=8)
 
 
 def test_autotune_picks_a_grid_point_and_keeps_bytes(small):

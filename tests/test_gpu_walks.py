@@ -2,7 +2,8 @@
 CPU oracle: bit-exact int32 rows.
 
 Coverage: the eight p == 1 / q == 1 / weighted specialisations over a (p, q)
-grid; lane-only, mixed and warp-only membership search; the exact fallback
+grid; membership searched in N(t) only, in the shorter of N(t) and N(x), or
+mixed by degree; the exact fallback
 (trial caps 0 and 2); tiny and structured graphs (house with a self-loop,
 directed with a dead end, star, path, K_n); ragged walk counts and lengths,
 unaligned output, explicit start lists, out-of-range starts, shards of a job,
@@ -102,11 +103,11 @@ def test_small_graphs_all_pq(name):
 
 
 @pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
-@pytest.mark.parametrize("warp_min", [1, 32, 1 << 30], ids=["warp", "mixed", "lane"])
-def test_rmat12_specialisations_and_search_paths(weighted, warp_min):
+@pytest.mark.parametrize("shorter_min", [0, 16, 0x7fffffff], ids=["shorter", "mixed", "n_t"])
+def test_rmat12_specialisations_and_search_paths(weighted, shorter_min):
     csr = rmat12(weighted)
     g = Graph.from_csr(csr)
-    g.set_tuning(warp_search_min=warp_min)
+    g.set_tuning(shorter_min=shorter_min)
     for (p, q) in [(1.0, 1.0), (2.0, 1.0), (1.0, 0.5), (0.5, 2.0), (4.0, 0.25), (0.25, 4.0)]:
         check_parity(csr, None, 24, 2, p, q, seed=99, graph=g)
 
