@@ -17,7 +17,7 @@
  *     with key = seed and counter = (w lo, w hi, s, k);
  *   - the proposal is x = row_v[floor((r1:r0) * deg_v / 2^64)];
  *   - it is accepted iff r2 < T_class (unweighted) or
- *     fl(r2 * wmax_v) < fl(T_class * w_vx) (weighted, IEEE double products).
+ *     r2 * wmax_v < T_class * w_vx (weighted, compared exactly over the reals).
  *     Here T_class = floor(alpha_class / max(1/p, 1, 1/q) * 2^32) and wmax_v is
  *     the largest weight in the row of v;
  *   - after `trial_cap` rejections the step is drawn by inverse transform over

@@ -60,6 +60,8 @@ def _bind(lib):
     lib.oracle_philox4x32_10.restype = None
     lib.oracle_thresholds.argtypes = [dbl, dbl, vp]
     lib.oracle_thresholds.restype = None
+    lib.oracle_weighted_accept.argtypes = [ctypes.c_uint32, ctypes.c_float, u64, ctypes.c_float]
+    lib.oracle_weighted_accept.restype = ctypes.c_int
     lib.oracle_node_wmax.argtypes = [vp, vp, i64, vp]
     lib.oracle_node_wmax.restype = None
     lib.oracle_next.argtypes = [vp, vp, vp, vp, i32, i32, dbl, dbl, u64, i64, i32, i64, vp]
@@ -121,6 +123,12 @@ def philox4x32_10(ctr, key, lib=None):
     o = np.zeros(4, dtype=np.uint32)
     lib.oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
     return o
+
+
+def weighted_accept(r2, wmax, T, w, lib=None):
+    """The weighted acceptance test r2 * wmax < T * w (exact)."""
+    lib = lib or load()
+    return bool(lib.oracle_weighted_accept(int(r2), float(wmax), int(T), float(w)))
 
 
 def thresholds(p, q, lib=None):

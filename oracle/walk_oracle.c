@@ -24,8 +24,11 @@
  *       key = (seed lo, seed hi), counter = (w lo, w hi, s, k),
  *   proposes x = row_v[ floor(((r1:r0) * deg_v) / 2^64) ] and accepts iff
  *       unweighted:  r2 < T_c
- *       weighted:    fl(r2 * wmax_v) < fl(T_c * w_vx)   (two IEEE double products)
- *   where wmax_v is the largest weight in the row of v.  After trial_cap
+ *       weighted:    r2 * wmax_v < T_c * w_vx          (exact, over the reals)
+ *   where wmax_v is the largest weight in the row of v.  The proposal x is
+ *   uniform over the row, so x is accepted with probability (to within
+ *   2^-32) (alpha_c / amax) * (w_vx / wmax_v), proportional to pi_vx: the
+ *   accepted draw follows eq. alphaRW exactly.  After trial_cap
  *   rejected trials the step is drawn exactly by inverse transform over the
  *   cumulative sum of pi in row order, the paper's own on-the-fly sampler
  *   ("Efficient sampling for Node2Vec RWs"), with u taken from the Philox block
@@ -33,9 +36,8 @@
  *
  * Written for clarity, not speed: one walk at a time, one trial at a time,
  * plain binary search for membership, no blocking and no reordering.
- * Build with -ffp-contract=off so that no product is fused into another
- * operation (the weighted acceptance test relies on two separately rounded
- * products).
+ * Build with -ffp-contract=off so that no product of the fallback's cumulative
+ * sum is fused into another operation.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -97,6 +99,37 @@ void oracle_thresholds(double p, double q, uint64_t T[3])
         double ratio = alpha[c] / amax;                 /* in (0, 1] */
         T[c] = (uint64_t)floor(ratio * 4294967296.0);   /* 2^32 when ratio == 1 */
     }
+}
+
+/* x = M * 2^E exactly, with M a non-negative integer below 2^24 (frexpf gives
+ * x = f * 2^e with f in [0.5, 1), and an fp32 value has at most 24 significant
+ * bits, so f * 2^24 is an integer). */
+static void split_float(float x, uint64_t* M, int* E)
+{
+    int e;
+    float f = frexpf(x, &e);
+    *M = (uint64_t)ldexpf(f, 24);
+    *E = e - 24;
+}
+
+/* Exact test r2 * wmax < T * w over the reals, for positive finite fp32 weights. */
+int oracle_weighted_accept(uint32_t r2, float wmax, uint64_t T, float w)
+{
+    uint64_t m1, m2;
+    int e1, e2;
+    split_float(wmax, &m1, &e1);
+    split_float(w, &m2, &e2);
+    unsigned __int128 lhs = (unsigned __int128)r2 * m1;   /* times 2^e1, below 2^56 */
+    unsigned __int128 rhs = (unsigned __int128)T * m2;    /* times 2^e2, at most 2^56 */
+    int d = e1 - e2;
+    if (d >= 0) {
+        if (lhs == 0) return rhs > 0;
+        if (d > 60) return 0;                 /* lhs * 2^d >= 2^60 > rhs */
+        return (lhs << d) < rhs;
+    }
+    if (rhs == 0) return 0;
+    if (-d > 60) return 1;                    /* rhs * 2^-d >= 2^60 > lhs */
+    return lhs < (rhs << (-d));
 }
 
 /* Largest weight of every row (0 for an empty row).  Weights are fp32. */
@@ -164,9 +197,7 @@ int32_t oracle_next(const int64_t* offsets, const int32_t* dsts, const float* we
         if (weights == NULL) {
             accept = (uint64_t)r[2] < thr;
         } else {
-            double lhs = (double)r[2] * (double)wmax[v];
-            double rhs = (double)thr * (double)weights[off + (int64_t)idx];
-            accept = lhs < rhs;
+            accept = oracle_weighted_accept(r[2], wmax[v], thr, weights[off + (int64_t)idx]);
         }
         if (accept) return x;
     }

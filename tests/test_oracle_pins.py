@@ -219,3 +219,24 @@ def test_parallel_equals_serial():
     a, _ = oracle.walks(g, None, 20, 3, 0.5, 2.0, seed=3)
     b = oracle.walks_parallel(g, None, 20, 3, 0.5, 2.0, seed=3, threads=4)
     assert np.array_equal(a, b)
+
+
+def test_weighted_rule_is_exact_rational_comparison():
+    # Pinned against Python's exact rationals: r2 * wmax < T * w over the reals.
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    f32 = np.float32
+    cases = []
+    for _ in range(20000):
+        w1 = f32(rng.uniform(0.1, 1.0))
+        w2 = f32(w1 * f32(rng.uniform(0.05, 1.0)))
+        cases.append((int(rng.integers(0, 2**32)), w1, int(rng.integers(1, 2**32 + 1)), w2))
+    # ties, zero r2, subnormal and far-apart exponents
+    tiny = np.frombuffer(np.uint32(5).tobytes(), np.float32)[0]
+    cases += [(2**31, f32(1.0), 2**31, f32(1.0)), (2**31 - 1, f32(1.0), 2**31, f32(1.0)),
+              (0, f32(1.0), 1, tiny), (1, f32(1.0), 2**32, tiny), (3, f32(0.75), 2, f32(0.5)),
+              (2, f32(0.75), 3, f32(0.5)), (1, f32(3e38), 2**32, f32(1e-30)),
+              (2**32 - 1, tiny, 2**32, tiny), (2**32 - 1, f32(2.0) * tiny, 2**32, tiny)]
+    for r2, wmax, T, w in cases:
+        want = Fraction(r2) * Fraction(float(wmax)) < Fraction(T) * Fraction(float(w))
+        assert oracle.weighted_accept(r2, wmax, T, w) == want, (r2, wmax, T, w)

@@ -4,7 +4,8 @@ the oracle source and compiled on the CPU, fails at least one pin.
 Mistakes: p and q swapped; the return test dropped (open neighbourhood); the
 range reduction one short; the weight left out of the acceptance test; the
 membership operands transposed; alpha left out of the fallback; the previous node
-updated after the current one; the wrong start index; acceptance inverted.
+updated after the current one; the wrong start index; acceptance inverted; the
+weighted test accepting ties or shifting the wrong way.
 """
 import os
 
@@ -21,8 +22,10 @@ PLANTS = {
                  "double a_ret = 1.0 / q, a_in = 1.0, a_out = 1.0 / p;"),
     "open_neighbourhood": ("    if (x == t) return CLS_RETURN;\n", ""),
     "range_one_short": ("* deg) >> 64)", "* (deg - 1)) >> 64)"),
-    "weight_ignored": ("(double)thr * (double)weights[off + (int64_t)idx]",
-                       "(double)thr * (double)wmax[v]"),
+    "weight_ignored": ("oracle_weighted_accept(r[2], wmax[v], thr, weights[off + (int64_t)idx])",
+                       "oracle_weighted_accept(r[2], wmax[v], thr, wmax[v])"),
+    "weighted_tie_accepted": ("return (lhs << d) < rhs;", "return (lhs << d) <= rhs;"),
+    "weighted_exponent_gap_sign": ("int d = e1 - e2;", "int d = e2 - e1;"),
     "membership_transposed": ("in_row(offsets, dsts, t, x)", "in_row(offsets, dsts, x, t)"),
     "fallback_without_alpha": ("double a = (cls == CLS_FIRST) ? 1.0 : alpha[cls];",
                                "double a = 1.0;"),
@@ -74,6 +77,15 @@ def pin_battery(lib):
     rows, _ = oracle.walks(g, starts, 8, 3, 1.0, 1.0, seed=2)
     if not all(rows[w, 0] == starts[w % len(starts)] for w in range(len(rows))):
         failed.append("starts")
+    # The weighted rule against exact rationals (ties included).
+    from fractions import Fraction
+    f32 = np.float32
+    for r2, wm, T, w in [(2**31, f32(1.0), 2**31, f32(1.0)), (3, f32(0.75), 2, f32(0.5)),
+                         (5, f32(0.5), 4, f32(0.25)), (2**20, f32(0.9), 2**30, f32(0.001))]:
+        want = Fraction(r2) * Fraction(float(wm)) < Fraction(T) * Fraction(float(w))
+        if oracle.weighted_accept(r2, wm, T, w, lib=lib) != want:
+            failed.append("weighted_rule")
+            break
     # First-order unweighted walks accept every proposal: one trial per step.
     st = oracle.OracleStats()
     oracle.walks(g, None, 10, 5, 1.0, 1.0, seed=4, stats=st)
