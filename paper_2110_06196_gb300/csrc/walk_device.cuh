@@ -22,7 +22,7 @@
 //   Philox4x32-10(key = seed, ctr = (w, s, k)) -> r0..r3
 //   e = off_v + mulhi64(r1:r0, deg_v); x = dsts[e] (+ w_vx)
 //   class: x == t -> return (1/p); x in N(t) -> in (1); else out (1/q)
-//   accept iff r2 < T_class  (weighted: r2 * wmax_v < T_class * w_vx in fp64)
+//   accept iff r2 < T_class  (weighted: r2 * wmax_v < T_class * w_vx, exactly)
 // The membership search runs only when the in and out thresholds give different
 // answers for this r2.  The decision is the same function of (r2, class) as
 // always, so the bytes written do not change.
@@ -209,11 +209,22 @@ __device__ __forceinline__ NodeRec load_rec(const GraphDev& g, int x) {
     return decode_rec(__ldg(g.rec + x));
 }
 
-// fl(r2 * wmax) < fl(T * w) with both products rounded once (no FMA).
+// Weighted acceptance, exact: r2 * wmax < T * w in real arithmetic, with
+// T = tm1 + 1 <= 2^32, r2 < 2^32 and 0 < w <= wmax finite fp32.  Writing an fp32
+// value as M * 2^E (M < 2^24 an integer) turns the test into
+// (r2 * M_wmax) << (E_wmax - E_w) < T * M_w, evaluated in integers.
 __device__ __forceinline__ bool weighted_accept(unsigned r2, float wmax, unsigned tm1, float w) {
-    const double lhs = __dmul_rn((double)r2, (double)wmax);
-    const double rhs = __dmul_rn((double)tm1 + 1.0, (double)w);
-    return lhs < rhs;
+    const unsigned b1 = __float_as_uint(wmax), b2 = __float_as_uint(w);
+    const unsigned e1 = (b1 >> 23) & 0xffu, e2 = (b2 >> 23) & 0xffu;
+    const unsigned long long m1 = (b1 & 0x7fffffu) | (e1 ? 0x800000u : 0u);
+    const unsigned long long m2 = (b2 & 0x7fffffu) | (e2 ? 0x800000u : 0u);
+    const int d = (int)(e1 ? e1 : 1u) - (int)(e2 ? e2 : 1u);   // >= 0 since w <= wmax
+    const unsigned long long lhs = (unsigned long long)r2 * m1;        // < 2^56
+    const unsigned long long rhs = ((unsigned long long)tm1 + 1ull) * m2;  // <= 2^56
+    if (lhs == 0) return rhs != 0;
+    if (d >= 64) return false;
+    if (d > 0 && (lhs >> (64 - d)) != 0) return false;
+    return (lhs << d) < rhs;
 }
 
 template <bool WEIGHTED>
@@ -512,9 +523,15 @@ struct Engine {
         return true;
     }
 
-    // Issue the next proposal of the current step.  While the trial cap is
-    // spent, steps are drawn by the exact fallback instead.  Returns have.
-    __device__ __forceinline__ bool start_trial(Lane& L) {
+    // Actions a lane asks for in one iteration.  The phase logic (divergent,
+    // short) only decides; the work itself (move, Philox + proposal load,
+    // record load, probe load) then runs once per iteration for all lanes that
+    // asked for it, so no warp issues several copies of it.
+    enum : int { A_NONE = 0, A_REC = 1, A_PROBE = 2, A_TRIAL = 4, A_ADV = 8 };
+
+    // Draw the next proposal of the current step and load it.  While the trial
+    // cap is spent, steps are drawn by the exact fallback instead.  Returns have.
+    __device__ __forceinline__ bool trial(Lane& L) {
         while (L.k >= trial_cap) {
             cnt.c[C_FALLBACKS]++;
             double a_ret, a_out;
@@ -534,50 +551,38 @@ struct Engine {
         return true;
     }
 
-    __device__ __forceinline__ bool reject(Lane& L) {
-        L.k++;
-        return start_trial(L);
-    }
-
-    __device__ __forceinline__ void issue_probe(Lane& L) {
-        cnt.c[C_PROBES]++;
-        ld_probe = __ldg(L.sb + (L.sn > 1 ? (L.sn >> 1) : 0));
-        L.phase = PH_SEARCH;
-    }
-
-    // The membership outcome is known: accept or reject the proposal.
-    __device__ __forceinline__ bool decide(Lane& L, bool found) {
-        const bool accept = (L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0;
-        if (!accept) return reject(L);
-        if (L.flags & F_HAVE_RX) {
-            const NodeRec rx = decode_rec(ld_rec);
-            if (!advance(L, L.x, rx.off, rx.deg, rx.wmax)) return false;
-            return start_trial(L);
+    // Decision of a proposal whose membership outcome is known.
+    __device__ __forceinline__ int decided(Lane& L, bool accept) {
+        if (!accept) {
+            L.k++;
+            L.flags &= ~F_HAVE_RX;
+            return A_TRIAL;
         }
-        ld_rec = __ldg(g.rec + L.x);
+        if (L.flags & F_HAVE_RX) return A_ADV | A_TRIAL;
         L.phase = PH_REC;
-        return true;
+        return A_REC;
     }
 
-    __device__ __forceinline__ bool begin_search(Lane& L, const int* base, int n, int key) {
+    __device__ __forceinline__ int search_from(Lane& L, const int* base, int n, int key) {
         L.sb = base;
         L.sn = n;
         L.skey = key;
-        if (n <= 0) return decide(L, false);
-        issue_probe(L);
-        return true;
+        if (n <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
+        L.phase = PH_SEARCH;
+        return A_PROBE;
     }
 
-    // One state-machine step for a lane that holds a walk.  Returns have.
-    __device__ __forceinline__ bool step(Lane& L) {
+    // Phase logic for a lane that holds a walk: consume last iteration's load
+    // and choose this iteration's actions.
+    __device__ __forceinline__ int consume(Lane& L) {
         switch (L.phase) {
             case PH_START:
-                return start_trial(L);
+                return A_TRIAL;
             case PH_CAND: {
                 const int x = ld_cand.x;
                 const float wx = __int_as_float(ld_cand.y);
                 L.x = x;
-                bool accept = false, decided = true;
+                bool accept = false;
                 if (L.t < 0) {
                     accept = WEIGHTED ? weighted_accept(L.r2, L.wmax_v, 0xffffffffu, wx) : true;
                 } else if ((HAS_P || HAS_Q) && x == L.t) {
@@ -587,54 +592,61 @@ struct Engine {
                 } else {
                     const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_in, wx);
                     const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_out, wx);
-                    if (ai == ao) {
-                        accept = ai;
-                    } else {
-                        decided = false;
+                    if (ai != ao) {
+                        // The class decides: x in N(t)?
+                        cnt.c[C_SEARCHES]++;
                         L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT)) | (ai ? F_ACC_IN : 0u) |
                                   (ao ? F_ACC_OUT : 0u);
+                        if (g.undirected && L.deg_t > shorter_min) {
+                            L.phase = PH_RECS;           // x's record first: needed if accepted
+                            return A_REC;
+                        }
+                        return search_from(L, g.dsts + L.off_t, L.deg_t, x);
                     }
+                    accept = ai;
                 }
-                if (decided) {
-                    if (!accept) return reject(L);
-                    ld_rec = __ldg(g.rec + x);
-                    L.phase = PH_REC;
-                    return true;
-                }
-                cnt.c[C_SEARCHES]++;
-                if (g.undirected && L.deg_t > shorter_min) {
-                    ld_rec = __ldg(g.rec + x);       // needed anyway if accepted
-                    L.phase = PH_RECS;
-                    return true;
-                }
-                return begin_search(L, g.dsts + L.off_t, L.deg_t, x);
+                return decided(L, accept);
             }
-            case PH_REC: {
-                const NodeRec rx = decode_rec(ld_rec);
-                if (!advance(L, L.x, rx.off, rx.deg, rx.wmax)) return false;
-                return start_trial(L);
-            }
+            case PH_REC:
+                return A_ADV | A_TRIAL;
             case PH_RECS: {
                 // ld_rec keeps x's record until the decision (no other record
                 // load is issued during a search).
                 const NodeRec rx = decode_rec(ld_rec);
                 L.flags |= F_HAVE_RX;
                 // x in N(t)  <=>  t in N(x) for symmetric graphs: search the shorter row.
-                if (rx.deg < L.deg_t) return begin_search(L, g.dsts + rx.off, rx.deg, L.t);
-                return begin_search(L, g.dsts + L.off_t, L.deg_t, L.x);
+                if (rx.deg < L.deg_t) return search_from(L, g.dsts + rx.off, rx.deg, L.t);
+                return search_from(L, g.dsts + L.off_t, L.deg_t, L.x);
             }
             case PH_SEARCH:
             default: {
                 const int val = ld_probe;
-                if (val == L.skey) return decide(L, true);
-                if (L.sn <= 1) return decide(L, false);
+                if (val == L.skey) return decided(L, (L.flags & F_ACC_IN) != 0);
+                if (L.sn <= 1) return decided(L, (L.flags & F_ACC_OUT) != 0);
                 const int half = L.sn >> 1;
                 if (val < L.skey) L.sb += half;
                 L.sn -= half;
-                issue_probe(L);
-                return true;
+                return A_PROBE;
             }
         }
+    }
+
+    // One iteration for a lane (have == true on entry).  Returns have.
+    __device__ __forceinline__ bool step(Lane& L) {
+        int act = consume(L);
+        bool have = true;
+        if (act & A_ADV) {
+            const NodeRec rx = decode_rec(ld_rec);
+            have = advance(L, L.x, rx.off, rx.deg, rx.wmax);
+            if (!have) act = A_NONE;
+        }
+        if (act & A_TRIAL) have = trial(L);
+        if (act & A_REC) ld_rec = __ldg(g.rec + L.x);
+        if (act & A_PROBE) {
+            cnt.c[C_PROBES]++;
+            ld_probe = __ldg(L.sb + (L.sn > 1 ? (L.sn >> 1) : 0));
+        }
+        return have;
     }
 };
 
