@@ -175,7 +175,12 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
-    const size_t m_alloc = (size_t)(num_entries > 0 ? num_entries : 1);
+    // dsts is padded by four entries so that a search probe, which reads the
+    // aligned 16-byte block around a list position, never leaves the allocation.
+    const size_t m_alloc = (size_t)num_entries + 4;
+    // Random 32-byte gathers are the whole workload: ask the L2 not to widen a
+    // miss into a 64- or 128-byte DRAM fetch (a per-context limit).
+    if (e == cudaSuccess) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
     if (e == cudaSuccess && g->weighted) e = cudaMalloc(&g->pairs, sizeof(int2) * m_alloc);

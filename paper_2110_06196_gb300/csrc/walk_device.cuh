@@ -16,7 +16,8 @@
 //   REC     the record of an accepted x arrived: emit x, move, start the next step
 //   RECS    the record of x arrived before a search: pick the shorter of N(t)
 //           and N(x) (undirected graphs) and issue the first probe
-//   SEARCH  one probe of a binary search arrived: narrow or finish
+//   SEARCH  one probe of a search arrived (the aligned 16-byte block of the
+//           list around the range's midpoint): narrow or finish
 //
 // Per trial (GRAPE, Methods, eq. alphaRW with the beta/gamma split of eqs. alpha, beta):
 //   Philox4x32-10(key = seed, ctr = (w, s, k)) -> r0..r3
@@ -145,10 +146,9 @@ struct Lane {
     unsigned r2;          // acceptance uniform
     int x;                // proposal
     unsigned flags;       // F_* bits below
-    // membership search over sb[0, sn) for skey
+    // membership search over sb[0, sn) for x (or for t, with F_KEY_T)
     const int* sb;
     int sn;
-    int skey;
 };
 
 enum : unsigned {
@@ -156,10 +156,23 @@ enum : unsigned {
     F_ACC_OUT = 2u,       // accept if x is not in N(t)
     F_HAVE_RX = 4u,       // the pending record load holds x's record
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
+    F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
 };
 
-struct LaneCounts {
+// Work counters, kept only by the counting instantiation of the kernels.
+template <bool ON>
+struct Counts {
     unsigned c[C_COUNT];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int i = 0; i < C_COUNT; ++i) c[i] = 0;
+    }
+    __device__ __forceinline__ void add(int i) { c[i]++; }
+};
+template <>
+struct Counts<false> {
+    __device__ __forceinline__ void clear() {}
+    __device__ __forceinline__ void add(int) {}
 };
 
 // Row writer.  Each lane stages its row's entries in its own 32-byte slot of
@@ -172,12 +185,12 @@ __device__ __forceinline__ int* out_stage() {
     return reinterpret_cast<int*>(stage_words) + 8 * threadIdx.x;
 }
 
-__device__ __forceinline__ void put(Lane& L, int s, int val) {
-    int* const p = L.row + s;
+__device__ __forceinline__ void put(const Lane& L, int* row, int s, int val, int len) {
+    int* const p = row + s;
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
     const uintptr_t sec = a & ~uintptr_t(31);
-    const bool inside = (L.flags & F_VEC) && sec >= reinterpret_cast<uintptr_t>(L.row) &&
-                        sec + 32 <= reinterpret_cast<uintptr_t>(L.row + L.len);
+    const bool inside = (L.flags & F_VEC) && sec >= reinterpret_cast<uintptr_t>(row) &&
+                        sec + 32 <= reinterpret_cast<uintptr_t>(row + len);
     if (!inside) {
         *p = val;
         return;
@@ -193,8 +206,8 @@ __device__ __forceinline__ void put(Lane& L, int s, int val) {
     }
 }
 
-__device__ __forceinline__ void fill_dead(Lane& L, int from) {
-    for (int j = from; j < L.len; ++j) put(L, j, -1);
+__device__ __forceinline__ void fill_dead(const Lane& L, int* row, int from, int len) {
+    for (int j = from; j < len; ++j) put(L, row, j, -1, len);
 }
 
 __device__ __forceinline__ NodeRec decode_rec(int4 r) {
@@ -237,9 +250,9 @@ __device__ __forceinline__ bool accept_test(unsigned r2, float wmax, unsigned tm
 // cumulative sum of pi in row order (GRAPE, "Efficient sampling for Node2Vec
 // RWs"), in fp64 with every product and sum rounded separately.
 template <bool WEIGHTED>
-__device__ int exact_fallback(const GraphDev& g, const Lane& L, double a_ret, double a_out,
-                              unsigned trial_cap) {
-    const uint4 r = trial_block(L.seed, L.w, L.s, trial_cap);
+__device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long long seed,
+                              double a_ret, double a_out, unsigned trial_cap) {
+    const uint4 r = trial_block(seed, L.w, L.s, trial_cap);
     const bool first = (L.t < 0);
     double total = 0.0;
     for (int j = 0; j < L.deg_v; ++j) {
@@ -291,10 +304,10 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     const long long v0 = wc.starts ? (long long)__ldg(wc.starts + i) : i;
     if (v0 < 0 || v0 >= g.n) {
         atomicOr(g.status, 1);
-        fill_dead(L, 0);
+        fill_dead(L, L.row, 0, wc.walk_len);
         return false;
     }
-    put(L, 0, (int)v0);
+    put(L, L.row, 0, (int)v0, wc.walk_len);
     const NodeRec r = load_rec(g, (int)v0);
     L.v = (int)v0;
     L.t = -1;
@@ -304,15 +317,17 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.s = 1;
     L.k = 0;
     L.phase = PH_START;
-    if (L.len <= 1) return false;
+    if (wc.walk_len <= 1) return false;
     if (r.deg == 0) {
-        fill_dead(L, 1);
+        fill_dead(L, L.row, 1, wc.walk_len);
         return false;
     }
     return true;
 }
 
-__device__ __forceinline__ void flush_counts(const GraphDev& g, LaneCounts& c) {
+__device__ __forceinline__ void flush_counts(const GraphDev&, Counts<false>&) {}
+
+__device__ __forceinline__ void flush_counts(const GraphDev& g, Counts<true>& c) {
     if (g.counters == nullptr) return;
 #pragma unroll
     for (int i = 0; i < C_COUNT; ++i) {
@@ -333,14 +348,27 @@ struct GridFeed {
     long long next;
     long long stride;
 
-    __device__ __forceinline__ void finish(int, LaneCounts& cnt) { cnt.c[C_WALKS]++; }
+    // Per-call constants are uniform: read them from the kernel parameters
+    // (constant bank) instead of holding them in every lane's registers.
+    __device__ __forceinline__ unsigned long long seed(const Lane&) const { return wc->seed; }
+    __device__ __forceinline__ int len(const Lane&) const { return wc->walk_len; }
+    __device__ __forceinline__ unsigned tm1_ret(const Lane&) const { return wc->tm1_ret; }
+    __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wc->tm1_in; }
+    __device__ __forceinline__ unsigned tm1_out(const Lane&) const { return wc->tm1_out; }
+    // the row of walk id w is row w - walk_base of this call's output
+    __device__ __forceinline__ int* row(const Lane& L) const {
+        return wc->out + (L.w - wc->walk_base) * (long long)wc->walk_len;
+    }
+
+    template <class C>
+    __device__ __forceinline__ void finish(int, C& cnt) { cnt.add(C_WALKS); }
     __device__ __forceinline__ void alphas(int, double& a_ret, double& a_out) const {
         a_ret = wc->a_ret;
         a_out = wc->a_out;
     }
     // Not warp-collective; every lane calls it.
-    __device__ __forceinline__ bool refill(const GraphDev& g, Lane& L, bool have,
-                                           LaneCounts& cnt) {
+    template <class C>
+    __device__ __forceinline__ bool refill(const GraphDev& g, Lane& L, bool have, C& cnt) {
         while (!have && next < wc->num_walks) {
             const long long row = next;
             next += stride;
@@ -381,8 +409,17 @@ struct QueueFeed {
     int cur_req;
     bool drained;
 
-    __device__ __forceinline__ void finish(int req, LaneCounts& cnt) {
-        cnt.c[C_WALKS]++;
+    // Per-request constants differ between lanes: held in the lane.
+    __device__ __forceinline__ unsigned long long seed(const Lane& L) const { return L.seed; }
+    __device__ __forceinline__ int len(const Lane& L) const { return L.len; }
+    __device__ __forceinline__ unsigned tm1_ret(const Lane& L) const { return L.tm1_ret; }
+    __device__ __forceinline__ unsigned tm1_in(const Lane& L) const { return L.tm1_in; }
+    __device__ __forceinline__ unsigned tm1_out(const Lane& L) const { return L.tm1_out; }
+    __device__ __forceinline__ int* row(const Lane& L) const { return L.row; }
+
+    template <class C>
+    __device__ __forceinline__ void finish(int req, C& cnt) {
+        cnt.add(C_WALKS);
         if (idle_spins <= 0) return;                 // batched: nothing to publish
         const WalkConst* r = reqs + req;
         unsigned long long* done =
@@ -455,8 +492,8 @@ struct QueueFeed {
     }
 
     // Warp-collective: every lane of the warp calls it.
-    __device__ __forceinline__ bool refill(const GraphDev& g, Lane& L, bool have,
-                                           LaneCounts& cnt) {
+    template <class C>
+    __device__ __forceinline__ bool refill(const GraphDev& g, Lane& L, bool have, C& cnt) {
         const int lane = threadIdx.x & 31;
         while (true) {
             const unsigned need = __ballot_sync(FULL, !have);
@@ -485,22 +522,24 @@ struct QueueFeed {
 // ---------------------------------------------------------------------------
 // The engine
 // ---------------------------------------------------------------------------
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, class Feed>
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
 struct Engine {
     const GraphDev& g;
     Feed& feed;
     unsigned trial_cap;
     int shorter_min;             // undirected: load rec[x] first to pick the shorter list
                                  // when deg_t exceeds this
-    LaneCounts& cnt;
-    int2& ld_cand;               // loads in flight (consumed next iteration)
-    int4& ld_rec;
-    int& ld_probe;
+    Counts<COUNT>& cnt;
+    int4& ld;                    // the load in flight (proposal, record or probe block),
+                                 // consumed next iteration
+    int4& rx;                    // x's record, held while a search runs
 
     // Emit x and move to it.  Returns true while the walk continues.
     __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg, float wmax) {
-        put(L, L.s, x);
-        cnt.c[C_STEPS]++;
+        const int len = feed.len(L);
+        int* const row = feed.row(L);
+        put(L, row, L.s, x, len);
+        cnt.add(C_STEPS);
         L.t = L.v;
         L.off_t = L.off_v;
         L.deg_t = L.deg_v;
@@ -511,16 +550,24 @@ struct Engine {
         L.s++;
         L.k = 0;
         L.flags &= ~F_HAVE_RX;
-        if (L.s >= L.len) {
+        if (L.s >= len) {
             feed.finish(L.req, cnt);
             return false;
         }
         if (deg == 0) {
-            fill_dead(L, L.s);
+            fill_dead(L, row, L.s, len);
             feed.finish(L.req, cnt);
             return false;
         }
         return true;
+    }
+
+    // The aligned 16-byte block of dsts that holds the midpoint of the search
+    // range.  dsts is 16-byte aligned and padded by 4 entries, so the block is
+    // always inside the allocation.
+    __device__ __forceinline__ static const int* probe_block(const Lane& L) {
+        return reinterpret_cast<const int*>(reinterpret_cast<uintptr_t>(L.sb + (L.sn >> 1)) &
+                                            ~uintptr_t(15));
     }
 
     // Actions a lane asks for in one iteration.  The phase logic (divergent,
@@ -533,20 +580,25 @@ struct Engine {
     // cap is spent, steps are drawn by the exact fallback instead.  Returns have.
     __device__ __forceinline__ bool trial(Lane& L) {
         while (L.k >= trial_cap) {
-            cnt.c[C_FALLBACKS]++;
+            cnt.add(C_FALLBACKS);
             double a_ret, a_out;
             feed.alphas(L.req, a_ret, a_out);
-            const int xf = exact_fallback<WEIGHTED>(g, L, a_ret, a_out, trial_cap);
+            const int xf = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
             const NodeRec rf = load_rec(g, xf);
             if (!advance(L, xf, rf.off, rf.deg, rf.wmax)) return false;
         }
-        cnt.c[C_TRIALS]++;
-        const uint4 r = trial_block(L.seed, L.w, L.s, L.k);
+        cnt.add(C_TRIALS);
+        const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
         L.r2 = r.z;
         const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
         const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-        if (WEIGHTED) ld_cand = __ldg(g.pairs + e);
-        else ld_cand = make_int2(__ldg(g.dsts + e), 0);
+        if (WEIGHTED) {
+            const int2 pr = __ldg(g.pairs + e);
+            ld.x = pr.x;
+            ld.y = pr.y;
+        } else {
+            ld.x = __ldg(g.dsts + e);
+        }
         L.phase = PH_CAND;
         return true;
     }
@@ -563,10 +615,10 @@ struct Engine {
         return A_REC;
     }
 
-    __device__ __forceinline__ int search_from(Lane& L, const int* base, int n, int key) {
+    __device__ __forceinline__ int search_from(Lane& L, const int* base, int n, bool key_is_t) {
         L.sb = base;
         L.sn = n;
-        L.skey = key;
+        L.flags = key_is_t ? (L.flags | F_KEY_T) : (L.flags & ~F_KEY_T);
         if (n <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
         L.phase = PH_SEARCH;
         return A_PROBE;
@@ -579,29 +631,29 @@ struct Engine {
             case PH_START:
                 return A_TRIAL;
             case PH_CAND: {
-                const int x = ld_cand.x;
-                const float wx = __int_as_float(ld_cand.y);
+                const int x = ld.x;
+                const float wx = __int_as_float(ld.y);
                 L.x = x;
                 bool accept = false;
                 if (L.t < 0) {
                     accept = WEIGHTED ? weighted_accept(L.r2, L.wmax_v, 0xffffffffu, wx) : true;
                 } else if ((HAS_P || HAS_Q) && x == L.t) {
-                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_ret, wx);
+                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_ret(L), wx);
                 } else if (!HAS_Q) {
-                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_in, wx);
+                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx);
                 } else {
-                    const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_in, wx);
-                    const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, L.tm1_out, wx);
+                    const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx);
+                    const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_out(L), wx);
                     if (ai != ao) {
                         // The class decides: x in N(t)?
-                        cnt.c[C_SEARCHES]++;
+                        cnt.add(C_SEARCHES);
                         L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT)) | (ai ? F_ACC_IN : 0u) |
                                   (ao ? F_ACC_OUT : 0u);
                         if (g.undirected && L.deg_t > shorter_min) {
                             L.phase = PH_RECS;           // x's record first: needed if accepted
                             return A_REC;
                         }
-                        return search_from(L, g.dsts + L.off_t, L.deg_t, x);
+                        return search_from(L, g.dsts + L.off_t, L.deg_t, false);
                     }
                     accept = ai;
                 }
@@ -610,22 +662,38 @@ struct Engine {
             case PH_REC:
                 return A_ADV | A_TRIAL;
             case PH_RECS: {
-                // ld_rec keeps x's record until the decision (no other record
-                // load is issued during a search).
-                const NodeRec rx = decode_rec(ld_rec);
+                // x's record is held in rx until the decision.
+                rx = ld;
+                const NodeRec r = decode_rec(ld);
                 L.flags |= F_HAVE_RX;
                 // x in N(t)  <=>  t in N(x) for symmetric graphs: search the shorter row.
-                if (rx.deg < L.deg_t) return search_from(L, g.dsts + rx.off, rx.deg, L.t);
-                return search_from(L, g.dsts + L.off_t, L.deg_t, L.x);
+                if (r.deg < L.deg_t) return search_from(L, g.dsts + r.off, r.deg, true);
+                return search_from(L, g.dsts + L.off_t, L.deg_t, false);
             }
             case PH_SEARCH:
             default: {
-                const int val = ld_probe;
-                if (val == L.skey) return decided(L, (L.flags & F_ACC_IN) != 0);
-                if (L.sn <= 1) return decided(L, (L.flags & F_ACC_OUT) != 0);
-                const int half = L.sn >> 1;
-                if (val < L.skey) L.sb += half;
-                L.sn -= half;
+                // The probe is the aligned 16-byte block holding the range's
+                // midpoint.  Every block entry inside [sb, sb + sn) narrows the
+                // range; entries outside it (a neighbouring row) are ignored.
+                const int* blk = probe_block(L);
+                const int* lo = L.sb;
+                const int* hi = L.sb + L.sn;
+                const int key = (L.flags & F_KEY_T) ? L.t : L.x;
+                const int v[4] = {ld.x, ld.y, ld.z, ld.w};
+                bool found = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int* p = blk + j;
+                    if (p >= L.sb && p < L.sb + L.sn) {
+                        found |= (v[j] == key);
+                        if (v[j] < key && p + 1 > lo) lo = p + 1;
+                        if (v[j] > key && p < hi) hi = p;
+                    }
+                }
+                if (found) return decided(L, (L.flags & F_ACC_IN) != 0);
+                if (hi <= lo) return decided(L, (L.flags & F_ACC_OUT) != 0);
+                L.sb = lo;
+                L.sn = (int)(hi - lo);
                 return A_PROBE;
             }
         }
@@ -636,35 +704,35 @@ struct Engine {
         int act = consume(L);
         bool have = true;
         if (act & A_ADV) {
-            const NodeRec rx = decode_rec(ld_rec);
-            have = advance(L, L.x, rx.off, rx.deg, rx.wmax);
+            // x's record: the load that just arrived (REC) or the one held
+            // through a search (RECS)
+            const NodeRec r = decode_rec((L.flags & F_HAVE_RX) ? rx : ld);
+            have = advance(L, L.x, r.off, r.deg, r.wmax);
             if (!have) act = A_NONE;
         }
         if (act & A_TRIAL) have = trial(L);
-        if (act & A_REC) ld_rec = __ldg(g.rec + L.x);
+        if (act & A_REC) ld = __ldg(g.rec + L.x);
         if (act & A_PROBE) {
-            cnt.c[C_PROBES]++;
-            ld_probe = __ldg(L.sb + (L.sn > 1 ? (L.sn >> 1) : 0));
+            cnt.add(C_PROBES);
+            ld = __ldg(reinterpret_cast<const int4*>(probe_block(L)));
         }
         return have;
     }
 };
 
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, class Feed>
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
                                           int shorter_min) {
     Lane L;
     L.t = -1;
     L.req = -1;
     L.phase = PH_START;
-    LaneCounts cnt;
-#pragma unroll
-    for (int i = 0; i < C_COUNT; ++i) cnt.c[i] = 0;
-    int2 ld_cand = make_int2(0, 0);
-    int4 ld_rec = make_int4(0, 0, 0, 0);
-    int ld_probe = 0;
-    Engine<WEIGHTED, HAS_P, HAS_Q, Feed> eng{g, feed, trial_cap, shorter_min, cnt,
-                                             ld_cand, ld_rec, ld_probe};
+    L.flags = 0;
+    Counts<COUNT> cnt;
+    cnt.clear();
+    int4 ld = make_int4(0, 0, 0, 0);
+    int4 rx = make_int4(0, 0, 0, 0);
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min, cnt, ld, rx};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);

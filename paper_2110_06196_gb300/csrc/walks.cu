@@ -27,18 +27,19 @@ constexpr int kMinBlocksQueue = 3;
 
 // Per-call walk kernel: the eight specialisations of GRAPE ("Implementation of
 // second-order RWs": p == 1, q == 1, weighted or not) as template arguments.
-template <bool W, bool P, bool Q>
+// COUNT: the instantiation that also keeps the work counters.
+template <bool W, bool P, bool Q, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
 walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min) {
     GridFeed f;
     f.wc = &wc;
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
-    walk_loop<W, P, Q>(g, f, trial_cap, shorter_min);
+    walk_loop<W, P, Q, COUNT>(g, f, trial_cap, shorter_min);
 }
 
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
-template <bool W>
+template <bool W, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksQueue)
 queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* head,
              const unsigned long long* tail, unsigned long long ring, long long idle_spins,
@@ -55,7 +56,7 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true>(g, f, trial_cap, shorter_min);
+    walk_loop<W, true, true, COUNT>(g, f, trial_cap, shorter_min);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint32_t* __restrict__ out) {
@@ -111,19 +112,26 @@ int occupancy_blocks(K kernel, int threads) {
     return nb;
 }
 
-template <bool W, bool P, bool Q>
-cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
-                        cudaStream_t stream) {
+template <bool W, bool P, bool Q, bool C>
+cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
+                          cudaStream_t stream) {
     const int threads = std::min(t.block_threads, kMaxThreads);
     int per_sm = t.blocks_per_sm;
-    if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q>, threads);
+    if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q, C>, threads);
     long long blocks = (wc.num_walks + threads - 1) / threads;
     const long long cap = (long long)g->num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    walk_kernel<W, P, Q><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
+    walk_kernel<W, P, Q, C><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
         g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min);
     return cudaGetLastError();
+}
+
+template <bool W, bool P, bool Q>
+cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
+                        cudaStream_t stream) {
+    return g->counting ? launch_walk_c<W, P, Q, true>(g, t, wc, stream)
+                       : launch_walk_c<W, P, Q, false>(g, t, wc, stream);
 }
 
 cudaError_t dispatch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
@@ -204,8 +212,8 @@ LaunchShape queue_launch_shape(const grape_graph* g, const grape_tuning_t& t, in
     s.threads = std::min(t.block_threads, kMaxThreads);
     int per_sm = t.blocks_per_sm;
     if (per_sm <= 0)
-        per_sm = weighted ? occupancy_blocks(queue_kernel<true>, s.threads)
-                          : occupancy_blocks(queue_kernel<false>, s.threads);
+        per_sm = weighted ? occupancy_blocks(queue_kernel<true, false>, s.threads)
+                          : occupancy_blocks(queue_kernel<false, false>, s.threads);
     s.blocks = g->num_sms * per_sm;
     return s;
 }
@@ -217,14 +225,19 @@ cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
                                 int blocks, cudaStream_t stream) {
     const LaunchShape s = queue_launch_shape(g, t, g->weighted);
     const int nb = blocks > 0 ? blocks : s.blocks;
-    if (g->weighted)
-        queue_kernel<true><<<nb, s.threads, stage_bytes(s.threads), stream>>>(g->dev(), reqs, chunks, head, tail, ring,
-                                                         idle_spins, exit_flag,
-                                                         (unsigned)t.trial_cap, t.shorter_min);
-    else
-        queue_kernel<false><<<nb, s.threads, stage_bytes(s.threads), stream>>>(g->dev(), reqs, chunks, head, tail, ring,
-                                                          idle_spins, exit_flag,
-                                                          (unsigned)t.trial_cap, t.shorter_min);
+    const size_t sh = stage_bytes(s.threads);
+    const unsigned cap = (unsigned)t.trial_cap;
+#define GRAPE_QUEUE_LAUNCH(W, C)                                                                 \
+    queue_kernel<W, C><<<nb, s.threads, sh, stream>>>(g->dev(), reqs, chunks, head, tail, ring, \
+                                                      idle_spins, exit_flag, cap, t.shorter_min)
+    if (g->weighted) {
+        if (g->counting) GRAPE_QUEUE_LAUNCH(true, true);
+        else GRAPE_QUEUE_LAUNCH(true, false);
+    } else {
+        if (g->counting) GRAPE_QUEUE_LAUNCH(false, true);
+        else GRAPE_QUEUE_LAUNCH(false, false);
+    }
+#undef GRAPE_QUEUE_LAUNCH
     return cudaGetLastError();
 }
 
