@@ -133,6 +133,12 @@ typedef struct grape_tuning {
     int32_t block_threads;    /* threads per block for walk kernels (multiple of 32, <= 256) */
     int32_t blocks_per_sm;    /* resident blocks per SM for the grid size; 0 = occupancy maximum */
     int32_t chunk_walks;      /* batched and served queues: walks per queue entry */
+    int32_t probe_words;      /* membership probes read 1 list entry (binary search) or the
+                                 aligned 4-entry 16-byte block around the midpoint */
+    int32_t l2_fetch_bytes;   /* 0: leave the L2 fetch granularity as it is; 32, 64 or 128: set
+                                 it (cudaLimitMaxL2FetchGranularity, a per-context limit) when
+                                 this tuning is applied */
+    int32_t pad;
 } grape_tuning_t;
 
 grape_status_t grape_graph_get_tuning(const grape_graph_t* graph, grape_tuning_t* tuning);

@@ -178,9 +178,6 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     // dsts is padded by four entries so that a search probe, which reads the
     // aligned 16-byte block around a list position, never leaves the allocation.
     const size_t m_alloc = (size_t)num_entries + 4;
-    // Random 32-byte gathers are the whole workload: ask the L2 not to widen a
-    // miss into a 64- or 128-byte DRAM fetch (a per-context limit).
-    if (e == cudaSuccess) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32);
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
     if (e == cudaSuccess && g->weighted) e = cudaMalloc(&g->pairs, sizeof(int2) * m_alloc);
@@ -251,6 +248,8 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.block_threads = 256;
     g->tuning.blocks_per_sm = 0;
     g->tuning.chunk_walks = 64;
+    g->tuning.probe_words = 1;
+    g->tuning.l2_fetch_bytes = 0;
     *out = g;
     return GRAPE_OK;
 }
@@ -284,8 +283,17 @@ grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t)
     if (!g || !t) return GRAPE_ERR_INVALID_ARG;
     if (t->trial_cap < 0 || t->trial_cap > 0xffffffffLL || t->shorter_min < 0 ||
         t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
-        t->blocks_per_sm < 0 || t->chunk_walks < 1)
+        t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->probe_words != 1 && t->probe_words != 4) ||
+        (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&
+         t->l2_fetch_bytes != 128))
         return GRAPE_ERR_INVALID_ARG;
+    if (t->l2_fetch_bytes != 0) {
+        // A per-context limit (released with the context): how far the L2
+        // widens a miss when it fetches from DRAM.
+        if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)t->l2_fetch_bytes) !=
+            cudaSuccess)
+            return GRAPE_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     return GRAPE_OK;

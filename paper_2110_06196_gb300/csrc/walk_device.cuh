@@ -529,6 +529,7 @@ struct Engine {
     unsigned trial_cap;
     int shorter_min;             // undirected: load rec[x] first to pick the shorter list
                                  // when deg_t exceeds this
+    bool block_probe;            // probes read 16-byte blocks (else single entries)
     Counts<COUNT>& cnt;
     int4& ld;                    // the load in flight (proposal, record or probe block),
                                  // consumed next iteration
@@ -568,6 +569,19 @@ struct Engine {
     __device__ __forceinline__ static const int* probe_block(const Lane& L) {
         return reinterpret_cast<const int*>(reinterpret_cast<uintptr_t>(L.sb + (L.sn >> 1)) &
                                             ~uintptr_t(15));
+    }
+
+    // Single-entry probes: plain binary search, probing sb[sn / 2].
+    __device__ __forceinline__ int binary_probe(Lane& L) {
+        const int key = (L.flags & F_KEY_T) ? L.t : L.x;
+        const int val = ld.x;
+        if (val == key) return decided(L, (L.flags & F_ACC_IN) != 0);
+        if (L.sn <= 1) return decided(L, (L.flags & F_ACC_OUT) != 0);
+        const int half = L.sn >> 1;
+        if (val < key) L.sb += half + 1;
+        L.sn = (val < key) ? L.sn - half - 1 : half;
+        if (L.sn <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
+        return A_PROBE;
     }
 
     // Actions a lane asks for in one iteration.  The phase logic (divergent,
@@ -672,6 +686,7 @@ struct Engine {
             }
             case PH_SEARCH:
             default: {
+                if (!block_probe) return binary_probe(L);
                 // The probe is the aligned 16-byte block holding the range's
                 // midpoint.  Every block entry inside [sb, sb + sn) narrows the
                 // range; entries outside it (a neighbouring row) are ignored.
@@ -714,7 +729,8 @@ struct Engine {
         if (act & A_REC) ld = __ldg(g.rec + L.x);
         if (act & A_PROBE) {
             cnt.add(C_PROBES);
-            ld = __ldg(reinterpret_cast<const int4*>(probe_block(L)));
+            if (block_probe) ld = __ldg(reinterpret_cast<const int4*>(probe_block(L)));
+            else ld.x = __ldg(L.sb + (L.sn >> 1));
         }
         return have;
     }
@@ -722,7 +738,7 @@ struct Engine {
 
 template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
-                                          int shorter_min) {
+                                          int shorter_min, int probe_words) {
     Lane L;
     L.t = -1;
     L.req = -1;
@@ -732,7 +748,8 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     cnt.clear();
     int4 ld = make_int4(0, 0, 0, 0);
     int4 rx = make_int4(0, 0, 0, 0);
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min, cnt, ld, rx};
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
+                                                    probe_words >= 4, cnt, ld, rx};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);
