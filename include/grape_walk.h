@@ -226,6 +226,31 @@ grape_status_t grape_walks_batched(const grape_graph_t* graph,
                                    int32_t num_requests, grape_stream_t stream);
 
 /*
+ * grape_walks_batched without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need walks (an allocator of their own owns the memory budget, or
+ * allocation is not allowed at that point of their program).  It writes the
+ * request table, per-request queue bounds and the queue head into one
+ * file-scope device array of fixed size (about 480 KB, held on every GPU that
+ * loads the library until the process exits), then runs the same walks as
+ * grape_walks_batched: each request's rows are byte-identical.
+ *   num_requests must be in [1, 4096]; larger batches return
+ *   GRAPE_ERR_INVALID_ARG before anything is enqueued.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call, on every stream, shares the one array per device.  The queue
+ *   head is cleared on each call; the rest keeps the last call's contents.
+ *   Calls whose work overlaps on the GPU (two streams, or a second call
+ *   before the first finished on another stream) race on it: order them on
+ *   one stream or synchronise between them.
+ *   No cudaMalloc, cudaFree or other allocating routine is called; the table
+ *   is uploaded from the host stack in batches of 32 requests.
+ */
+grape_status_t grape_walks_batched_static(const grape_graph_t* graph,
+                                          const grape_walk_request_t* requests,
+                                          int32_t num_requests, grape_stream_t stream);
+
+/*
  * Autotune the batched path for this graph: times a grid of (chunk_walks,
  * shorter_min) on the given requests with CUDA events, and stores the
  * fastest pair in the graph's tuning (also returned in *best when not NULL).

@@ -91,6 +91,7 @@ SIGNATURES = {
     "grape_batch_plan_launch": (c_i32, [c_vp, c_vp]),
     "grape_batch_plan_destroy": (None, [c_vp]),
     "grape_walks_batched": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
+    "grape_walks_batched_static": (c_i32, [c_vp, c_vp, c_i32, c_vp]),
     "grape_autotune_batched": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     "grape_stream_status": (c_i32, [c_vp, c_vp]),
     "grape_counters_enable": (c_i32, [c_vp, c_i32]),

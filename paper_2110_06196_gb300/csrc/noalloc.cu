@@ -1,0 +1,226 @@
+// noalloc.cu -- batched walks that allocate nothing.
+//
+// grape_walks_batched builds its request table, queue entries and queue head
+// in memory it allocates with cudaMalloc.  Some callers cannot allocate device
+// memory at the moment they want walks: code running under a memory budget
+// enforced by another allocator, code inside a region where allocation is
+// forbidden, or callers on a device whose memory is already fully committed.
+// For them, grape_walks_batched_static keeps the same state in one file-scope
+// device array of fixed size instead.  It takes the queue entries implicitly
+// from a prefix table (entry h belongs to the request whose prefix range holds
+// h), so the array's size depends only on the number of requests.
+//
+// The array is a host-side stand-in in host code: the kernel gets the device
+// address that cudaGetSymbolAddress returns, fetched once per device at set-up.
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+using namespace grape;
+
+namespace {
+
+constexpr int kStaticMaxRequests = 4096;
+
+struct StaticScratch {
+    WalkConst reqs[kStaticMaxRequests];
+    long long chunk_end[kStaticMaxRequests];   // inclusive prefix of per-request entry counts
+    unsigned long long head;                   // next queue entry to take
+};
+
+constexpr size_t kStaticScratchBytes = (sizeof(StaticScratch) + 255) & ~size_t(255);
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_batch_scratch[kStaticScratchBytes];
+
+// Per-device address of g_batch_scratch, filled by the first call on a device.
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Queue entries without a stored entry list: entry h is entry
+// h - chunk_end[r - 1] of the request r whose prefix range holds h.
+struct StaticQueueFeed {
+    const StaticScratch* sc;
+    unsigned long long* head;
+    long long total_chunks;
+    int num_reqs;
+    int chunk_walks;
+    long long cur_lo;
+    int cur_left;
+    int cur_req;
+    bool drained;
+
+    __device__ __forceinline__ unsigned long long seed(const Lane& L) const { return L.seed; }
+    __device__ __forceinline__ int len(const Lane& L) const { return L.len; }
+    __device__ __forceinline__ unsigned tm1_ret(const Lane& L) const { return L.tm1_ret; }
+    __device__ __forceinline__ unsigned tm1_in(const Lane& L) const { return L.tm1_in; }
+    __device__ __forceinline__ unsigned tm1_out(const Lane& L) const { return L.tm1_out; }
+    __device__ __forceinline__ int* row(const Lane& L) const { return L.row; }
+
+    template <class C>
+    __device__ __forceinline__ void finish(int, C& cnt) { cnt.add(C_WALKS); }
+    __device__ __forceinline__ void alphas(int req, double& a_ret, double& a_out) const {
+        a_ret = sc->reqs[req].a_ret;
+        a_out = sc->reqs[req].a_out;
+    }
+
+    __device__ __forceinline__ bool take_chunk(int lane) {
+        long long lo = 0;
+        int cnt = 0, rq = -1, ok = 0;
+        if (lane == 0) {
+            const unsigned long long h = atomicAdd(head, 1ull);
+            if ((long long)h < total_chunks) {
+                // request whose prefix range holds h: first r with chunk_end[r] > h
+                int a = 0, b = num_reqs - 1;
+                while (a < b) {
+                    const int m = (a + b) >> 1;
+                    if (sc->chunk_end[m] > (long long)h) b = m; else a = m + 1;
+                }
+                const long long first = a ? sc->chunk_end[a - 1] : 0;
+                const long long nw = sc->reqs[a].num_walks;
+                lo = ((long long)h - first) * chunk_walks;
+                cnt = (int)((nw - lo) < chunk_walks ? (nw - lo) : chunk_walks);
+                rq = a;
+                ok = 1;
+            }
+        }
+        ok = __shfl_sync(FULL, ok, 0);
+        if (!ok) return false;
+        cur_lo = __shfl_sync(FULL, lo, 0);
+        cur_left = __shfl_sync(FULL, cnt, 0);
+        cur_req = __shfl_sync(FULL, rq, 0);
+        return true;
+    }
+
+    template <class C>
+    __device__ __forceinline__ bool refill(const GraphDev& g, Lane& L, bool have, C& cnt) {
+        const int lane = threadIdx.x & 31;
+        while (true) {
+            const unsigned need = __ballot_sync(FULL, !have);
+            if (need == 0 || drained) break;
+            if (cur_left == 0) {
+                if (!take_chunk(lane)) {
+                    drained = true;
+                    break;
+                }
+            }
+            const int rank = __popc(need & ((1u << lane) - 1u));
+            const int n_need = __popc(need);
+            const int give = n_need < cur_left ? n_need : cur_left;
+            if (!have && rank < give) {
+                have = begin_walk(g, sc->reqs[cur_req], cur_req, cur_lo + rank, L);
+                if (!have) finish(cur_req, cnt);
+            }
+            cur_lo += give;
+            cur_left -= give;
+        }
+        return have;
+    }
+};
+
+template <bool W>
+__global__ void __launch_bounds__(256, 3)
+static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks, int num_reqs,
+                    int chunk_walks, unsigned trial_cap, int shorter_min, int probe_words) {
+    StaticQueueFeed f;
+    f.sc = sc;
+    f.head = const_cast<unsigned long long*>(&sc->head);
+    f.total_chunks = total_chunks;
+    f.num_reqs = num_reqs;
+    f.chunk_walks = chunk_walks;
+    f.cur_lo = 0;
+    f.cur_left = 0;
+    f.cur_req = 0;
+    f.drained = false;
+    walk_loop<W, true, true, false>(g, f, trial_cap, shorter_min, probe_words);
+}
+
+// Device address of g_batch_scratch on the current device (set-up on first use).
+grape_status_t scratch_address(StaticScratch** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GRAPE_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_batch_scratch);
+        if (e != cudaSuccess || !p) return GRAPE_ERR_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<StaticScratch*>(g_scratch_addr[dev]);
+    return GRAPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grape_status_t grape_walks_batched_static(const grape_graph_t* g,
+                                          const grape_walk_request_t* reqs, int32_t n,
+                                          grape_stream_t stream_) {
+    if (!g || !reqs || n < 1) return GRAPE_ERR_INVALID_ARG;
+    if (n > kStaticMaxRequests) return GRAPE_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    grape_tuning_t t;
+    grape_graph_get_tuning(g, &t);
+    const int cw = t.chunk_walks;
+    // Validate every request before touching the shared array.
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        WalkConst wc;
+        const grape_walk_request_t& r = reqs[i];
+        const grape_status_t st = make_walk_const(g, r.starts, r.num_starts, r.walk_len,
+                                                  r.walks_per_node, r.p, r.q, r.seed, r.out, &wc);
+        if (st != GRAPE_OK) return st;
+        total += (wc.num_walks + cw - 1) / cw;
+    }
+    StaticScratch* sc = nullptr;
+    grape_status_t st = scratch_address(&sc);
+    if (st != GRAPE_OK) return st;
+    // Upload in small batches from the stack (no heap allocation): the copy
+    // from pageable memory has consumed the buffer when the call returns.
+    constexpr int kBatch = 32;
+    WalkConst wcs[kBatch];
+    long long ends[kBatch];
+    long long run = 0;
+    for (int i0 = 0; i0 < n; i0 += kBatch) {
+        const int m = (n - i0) < kBatch ? (n - i0) : kBatch;
+        for (int j = 0; j < m; ++j) {
+            const grape_walk_request_t& r = reqs[i0 + j];
+            make_walk_const(g, r.starts, r.num_starts, r.walk_len, r.walks_per_node, r.p, r.q,
+                            r.seed, r.out, &wcs[j]);
+            run += (wcs[j].num_walks + cw - 1) / cw;
+            ends[j] = run;
+        }
+        cudaError_t e = cudaMemcpyAsync(&sc->reqs[i0], wcs, sizeof(WalkConst) * m,
+                                        cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&sc->chunk_end[i0], ends, sizeof(long long) * m,
+                                cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    // The queue head is the only state that must start at zero.
+    cudaError_t e = cudaMemsetAsync(&sc->head, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const LaunchShape s = queue_launch_shape(g, t, g->weighted);
+    int per_sm = 0;
+    if (g->weighted)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_queue_kernel<true>, s.threads,
+                                                      (size_t)s.threads * 32);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_queue_kernel<false>,
+                                                      s.threads, (size_t)s.threads * 32);
+    if (per_sm < 1) per_sm = 1;
+    const int blocks = g->num_sms * per_sm;
+    const size_t sh = (size_t)s.threads * 32;
+    if (g->weighted)
+        static_queue_kernel<true><<<blocks, s.threads, sh, stream>>>(
+            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.probe_words);
+    else
+        static_queue_kernel<false><<<blocks, s.threads, sh, stream>>>(
+            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.probe_words);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"
