@@ -248,7 +248,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.block_threads = 256;
     g->tuning.blocks_per_sm = 0;
     g->tuning.chunk_walks = 64;
-    g->tuning.probe_words = 1;
+    g->tuning.probe_words = 4;
     g->tuning.l2_fetch_bytes = 0;
     *out = g;
     return GRAPE_OK;

@@ -105,7 +105,8 @@ def uniform_pairs(n: int, seed: int, begin: int, count: int, device):
 def first_unique_undirected(pair_fn, n: int, m: int, device, overshoot: float = 1.3):
     """The first m distinct unordered non-loop pairs of a candidate stream, in
     stream order.  Grows the prefix until m are found, so the result does not
-    depend on the initial prefix length."""
+    depend on the initial prefix length.  Keys are sorted in parts of disjoint
+    key ranges so that no single sort exceeds torch's 2^31 - 1 element limit."""
     count = max(int(m * overshoot) + 1024, 16)
     while True:
         src, dst = pair_fn(0, count)
@@ -113,13 +114,21 @@ def first_unique_undirected(pair_fn, n: int, m: int, device, overshoot: float = 
         hi = torch.maximum(src, dst)
         ok = lo != hi
         key = torch.where(ok, lo * n + hi, torch.full_like(lo, -1))
-        del src, dst, lo, hi
-        skey, order = torch.sort(key, stable=True)
-        first = torch.ones_like(skey, dtype=torch.bool)
-        first[1:] = skey[1:] != skey[:-1]
-        first &= skey >= 0
-        pos = torch.sort(order[first]).values
-        del skey, order, first
+        del src, dst, lo, hi, ok
+        parts = 1
+        while count // parts > (1 << 29):
+            parts *= 2
+        bounds = [n * n * j // parts for j in range(parts + 1)]
+        firsts = []
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            idx = torch.nonzero((key >= a) & (key < b)).squeeze(1)
+            skey, order = torch.sort(key[idx], stable=True)
+            first = torch.ones_like(skey, dtype=torch.bool)
+            first[1:] = skey[1:] != skey[:-1]
+            firsts.append(idx[order[first]])
+            del idx, skey, order, first
+        pos = torch.sort(torch.cat(firsts)).values
+        del firsts
         if pos.numel() >= m:
             pos = pos[:m]
             keys = key[pos]
@@ -164,21 +173,40 @@ class CSRGraph:
 
 def symmetric_csr(n: int, u: torch.Tensor, v: torch.Tensor, w: torch.Tensor | None,
                   name: str = "") -> CSRGraph:
-    """CSR holding both directions of every undirected pair, rows sorted."""
-    src = torch.cat([u, v])
-    dst = torch.cat([v, u])
-    ww = None if w is None else torch.cat([w, w])
-    key = src * n + dst
-    key, order = torch.sort(key)
-    dst_sorted = (key % n).to(torch.int32)
-    src_sorted = key // n
-    if ww is not None:
-        ww = ww[order]
-    del order, key
-    counts = torch.bincount(src_sorted, minlength=n)
-    offsets = torch.zeros(n + 1, dtype=torch.int64, device=u.device)
+    """CSR holding both directions of every undirected pair, rows sorted.
+
+    Rows are built in parts of consecutive node ranges, each sorted on its own,
+    so that no single sort exceeds torch's 2^31 - 1 element limit."""
+    dev = u.device
+    counts = torch.bincount(u, minlength=n) + torch.bincount(v, minlength=n)
+    offsets = torch.zeros(n + 1, dtype=torch.int64, device=dev)
     offsets[1:] = torch.cumsum(counts, 0)
-    return CSRGraph(offsets, dst_sorted, ww, n, name)
+    del counts
+    m2 = 2 * u.numel()
+    dsts = torch.empty(m2, dtype=torch.int32, device=dev)
+    ww = None if w is None else torch.empty(m2, dtype=torch.float32, device=dev)
+    parts = 1
+    while m2 // parts > (1 << 29):
+        parts *= 2
+    bounds = [n * j // parts for j in range(parts + 1)]
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        sa = (u >= lo) & (u < hi)
+        sb = (v >= lo) & (v < hi)
+        src = torch.cat([u[sa], v[sb]])
+        dst = torch.cat([v[sa], u[sb]])
+        wp = None if w is None else torch.cat([w[sa], w[sb]])
+        del sa, sb
+        if src.numel() >= (1 << 31) - 1:
+            raise RuntimeError("graph part too large for one sort")
+        key = (src - lo) * n + dst
+        del src
+        key, order = torch.sort(key)
+        a, b = int(offsets[lo]), int(offsets[hi])
+        dsts[a:b] = (key % n).to(torch.int32)
+        if ww is not None:
+            ww[a:b] = wp[order]
+        del key, order, dst, wp
+    return CSRGraph(offsets, dsts, ww, n, name)
 
 
 def pair_weights(seed: int, pos: torch.Tensor) -> torch.Tensor:
