@@ -93,7 +93,10 @@ typedef struct grape_graph grape_graph_t;
  *   offsets, dsts, weights: device pointers laid out as in Conventions.  The
  *       caller keeps ownership; they may be freed once `stream` has reached
  *       this call's work (the copies are enqueued on it).
- *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62].
+ *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62], and below 2^32 for
+ *   weighted graphs.  The graph holds 16 * num_nodes + 20 * num_entries bytes
+ *   (node records, sorted rows, and one 16-byte proposal entry per CSR entry
+ *   that carries the target's degree and row offset).
  *   flags: GRAPE_UNDIRECTED | GRAPE_VALIDATE.  With GRAPE_VALIDATE the call
  *       synchronises `stream` and returns GRAPE_ERR_INVALID_GRAPH for:
  *       non-monotone offsets, wrong first or last offset, ids out of range,

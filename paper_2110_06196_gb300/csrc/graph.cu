@@ -5,9 +5,10 @@
 // CSR with each adjacency list sorted), re-laid out for the walk kernels:
 //   rec[v]   16-byte record {row offset (int64), degree (int32), max row weight (fp32)}
 //            so that one aligned 16-byte load gives everything a step needs about v;
-//   dsts[e]  int32 sorted rows, read by the membership searches;
-//   pairs[e] int2 {dst, weight bits} (weighted graphs), so a weighted proposal
-//            reads its candidate and its weight from one 32-byte sector.
+//   dsts[e]  int32 sorted rows, read by the membership searches (padded by 4);
+//   fat[e]   16-byte proposal entry {x, deg_x, off_x, w_vx}: a proposal reads
+//            its target, the target's row and its weight from one sector, so an
+//            accepted step needs no further gather (edge-inlined records).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -48,8 +49,7 @@ __global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, long l
 __global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
                                   const int32_t* __restrict__ dsts,
                                   const float* __restrict__ weights, long long n, int validate,
-                                  int4* __restrict__ rec, int2* __restrict__ pairs, int* bad,
-                                  int* max_deg) {
+                                  int4* __restrict__ rec, int* bad, int* max_deg) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
@@ -65,7 +65,6 @@ __global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
                 const float w = weights[e];
                 if (validate && !(isfinite(w) && w > 0.0f)) flags |= BAD_WEIGHTS;
                 wmax = fmaxf(wmax, w);
-                pairs[e] = make_int2(x, __float_as_int(w));
             }
         }
 #pragma unroll
@@ -84,9 +83,24 @@ __global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
     }
 }
 
+// Proposal entries: fat[e] = {x, deg_x, off_x lo, off_x hi} or, weighted,
+// {x, deg_x, off_x (32-bit), w_vx bits}.  Ids were checked by build_rows_kernel.
+__global__ void build_fat_kernel(const int32_t* __restrict__ dsts, const float* __restrict__ weights,
+                                 const int4* __restrict__ rec, long long m,
+                                 int4* __restrict__ fat) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int x = dsts[e];
+        const int4 r = rec[x];
+        fat[e] = weights ? make_int4(x, r.z, r.x, __float_as_int(weights[e]))
+                         : make_int4(x, r.z, r.x, r.y);
+    }
+}
+
 // Undirected graphs: every entry v -> x has a reverse entry x -> v with the same weight.
 __global__ void check_symmetry_kernel(const int4* __restrict__ rec, const int32_t* __restrict__ dsts,
-                                      const int2* __restrict__ pairs, long long n, int* bad) {
+                                      const int4* __restrict__ fat, int weighted, long long n,
+                                      int* bad) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
@@ -107,7 +121,7 @@ __global__ void check_symmetry_kernel(const int4* __restrict__ rec, const int32_
             }
             if (lo >= xa + rx.z || dsts[lo] != v) {
                 flags |= BAD_SYMMETRY;
-            } else if (pairs && pairs[lo].y != pairs[e].y) {
+            } else if (weighted && fat[lo].w != fat[e].w) {
                 flags |= BAD_SYMMETRY;
             }
         }
@@ -120,7 +134,7 @@ void free_graph(grape_graph* g) {
     if (!g) return;
     cudaFree(g->rec);
     cudaFree(g->dsts);
-    cudaFree(g->pairs);
+    cudaFree(g->fat);
     cudaFree(g->status);
     cudaFree(g->counters);
     delete g;
@@ -162,6 +176,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     *out = nullptr;
     if (!offsets || num_nodes < 1 || num_nodes > 0x7fffffffLL || num_entries < 0 ||
         num_entries > (1LL << 62) || (num_entries > 0 && !dsts) ||
+        (weights && num_entries >= (1LL << 32)) ||
         (flags & ~(GRAPE_UNDIRECTED | GRAPE_VALIDATE)))
         return GRAPE_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
@@ -180,7 +195,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     const size_t m_alloc = (size_t)num_entries + 4;
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
-    if (e == cudaSuccess && g->weighted) e = cudaMalloc(&g->pairs, sizeof(int2) * m_alloc);
+    if (e == cudaSuccess) e = cudaMalloc(&g->fat, sizeof(int4) * (num_entries > 0 ? (size_t)num_entries : 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * grape::C_COUNT);
     if (e != cudaSuccess) {
@@ -188,7 +203,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
         return grape::cuda_status(e);
     }
     g->device_bytes = (int64_t)(sizeof(int4) * num_nodes + sizeof(int32_t) * m_alloc +
-                                (g->weighted ? sizeof(int2) * m_alloc : 0));
+                                sizeof(int4) * (size_t)num_entries);
     int* scratch = g->status;   // [0] status word, [1] bad flags, [2] max degree
     int host[4] = {0, 0, 0, 0};
     e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
@@ -214,7 +229,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     if (e == cudaSuccess) {
         build_rows_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
             offsets, dsts, weights, num_nodes, (flags & GRAPE_VALIDATE) ? 1 : 0, g->rec,
-            g->pairs, scratch + 1, scratch + 2);
+            scratch + 1, scratch + 2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
@@ -223,10 +238,20 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
         free_graph(g);
         return e != cudaSuccess ? grape::cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
     }
-    // 3. Symmetry (ids are known in range now).
+    // 3. Proposal entries (ids are known in range now).
+    if (num_entries > 0) {
+        build_fat_kernel<<<grid_for(g->num_sms, num_entries, 256), 256, 0, stream>>>(
+            g->dsts, weights, g->rec, num_entries, g->fat);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            free_graph(g);
+            return grape::cuda_status(e);
+        }
+    }
+    // 4. Symmetry.
     if ((flags & GRAPE_VALIDATE) && g->undirected) {
         check_symmetry_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
-            g->rec, g->dsts, g->pairs, num_nodes, scratch + 1);
+            g->rec, g->dsts, g->fat, g->weighted ? 1 : 0, num_nodes, scratch + 1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(host, scratch, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

@@ -19,7 +19,7 @@ struct grape_graph {
     int num_sms = 0;
     int4* rec = nullptr;          // NodeRec[n]
     int32_t* dsts = nullptr;      // [m]
-    int2* pairs = nullptr;        // [m] weighted only
+    int4* fat = nullptr;          // [m] proposal entries (edge-inlined records)
     int* status = nullptr;        // device status word
     unsigned long long* counters = nullptr;  // [6]
     bool counting = false;
@@ -31,7 +31,7 @@ struct grape_graph {
         grape::GraphDev g;
         g.rec = rec;
         g.dsts = dsts;
-        g.pairs = pairs;
+        g.fat = fat;
         g.n = n;
         g.status = status;
         g.counters = counting ? counters : nullptr;

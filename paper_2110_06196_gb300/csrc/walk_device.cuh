@@ -5,19 +5,16 @@
 // (request, walk range) entries), and served (the same queue, fed while the
 // kernel runs).
 //
-// The engine is a per-lane state machine that issues at most ONE dependent
-// global load per lane per loop iteration and consumes it in the next
-// iteration.  A lane deep in a membership search on a hub list therefore does
-// not hold up the other 31 lanes of its warp; they keep drawing proposals and
-// loading records, so every iteration keeps up to 32 independent gathers per
-// warp in flight.  Phases:
-//   CAND    a proposal's (dst[, weight]) arrived: classify and decide, or
-//           start a membership search
-//   REC     the record of an accepted x arrived: emit x, move, start the next step
-//   RECS    the record of x arrived before a search: pick the shorter of N(t)
-//           and N(x) (undirected graphs) and issue the first probe
-//   SEARCH  one probe of a search arrived (the aligned 16-byte block of the
-//           list around the range's midpoint): narrow or finish
+// The engine is a per-lane state machine that issues at most one dependent
+// gather per lane per loop iteration and consumes it in the next iteration.
+// A lane deep in a membership search on a hub list therefore does not hold up
+// the other 31 lanes of its warp.  Proposal entries carry the proposed node's
+// degree and row offset ("edge-inlined records", see GraphDev::fat), so an
+// accepted proposal needs no second gather: a step is (proposals + probes)
+// dependent gathers.  Phases:
+//   CAND    a proposal entry arrived: classify and decide, or start a search
+//   SEARCH  a probe arrived (the aligned 16-byte block of the list around the
+//           range's midpoint, or one entry): narrow or finish
 //
 // Per trial (GRAPE, Methods, eq. alphaRW with the beta/gamma split of eqs. alpha, beta):
 //   Philox4x32-10(key = seed, ctr = (w, s, k)) -> r0..r3
@@ -47,8 +44,11 @@ enum Counter : int { C_STEPS = 0, C_TRIALS, C_SEARCHES, C_PROBES, C_FALLBACKS, C
 
 struct GraphDev {
     const int4* rec;            // [n] NodeRec viewed as int4
-    const int* dsts;            // [m] sorted rows
-    const int2* pairs;          // [m] (dst, weight bits) for weighted graphs, else nullptr
+    const int* dsts;            // [m + 4] sorted rows (membership search, fallback)
+    // [m] proposal entries, one 16-byte word per CSR entry e (row v, target x):
+    //   unweighted: {x, deg_x, off_x lo, off_x hi}
+    //   weighted:   {x, deg_x, off_x (32-bit), w_vx bits}   (needs m < 2^32)
+    const int4* fat;
     long long n;
     int* status;                // device status word (1 = bad start id)
     unsigned long long* counters;  // [C_COUNT] or nullptr
@@ -126,12 +126,12 @@ __device__ __forceinline__ bool lane_search(const int* __restrict__ a, int n, in
 // ---------------------------------------------------------------------------
 // Lane state
 // ---------------------------------------------------------------------------
-enum Phase : int { PH_START = 0, PH_CAND = 1, PH_REC = 2, PH_RECS = 3, PH_SEARCH = 4 };
+enum Phase : int { PH_START = 0, PH_CAND = 1, PH_SEARCH = 2 };
 
 struct Lane {
     long long w;          // walk id (Philox counter words 0-1)
     long long off_v, off_t;
-    int* row;             // this walk's output row
+    int* row;             // this walk's output row (batched / served)
     unsigned long long seed;
     unsigned tm1_ret, tm1_in, tm1_out;
     unsigned k;           // trial index within the step
@@ -141,11 +141,13 @@ struct Lane {
     int deg_v, deg_t;
     float wmax_v;
     int req;              // request index (batched / served), -1 for per-call
-    // the trial in flight
     int phase;
-    unsigned r2;          // acceptance uniform
-    int x;                // proposal
+    unsigned r2;          // acceptance uniform of the proposal in flight
     unsigned flags;       // F_* bits below
+    // the proposal under a membership search
+    int x;
+    int xdeg;
+    long long xoff;
     // membership search over sb[0, sn) for x (or for t, with F_KEY_T)
     const int* sb;
     int sn;
@@ -154,7 +156,7 @@ struct Lane {
 enum : unsigned {
     F_ACC_IN = 1u,        // accept if x is in N(t)
     F_ACC_OUT = 2u,       // accept if x is not in N(t)
-    F_HAVE_RX = 4u,       // the pending record load holds x's record
+    F_WMAX = 4u,          // a load of wmax_v is in flight (weighted graphs)
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
 };
@@ -263,7 +265,7 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
             if (x == L.t) a = a_ret;
             else if (!lane_search(g.dsts + L.off_t, L.deg_t, x)) a = a_out;
         }
-        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.pairs[e].y)) : 1.0;
+        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[e].w)) : 1.0;
         total = __dadd_rn(total, __dmul_rn(a, w));
     }
     const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
@@ -277,7 +279,7 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
             if (x == L.t) a = a_ret;
             else if (!lane_search(g.dsts + L.off_t, L.deg_t, x)) a = a_out;
         }
-        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.pairs[e].y)) : 1.0;
+        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[e].w)) : 1.0;
         run = __dadd_rn(run, __dmul_rn(a, w));
         if (run > u) return x;
     }
@@ -317,6 +319,7 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.s = 1;
     L.k = 0;
     L.phase = PH_START;
+    L.flags &= ~(F_WMAX | F_KEY_T | F_ACC_IN | F_ACC_OUT);
     if (wc.walk_len <= 1) return false;
     if (r.deg == 0) {
         fill_dead(L, L.row, 1, wc.walk_len);
@@ -527,16 +530,16 @@ struct Engine {
     const GraphDev& g;
     Feed& feed;
     unsigned trial_cap;
-    int shorter_min;             // undirected: load rec[x] first to pick the shorter list
-                                 // when deg_t exceeds this
+    int shorter_min;             // undirected: search the shorter of N(t), N(x) when
+                                 // deg_t exceeds this
     bool block_probe;            // probes read 16-byte blocks (else single entries)
     Counts<COUNT>& cnt;
-    int4& ld;                    // the load in flight (proposal, record or probe block),
+    int4& ld;                    // the gather in flight (proposal entry or probe),
                                  // consumed next iteration
-    int4& rx;                    // x's record, held while a search runs
+    float& ld_wmax;              // weighted: wmax of the node just moved to
 
     // Emit x and move to it.  Returns true while the walk continues.
-    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg, float wmax) {
+    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg) {
         const int len = feed.len(L);
         int* const row = feed.row(L);
         put(L, row, L.s, x, len);
@@ -547,10 +550,8 @@ struct Engine {
         L.v = x;
         L.off_v = off;
         L.deg_v = deg;
-        L.wmax_v = wmax;
         L.s++;
         L.k = 0;
-        L.flags &= ~F_HAVE_RX;
         if (L.s >= len) {
             feed.finish(L.req, cnt);
             return false;
@@ -560,6 +561,38 @@ struct Engine {
             feed.finish(L.req, cnt);
             return false;
         }
+        if (WEIGHTED) {
+            // wmax of the new v is needed by the next proposal's decision: it
+            // travels alongside that proposal's gather.
+            ld_wmax = __ldg(reinterpret_cast<const float*>(g.rec + x) + 3);
+            L.flags |= F_WMAX;
+        }
+        return true;
+    }
+
+    // Draw the next proposal of the current step and gather its entry.  While
+    // the trial cap is spent, steps are drawn by the exact fallback instead.
+    // Returns have.
+    __device__ __forceinline__ bool trial(Lane& L) {
+        while (L.k >= trial_cap) {
+            cnt.add(C_FALLBACKS);
+            if (WEIGHTED && (L.flags & F_WMAX)) {
+                L.wmax_v = ld_wmax;
+                L.flags &= ~F_WMAX;
+            }
+            double a_ret, a_out;
+            feed.alphas(L.req, a_ret, a_out);
+            const int xf = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
+            const NodeRec rf = load_rec(g, xf);
+            if (!advance(L, xf, rf.off, rf.deg)) return false;
+        }
+        cnt.add(C_TRIALS);
+        const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
+        L.r2 = r.z;
+        const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+        const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
+        ld = __ldg(g.fat + e);
+        L.phase = PH_CAND;
         return true;
     }
 
@@ -571,65 +604,18 @@ struct Engine {
                                             ~uintptr_t(15));
     }
 
-    // Single-entry probes: plain binary search, probing sb[sn / 2].
-    __device__ __forceinline__ int binary_probe(Lane& L) {
-        const int key = (L.flags & F_KEY_T) ? L.t : L.x;
-        const int val = ld.x;
-        if (val == key) return decided(L, (L.flags & F_ACC_IN) != 0);
-        if (L.sn <= 1) return decided(L, (L.flags & F_ACC_OUT) != 0);
-        const int half = L.sn >> 1;
-        if (val < key) L.sb += half + 1;
-        L.sn = (val < key) ? L.sn - half - 1 : half;
-        if (L.sn <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
-        return A_PROBE;
-    }
-
-    // Actions a lane asks for in one iteration.  The phase logic (divergent,
-    // short) only decides; the work itself (move, Philox + proposal load,
-    // record load, probe load) then runs once per iteration for all lanes that
-    // asked for it, so no warp issues several copies of it.
-    enum : int { A_NONE = 0, A_REC = 1, A_PROBE = 2, A_TRIAL = 4, A_ADV = 8 };
-
-    // Draw the next proposal of the current step and load it.  While the trial
-    // cap is spent, steps are drawn by the exact fallback instead.  Returns have.
-    __device__ __forceinline__ bool trial(Lane& L) {
-        while (L.k >= trial_cap) {
-            cnt.add(C_FALLBACKS);
-            double a_ret, a_out;
-            feed.alphas(L.req, a_ret, a_out);
-            const int xf = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
-            const NodeRec rf = load_rec(g, xf);
-            if (!advance(L, xf, rf.off, rf.deg, rf.wmax)) return false;
-        }
-        cnt.add(C_TRIALS);
-        const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
-        L.r2 = r.z;
-        const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
-        const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-        if (WEIGHTED) {
-            const int2 pr = __ldg(g.pairs + e);
-            ld.x = pr.x;
-            ld.y = pr.y;
-        } else {
-            ld.x = __ldg(g.dsts + e);
-        }
-        L.phase = PH_CAND;
-        return true;
-    }
+    enum : int { A_NONE = 0, A_PROBE = 1, A_TRIAL = 2, A_ADV = 4 };
 
     // Decision of a proposal whose membership outcome is known.
     __device__ __forceinline__ int decided(Lane& L, bool accept) {
         if (!accept) {
             L.k++;
-            L.flags &= ~F_HAVE_RX;
             return A_TRIAL;
         }
-        if (L.flags & F_HAVE_RX) return A_ADV | A_TRIAL;
-        L.phase = PH_REC;
-        return A_REC;
+        return A_ADV | A_TRIAL;
     }
 
-    __device__ __forceinline__ int search_from(Lane& L, const int* base, int n, bool key_is_t) {
+    __device__ __forceinline__ int search(Lane& L, const int* base, int n, bool key_is_t) {
         L.sb = base;
         L.sn = n;
         L.flags = key_is_t ? (L.flags | F_KEY_T) : (L.flags & ~F_KEY_T);
@@ -638,95 +624,89 @@ struct Engine {
         return A_PROBE;
     }
 
-    // Phase logic for a lane that holds a walk: consume last iteration's load
-    // and choose this iteration's actions.
+    // Phase logic for a lane that holds a walk: consume last iteration's gather
+    // and choose this iteration's actions.  The proposal's x, offset and degree
+    // are left in L.x / L.xoff / L.xdeg for an A_ADV.
     __device__ __forceinline__ int consume(Lane& L) {
-        switch (L.phase) {
-            case PH_START:
-                return A_TRIAL;
-            case PH_CAND: {
-                const int x = ld.x;
-                const float wx = __int_as_float(ld.y);
-                L.x = x;
-                bool accept = false;
-                if (L.t < 0) {
-                    accept = WEIGHTED ? weighted_accept(L.r2, L.wmax_v, 0xffffffffu, wx) : true;
-                } else if ((HAS_P || HAS_Q) && x == L.t) {
-                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_ret(L), wx);
-                } else if (!HAS_Q) {
-                    accept = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx);
-                } else {
-                    const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx);
-                    const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_out(L), wx);
-                    if (ai != ao) {
-                        // The class decides: x in N(t)?
-                        cnt.add(C_SEARCHES);
-                        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT)) | (ai ? F_ACC_IN : 0u) |
-                                  (ao ? F_ACC_OUT : 0u);
-                        if (g.undirected && L.deg_t > shorter_min) {
-                            L.phase = PH_RECS;           // x's record first: needed if accepted
-                            return A_REC;
-                        }
-                        return search_from(L, g.dsts + L.off_t, L.deg_t, false);
-                    }
-                    accept = ai;
-                }
-                return decided(L, accept);
+        if (L.phase == PH_START) return A_TRIAL;
+        if (L.phase == PH_CAND) {
+            if (WEIGHTED && (L.flags & F_WMAX)) {
+                L.wmax_v = ld_wmax;
+                L.flags &= ~F_WMAX;
             }
-            case PH_REC:
-                return A_ADV | A_TRIAL;
-            case PH_RECS: {
-                // x's record is held in rx until the decision.
-                rx = ld;
-                const NodeRec r = decode_rec(ld);
-                L.flags |= F_HAVE_RX;
-                // x in N(t)  <=>  t in N(x) for symmetric graphs: search the shorter row.
-                if (r.deg < L.deg_t) return search_from(L, g.dsts + r.off, r.deg, true);
-                return search_from(L, g.dsts + L.off_t, L.deg_t, false);
+            const int x = ld.x;
+            L.x = x;
+            L.xdeg = ld.y;
+            L.xoff = WEIGHTED ? (long long)(unsigned)ld.z
+                              : (long long)(((unsigned long long)(unsigned)ld.w << 32) |
+                                            (unsigned)ld.z);
+            const float wx = WEIGHTED ? __int_as_float(ld.w) : 1.0f;
+            if (L.t < 0) {
+                return decided(L, WEIGHTED ? weighted_accept(L.r2, L.wmax_v, 0xffffffffu, wx) : true);
             }
-            case PH_SEARCH:
-            default: {
-                if (!block_probe) return binary_probe(L);
-                // The probe is the aligned 16-byte block holding the range's
-                // midpoint.  Every block entry inside [sb, sb + sn) narrows the
-                // range; entries outside it (a neighbouring row) are ignored.
-                const int* blk = probe_block(L);
-                const int* lo = L.sb;
-                const int* hi = L.sb + L.sn;
-                const int key = (L.flags & F_KEY_T) ? L.t : L.x;
-                const int v[4] = {ld.x, ld.y, ld.z, ld.w};
-                bool found = false;
+            if ((HAS_P || HAS_Q) && x == L.t)
+                return decided(L, accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_ret(L), wx));
+            if (!HAS_Q)
+                return decided(L, accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx));
+            const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx);
+            const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_out(L), wx);
+            if (ai == ao) return decided(L, ai);
+            // The class decides: is x in N(t)?
+            cnt.add(C_SEARCHES);
+            L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT)) | (ai ? F_ACC_IN : 0u) |
+                      (ao ? F_ACC_OUT : 0u);
+            // x in N(t)  <=>  t in N(x) for symmetric graphs: search the shorter row.
+            if (g.undirected && L.deg_t > shorter_min && L.xdeg < L.deg_t)
+                return search(L, g.dsts + L.xoff, L.xdeg, true);
+            return search(L, g.dsts + L.off_t, L.deg_t, false);
+        }
+        // PH_SEARCH
+        const int key = (L.flags & F_KEY_T) ? L.t : L.x;
+        if (!block_probe) {
+            const int val = ld.x;
+            if (val == key) return decided(L, (L.flags & F_ACC_IN) != 0);
+            if (L.sn <= 1) return decided(L, (L.flags & F_ACC_OUT) != 0);
+            const int half = L.sn >> 1;
+            if (val < key) L.sb += half + 1;
+            L.sn = (val < key) ? L.sn - half - 1 : half;
+            if (L.sn <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
+            return A_PROBE;
+        }
+        // The probe is the aligned 16-byte block holding the range's midpoint.
+        // Every block entry inside [sb, sb + sn) narrows the range; entries
+        // outside it (a neighbouring row) are ignored.
+        const int* blk = probe_block(L);
+        const int* lo = L.sb;
+        const int* hi = L.sb + L.sn;
+        const int v[4] = {ld.x, ld.y, ld.z, ld.w};
+        bool found = false;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int* p = blk + j;
-                    if (p >= L.sb && p < L.sb + L.sn) {
-                        found |= (v[j] == key);
-                        if (v[j] < key && p + 1 > lo) lo = p + 1;
-                        if (v[j] > key && p < hi) hi = p;
-                    }
-                }
-                if (found) return decided(L, (L.flags & F_ACC_IN) != 0);
-                if (hi <= lo) return decided(L, (L.flags & F_ACC_OUT) != 0);
-                L.sb = lo;
-                L.sn = (int)(hi - lo);
-                return A_PROBE;
+        for (int j = 0; j < 4; ++j) {
+            const int* p = blk + j;
+            if (p >= L.sb && p < L.sb + L.sn) {
+                found |= (v[j] == key);
+                if (v[j] < key && p + 1 > lo) lo = p + 1;
+                if (v[j] > key && p < hi) hi = p;
             }
         }
+        if (found) return decided(L, (L.flags & F_ACC_IN) != 0);
+        if (hi <= lo) return decided(L, (L.flags & F_ACC_OUT) != 0);
+        L.sb = lo;
+        L.sn = (int)(hi - lo);
+        return A_PROBE;
     }
 
-    // One iteration for a lane (have == true on entry).  Returns have.
+    // One iteration for a lane (have == true on entry).  Returns have.  The
+    // phase logic only decides; the move, Philox + gather and probe load run
+    // once per iteration for all lanes that asked for them.
     __device__ __forceinline__ bool step(Lane& L) {
         int act = consume(L);
         bool have = true;
         if (act & A_ADV) {
-            // x's record: the load that just arrived (REC) or the one held
-            // through a search (RECS)
-            const NodeRec r = decode_rec((L.flags & F_HAVE_RX) ? rx : ld);
-            have = advance(L, L.x, r.off, r.deg, r.wmax);
+            have = advance(L, L.x, L.xoff, L.xdeg);
             if (!have) act = A_NONE;
         }
         if (act & A_TRIAL) have = trial(L);
-        if (act & A_REC) ld = __ldg(g.rec + L.x);
         if (act & A_PROBE) {
             cnt.add(C_PROBES);
             if (block_probe) ld = __ldg(reinterpret_cast<const int4*>(probe_block(L)));
@@ -747,9 +727,9 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     Counts<COUNT> cnt;
     cnt.clear();
     int4 ld = make_int4(0, 0, 0, 0);
-    int4 rx = make_int4(0, 0, 0, 0);
+    float ld_wmax = 0.0f;
     Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
-                                                    probe_words >= 4, cnt, ld, rx};
+                                                    probe_words >= 4, cnt, ld, ld_wmax};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);
