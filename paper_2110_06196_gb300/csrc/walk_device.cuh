@@ -444,11 +444,15 @@ struct QueueFeed {
     }
 
     // Take one queue entry for the warp (lane 0 decides, then broadcast).
-    // Returns false when the queue is drained (batched) or idle too long (served).
-    __device__ __forceinline__ bool take_chunk(int lane) {
+    // Returns 1 with an entry; 0 when a served queue is empty right now (only
+    // when `wait` is false); -1 when the queue is drained (batched), the server
+    // is shutting down, or a waiting warp stayed idle for idle_spins polls.
+    // Only a warp that holds no walk at all waits: a warp with walks in flight
+    // polls once and carries on, so an empty queue never stalls live walks.
+    __device__ __forceinline__ int take_chunk(int lane, bool wait) {
         long long lo = 0;
         int cnt = 0, rq = -1;
-        int ok = 0;
+        int ok = -1;
         if (lane == 0) {
             long long spins = 0;
             while (true) {
@@ -482,16 +486,20 @@ struct QueueFeed {
                     break;
                 }
                 if (idle_spins <= 0) break;                  // batched: queue drained
+                if (!wait) {                                 // served, walks in flight
+                    ok = 0;
+                    break;
+                }
                 if (++spins > idle_spins) break;             // served: bounded idle wait
                 __nanosleep(1000);
             }
         }
         ok = __shfl_sync(FULL, ok, 0);
-        if (!ok) return false;
+        if (ok <= 0) return ok;
         cur_lo = __shfl_sync(FULL, lo, 0);
         cur_left = __shfl_sync(FULL, cnt, 0);
         cur_req = __shfl_sync(FULL, rq, 0);
-        return true;
+        return 1;
     }
 
     // Warp-collective: every lane of the warp calls it.
@@ -502,7 +510,9 @@ struct QueueFeed {
             const unsigned need = __ballot_sync(FULL, !have);
             if (need == 0 || drained) break;
             if (cur_left == 0) {
-                if (!take_chunk(lane)) {
+                const int got = take_chunk(lane, need == FULL);
+                if (got == 0) break;          // nothing queued yet: live walks go on
+                if (got < 0) {
                     drained = true;
                     break;
                 }
