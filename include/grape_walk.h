@@ -299,7 +299,8 @@ typedef struct grape_server_config {
     int32_t max_inflight;       /* requests admitted at once (ring slots), <= 65536 */
     int32_t chunk_walks;        /* walks per work-queue entry (0 = graph tuning) */
     int64_t max_chunks;         /* capacity of the device work queue, in entries */
-    int64_t idle_exit_us;       /* the resident kernel exits after this long without work */
+    int64_t idle_exit_us;       /* the resident kernel is stopped once the server has had nothing
+                                   in flight for this long (relaunched with the next request) */
     int32_t admit_timeout_ms;   /* submit waits this long for memory/slots, then GRAPE_ERR_BUSY */
     int32_t pad;
 } grape_server_config_t;
@@ -320,8 +321,10 @@ typedef struct grape_server_stats {
  * into queue entries of chunk_walks walks, appended to the queue that a
  * resident kernel is draining.  Work that arrives while other requests run is
  * picked up by the running kernel.  Finished rows are copied to the host on the
- * copy stream while the kernel keeps running.  The resident kernel's waits are
- * bounded (idle_exit_us); it is relaunched when new work arrives.
+ * copy stream while the kernel keeps running.  The server stops the resident
+ * kernel after idle_exit_us without work in flight (all its warps leave
+ * together) and relaunches it with the next request; the kernel's own waits
+ * are bounded (about two seconds of polling) should the host never stop it.
  */
 grape_status_t grape_walk_server_create(const grape_graph_t* graph,
                                         const grape_server_config_t* config,

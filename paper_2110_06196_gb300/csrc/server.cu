@@ -11,10 +11,11 @@
 // rows to the caller's host buffer on a separate copy stream while the kernel
 // keeps working, and frees the arena bytes.
 //
-// Waits are bounded on both sides.  An idle kernel polls the tail for at most
-// `idle_exit_us` and then exits.  The driver relaunches it when work is queued
-// and no kernel is running.  Shutdown raises an exit flag that the kernel reads
-// before taking each entry.
+// Waits are bounded on both sides.  Warps without walks poll the tail; the
+// driver raises an exit flag once nothing has been in flight for
+// `idle_exit_us`, and relaunches the kernel when work is queued and no kernel
+// is running.  Shutdown raises the same flag, which the kernel reads before
+// taking each entry.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -129,6 +130,8 @@ struct grape_server {
     cudaStream_t compute = nullptr, copy = nullptr, ctl = nullptr;
     cudaEvent_t kernel_done = nullptr;
     bool kernel_launched = false;
+    bool exit_raised = false;          // d_exit is set for the running kernel
+    int64_t idle_since = 0;            // when the server last became idle (ns)
 
     // host state
     std::unique_ptr<Arena> arena;
@@ -272,8 +275,22 @@ void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t r
     cv.notify_all();
 }
 
+// The resident kernel's lifetime is decided here, for all of its warps at
+// once.  Its warps never retire for lack of work on their own (a warp that did
+// would leave the next request to the warps that happened to stay); after the
+// server has had nothing in flight for idle_exit_us, the driver raises the
+// exit flag and every warp leaves.  The kernel's own idle wait is only a
+// safety bound of about two seconds of polling for the case that the host
+// never raises the flag.
 void grape_server::run() {
-    const long long idle_spins = std::max<long long>(1, cfg.idle_exit_us);
+    const long long idle_spins = 2000000;   // ~2 s of 1 us sleeps per idle warp
+    auto set_exit = [&](int v) {
+        static thread_local int word;
+        word = v;
+        cudaError_t e = cudaMemcpyAsync(d_exit, &word, sizeof(int), cudaMemcpyHostToDevice, ctl);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
+        return e;
+    };
     while (true) {
         bool busy = false;
         std::vector<std::shared_ptr<Req>> admitted;
@@ -320,12 +337,24 @@ void grape_server::run() {
             std::lock_guard<std::mutex> lk(mu);
             inflight = stats.inflight > 0;
         }
-        if (inflight) {
-            const bool running = kernel_launched && cudaEventQuery(kernel_done) == cudaErrorNotReady;
-            if (!running) {
-                cudaError_t e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl, d_ctl + 1,
-                                                    (unsigned long long)cfg.max_chunks, idle_spins,
-                                                    d_exit, 0, compute);
+        const bool running = kernel_launched && cudaEventQuery(kernel_done) == cudaErrorNotReady;
+        if (!inflight) {
+            if (idle_since == 0) idle_since = now_ns();
+            if (running && !exit_raised &&
+                now_ns() - idle_since > cfg.idle_exit_us * 1000) {
+                if (set_exit(1) == cudaSuccess) exit_raised = true;
+            }
+        } else {
+            idle_since = 0;
+        }
+        if (inflight && !running) {
+            {
+                cudaError_t e = exit_raised ? set_exit(0) : cudaSuccess;
+                if (e == cudaSuccess) exit_raised = false;
+                if (e == cudaSuccess)
+                    e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl, d_ctl + 1,
+                                            (unsigned long long)cfg.max_chunks, idle_spins,
+                                            d_exit, 0, compute);
                 if (e == cudaSuccess) e = cudaEventRecord(kernel_done, compute);
                 std::lock_guard<std::mutex> lk(mu);
                 if (e == cudaSuccess) {
