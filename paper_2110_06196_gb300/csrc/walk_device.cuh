@@ -94,11 +94,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
             k.x += 0x9E3779B9u;
             k.y += 0xBB67AE85u;
         }
-        const unsigned hi0 = __umulhi(0xD2511F53u, c.x);
-        const unsigned lo0 = 0xD2511F53u * c.x;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
-        const unsigned lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        // one 32x32 -> 64 product each (high and low words from one multiply)
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k.x, (unsigned)p1,
+                       (unsigned)(p0 >> 32) ^ c.w ^ k.y, (unsigned)p0);
     }
     return c;
 }
@@ -240,6 +240,33 @@ __device__ __forceinline__ bool weighted_accept(unsigned r2, float wmax, unsigne
     if (d >= 64) return false;
     if (d > 0 && (lhs >> (64 - d)) != 0) return false;
     return (lhs << d) < rhs;
+}
+
+// The same test against two thresholds at once (the in and out classes):
+// r2 * wmax is split and shifted once.
+__device__ __forceinline__ void weighted_accept2(unsigned r2, float wmax, unsigned tm1_a,
+                                                 unsigned tm1_b, float w, bool& acc_a,
+                                                 bool& acc_b) {
+    const unsigned b1 = __float_as_uint(wmax), b2 = __float_as_uint(w);
+    const unsigned e1 = (b1 >> 23) & 0xffu, e2 = (b2 >> 23) & 0xffu;
+    const unsigned long long m1 = (b1 & 0x7fffffu) | (e1 ? 0x800000u : 0u);
+    const unsigned long long m2 = (b2 & 0x7fffffu) | (e2 ? 0x800000u : 0u);
+    const int d = (int)(e1 ? e1 : 1u) - (int)(e2 ? e2 : 1u);
+    const unsigned long long lhs = (unsigned long long)r2 * m1;
+    const unsigned long long rhs_a = ((unsigned long long)tm1_a + 1ull) * m2;
+    const unsigned long long rhs_b = ((unsigned long long)tm1_b + 1ull) * m2;
+    if (lhs == 0) {
+        acc_a = rhs_a != 0;
+        acc_b = rhs_b != 0;
+        return;
+    }
+    if (d >= 64 || (d > 0 && (lhs >> (64 - d)) != 0)) {
+        acc_a = acc_b = false;
+        return;
+    }
+    const unsigned long long l = lhs << d;
+    acc_a = l < rhs_a;
+    acc_b = l < rhs_b;
 }
 
 template <bool WEIGHTED>
@@ -658,8 +685,13 @@ struct Engine {
                 return decided(L, accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_ret(L), wx));
             if (!HAS_Q)
                 return decided(L, accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx));
-            const bool ai = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx);
-            const bool ao = accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_out(L), wx);
+            bool ai, ao;
+            if (WEIGHTED) {
+                weighted_accept2(L.r2, L.wmax_v, feed.tm1_in(L), feed.tm1_out(L), wx, ai, ao);
+            } else {
+                ai = L.r2 <= feed.tm1_in(L);
+                ao = L.r2 <= feed.tm1_out(L);
+            }
             if (ai == ao) return decided(L, ai);
             // The class decides: is x in N(t)?
             cnt.add(C_SEARCHES);
