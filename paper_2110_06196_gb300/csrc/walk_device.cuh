@@ -148,9 +148,11 @@ struct Lane {
     int x;
     int xdeg;
     long long xoff;
-    // membership search over sb[0, sn) for x (or for t, with F_KEY_T)
-    const int* sb;
+    // membership search over dsts[sb, sb + sn) for x (or for t, with F_KEY_T);
+    // sd = (start of the probe block in flight) - sb
+    long long sb;
     int sn;
+    int sd;
 };
 
 enum : unsigned {
@@ -159,7 +161,9 @@ enum : unsigned {
     F_WMAX = 4u,          // a load of wmax_v is in flight (weighted graphs)
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
+    // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
+constexpr int F_PHASE_SHIFT = 8;
 
 // Work counters, kept only by the counting instantiation of the kernels.
 template <bool ON>
@@ -188,28 +192,36 @@ __device__ __forceinline__ int* out_stage() {
 }
 
 __device__ __forceinline__ void put(const Lane& L, int* row, int s, int val, int len) {
-    int* const p = row + s;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    const uintptr_t sec = a & ~uintptr_t(31);
-    const bool inside = (L.flags & F_VEC) && sec >= reinterpret_cast<uintptr_t>(row) &&
-                        sec + 32 <= reinterpret_cast<uintptr_t>(row + len);
-    if (!inside) {
-        *p = val;
+    const int j = (int)(((L.flags >> F_PHASE_SHIFT) + (unsigned)s) & 7u);  // slot in the sector
+    const int sec0 = s - j;                                                 // sector's first entry
+    if (!(L.flags & F_VEC) || sec0 < 0 || sec0 + 8 > len) {
+        row[s] = val;                       // a sector shared with a neighbouring row
         return;
     }
     int* st = out_stage();
-    const int j = (int)((a >> 2) & 7);
     st[j] = val;
     if (j == 7) {
         const int4* s4 = reinterpret_cast<const int4*>(st);
-        int4* g4 = reinterpret_cast<int4*>(sec);
+        int4* g4 = reinterpret_cast<int4*>(row + sec0);
         g4[0] = s4[0];
         g4[1] = s4[1];
     }
 }
 
+// Entries from..len-1 are -1: staged up to the next sector boundary, then whole
+// sectors as two 16-byte stores each, then the ragged end singly.
 __device__ __forceinline__ void fill_dead(const Lane& L, int* row, int from, int len) {
-    for (int j = from; j < len; ++j) put(L, row, j, -1, len);
+    int s = from;
+    while (s < len && (((L.flags >> F_PHASE_SHIFT) + (unsigned)s) & 7u) != 0) put(L, row, s++, -1, len);
+    if (L.flags & F_VEC) {
+        const int4 m1 = make_int4(-1, -1, -1, -1);
+        for (; s + 8 <= len; s += 8) {
+            int4* g4 = reinterpret_cast<int4*>(row + s);
+            g4[0] = m1;
+            g4[1] = m1;
+        }
+    }
+    for (; s < len; ++s) row[s] = -1;
 }
 
 __device__ __forceinline__ NodeRec decode_rec(int4 r) {
@@ -328,7 +340,8 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.tm1_ret = wc.tm1_ret;
     L.tm1_in = wc.tm1_in;
     L.tm1_out = wc.tm1_out;
-    L.flags = wc.out_vec ? F_VEC : 0u;
+    L.flags = (wc.out_vec ? F_VEC : 0u) |
+              ((unsigned)((row * (long long)wc.walk_len) & 7) << F_PHASE_SHIFT);
     const long long i = w % wc.num_starts;
     const long long v0 = wc.starts ? (long long)__ldg(wc.starts + i) : i;
     if (v0 < 0 || v0 >= g.n) {
@@ -569,9 +582,8 @@ struct Engine {
     unsigned trial_cap;
     int shorter_min;             // undirected: search the shorter of N(t), N(x) when
                                  // deg_t exceeds this
-    bool block_probe;            // probes read 16-byte blocks (else single entries)
     Counts<COUNT>& cnt;
-    int4& ld;                    // the gather in flight (proposal entry or probe),
+    int4& ld;                    // the gather in flight (proposal entry or probe block),
                                  // consumed next iteration
     float& ld_wmax;              // weighted: wmax of the node just moved to
 
@@ -607,10 +619,8 @@ struct Engine {
         return true;
     }
 
-    // Draw the next proposal of the current step and gather its entry.  While
-    // the trial cap is spent, steps are drawn by the exact fallback instead.
-    // Returns have.
-    __device__ __forceinline__ bool trial(Lane& L) {
+    // Steps drawn by the exact fallback while the trial cap is spent.  Returns have.
+    __device__ __forceinline__ bool fallback_steps(Lane& L) {
         while (L.k >= trial_cap) {
             cnt.add(C_FALLBACKS);
             if (WEIGHTED && (L.flags & F_WMAX)) {
@@ -623,138 +633,120 @@ struct Engine {
             const NodeRec rf = load_rec(g, xf);
             if (!advance(L, xf, rf.off, rf.deg)) return false;
         }
-        cnt.add(C_TRIALS);
-        const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
-        L.r2 = r.z;
-        const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
-        const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-        ld = __ldg(g.fat + e);
-        L.phase = PH_CAND;
         return true;
     }
 
-    // The aligned 16-byte block of dsts that holds the midpoint of the search
-    // range.  dsts is 16-byte aligned and padded by 4 entries, so the block is
-    // always inside the allocation.
-    __device__ __forceinline__ static const int* probe_block(const Lane& L) {
-        return reinterpret_cast<const int*>(reinterpret_cast<uintptr_t>(L.sb + (L.sn >> 1)) &
-                                            ~uintptr_t(15));
-    }
-
-    enum : int { A_NONE = 0, A_PROBE = 1, A_TRIAL = 2, A_ADV = 4 };
-
-    // Decision of a proposal whose membership outcome is known.
-    __device__ __forceinline__ int decided(Lane& L, bool accept) {
-        if (!accept) {
-            L.k++;
-            return A_TRIAL;
-        }
-        return A_ADV | A_TRIAL;
-    }
-
-    __device__ __forceinline__ int search(Lane& L, const int* base, int n, bool key_is_t) {
-        L.sb = base;
-        L.sn = n;
-        L.flags = key_is_t ? (L.flags | F_KEY_T) : (L.flags & ~F_KEY_T);
-        if (n <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
-        L.phase = PH_SEARCH;
-        return A_PROBE;
-    }
-
-    // Phase logic for a lane that holds a walk: consume last iteration's gather
-    // and choose this iteration's actions.  The proposal's x, offset and degree
-    // are left in L.x / L.xoff / L.xdeg for an A_ADV.
-    __device__ __forceinline__ int consume(Lane& L) {
-        if (L.phase == PH_START) return A_TRIAL;
-        if (L.phase == PH_CAND) {
-            if (WEIGHTED && (L.flags & F_WMAX)) {
-                L.wmax_v = ld_wmax;
-                L.flags &= ~F_WMAX;
-            }
-            const int x = ld.x;
-            L.x = x;
-            L.xdeg = ld.y;
-            L.xoff = WEIGHTED ? (long long)(unsigned)ld.z
-                              : (long long)(((unsigned long long)(unsigned)ld.w << 32) |
-                                            (unsigned)ld.z);
-            const float wx = WEIGHTED ? __int_as_float(ld.w) : 1.0f;
-            if (L.t < 0) {
-                return decided(L, WEIGHTED ? weighted_accept(L.r2, L.wmax_v, 0xffffffffu, wx) : true);
-            }
-            if ((HAS_P || HAS_Q) && x == L.t)
-                return decided(L, accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_ret(L), wx));
-            if (!HAS_Q)
-                return decided(L, accept_test<WEIGHTED>(L.r2, L.wmax_v, feed.tm1_in(L), wx));
-            bool ai, ao;
-            if (WEIGHTED) {
-                weighted_accept2(L.r2, L.wmax_v, feed.tm1_in(L), feed.tm1_out(L), wx, ai, ao);
-            } else {
-                ai = L.r2 <= feed.tm1_in(L);
-                ao = L.r2 <= feed.tm1_out(L);
-            }
-            if (ai == ao) return decided(L, ai);
-            // The class decides: is x in N(t)?
-            cnt.add(C_SEARCHES);
-            L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT)) | (ai ? F_ACC_IN : 0u) |
-                      (ao ? F_ACC_OUT : 0u);
-            // x in N(t)  <=>  t in N(x) for symmetric graphs: search the shorter row.
-            if (g.undirected && L.deg_t > shorter_min && L.xdeg < L.deg_t)
-                return search(L, g.dsts + L.xoff, L.xdeg, true);
-            return search(L, g.dsts + L.off_t, L.deg_t, false);
-        }
-        // PH_SEARCH
-        const int key = (L.flags & F_KEY_T) ? L.t : L.x;
-        if (!block_probe) {
-            const int val = ld.x;
-            if (val == key) return decided(L, (L.flags & F_ACC_IN) != 0);
-            if (L.sn <= 1) return decided(L, (L.flags & F_ACC_OUT) != 0);
-            const int half = L.sn >> 1;
-            if (val < key) L.sb += half + 1;
-            L.sn = (val < key) ? L.sn - half - 1 : half;
-            if (L.sn <= 0) return decided(L, (L.flags & F_ACC_OUT) != 0);
-            return A_PROBE;
-        }
-        // The probe is the aligned 16-byte block holding the range's midpoint.
-        // Every block entry inside [sb, sb + sn) narrows the range; entries
-        // outside it (a neighbouring row) are ignored.
-        const int* blk = probe_block(L);
-        const int* lo = L.sb;
-        const int* hi = L.sb + L.sn;
-        const int v[4] = {ld.x, ld.y, ld.z, ld.w};
-        bool found = false;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int* p = blk + j;
-            if (p >= L.sb && p < L.sb + L.sn) {
-                found |= (v[j] == key);
-                if (v[j] < key && p + 1 > lo) lo = p + 1;
-                if (v[j] > key && p < hi) hi = p;
-            }
-        }
-        if (found) return decided(L, (L.flags & F_ACC_IN) != 0);
-        if (hi <= lo) return decided(L, (L.flags & F_ACC_OUT) != 0);
-        L.sb = lo;
-        L.sn = (int)(hi - lo);
-        return A_PROBE;
-    }
-
-    // One iteration for a lane (have == true on entry).  Returns have.  The
-    // phase logic only decides; the move, Philox + gather and probe load run
-    // once per iteration for all lanes that asked for them.
+    // One iteration for a lane that holds a walk.  Returns have.
+    //
+    // Every lane runs the same straight-line code: the proposal decision and
+    // the probe update are evaluated with selects; Philox is computed
+    // unconditionally (some lane of the warp almost always needs it); the
+    // next gather is one 16-byte load whose address is either the next
+    // proposal's entry or the next probe block.  Only walk ends, dead ends and
+    // the rare fallback branch.
     __device__ __forceinline__ bool step(Lane& L) {
-        int act = consume(L);
+        const int phase = L.phase;
+        if (WEIGHTED && (L.flags & F_WMAX) && phase == PH_CAND) {
+            L.wmax_v = ld_wmax;
+            L.flags &= ~F_WMAX;
+        }
+        // ---- proposal view of the arrived gather (phase CAND) ----
+        const int xc = ld.x;
+        const int degc = ld.y;
+        const long long offc = WEIGHTED
+            ? (long long)(unsigned)ld.z
+            : (long long)(((unsigned long long)(unsigned)ld.w << 32) | (unsigned)ld.z);
+        const float wc = WEIGHTED ? __int_as_float(ld.w) : 1.0f;
+        // thresholds of the two possible classes: (in, out), or one class twice
+        const bool first = L.t < 0;
+        const bool ret = (HAS_P || HAS_Q) && !first && xc == L.t;
+        unsigned ta, tb;
+        if (first) {
+            ta = tb = 0xffffffffu;
+        } else if (ret) {
+            ta = tb = feed.tm1_ret(L);
+        } else {
+            ta = feed.tm1_in(L);
+            tb = HAS_Q ? feed.tm1_out(L) : ta;
+        }
+        bool acc_a, acc_b;
+        if (WEIGHTED) {
+            weighted_accept2(L.r2, L.wmax_v, ta, tb, wc, acc_a, acc_b);
+        } else {
+            acc_a = L.r2 <= ta;
+            acc_b = L.r2 <= tb;
+        }
+        const bool cand = phase == PH_CAND;
+        const bool cand_search = HAS_Q && cand && (acc_a != acc_b);
+        // ---- probe view of the arrived gather (phase SEARCH) ----
+        const bool srch = HAS_Q && phase == PH_SEARCH;
+        const int key = (L.flags & F_KEY_T) ? L.t : L.x;
+        int lo = 0, hi = L.sn;
+        bool found = false;
+        {
+            const int vals[4] = {ld.x, ld.y, ld.z, ld.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int dj = L.sd + j;
+                const bool in = (unsigned)dj < (unsigned)L.sn;
+                found |= in && vals[j] == key;
+                if (in && vals[j] < key) lo = max(lo, dj + 1);
+                if (in && vals[j] > key) hi = min(hi, dj);
+            }
+        }
+        const bool s_done = srch && (found || hi <= lo);
+        // ---- outcome ----
+        const bool decided = (cand && !cand_search) || s_done;
+        const bool accept = cand ? acc_a
+                                 : (found ? (L.flags & F_ACC_IN) != 0 : (L.flags & F_ACC_OUT) != 0);
+        bool probe = false;
+        if (cand_search) {
+            // The class decides: is x in N(t)?  x in N(t) <=> t in N(x) for
+            // symmetric graphs: search the shorter row.
+            cnt.add(C_SEARCHES);
+            L.x = xc;
+            L.xdeg = degc;
+            L.xoff = offc;
+            const bool use_x = g.undirected && L.deg_t > shorter_min && degc < L.deg_t;
+            L.sb = use_x ? offc : L.off_t;
+            L.sn = use_x ? degc : L.deg_t;
+            L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T)) | (acc_a ? F_ACC_IN : 0u) |
+                      (acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
+            probe = true;
+        } else if (srch && !s_done) {
+            L.sb += lo;
+            L.sn = hi - lo;
+            probe = true;
+        }
         bool have = true;
-        if (act & A_ADV) {
-            have = advance(L, L.x, L.xoff, L.xdeg);
-            if (!have) act = A_NONE;
+        if (decided) {
+            if (accept) {
+                have = advance(L, cand ? xc : L.x, cand ? offc : L.xoff, cand ? degc : L.xdeg);
+            } else {
+                L.k++;
+            }
         }
-        if (act & A_TRIAL) have = trial(L);
-        if (act & A_PROBE) {
+        if (!have) return false;
+        if (!probe && L.k >= trial_cap) {
+            if (!fallback_steps(L)) return false;
+        }
+        // ---- the next gather: a probe block or the next proposal's entry ----
+        const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
+        const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+        const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
+        const long long bi = (L.sb + (L.sn >> 1)) & ~3LL;      // aligned block around the midpoint
+        const int4* addr = probe ? reinterpret_cast<const int4*>(g.dsts + bi) : g.fat + e;
+        if (probe) {
+            L.sd = (int)(bi - L.sb);
+            L.phase = PH_SEARCH;
             cnt.add(C_PROBES);
-            if (block_probe) ld = __ldg(reinterpret_cast<const int4*>(probe_block(L)));
-            else ld.x = __ldg(L.sb + (L.sn >> 1));
+        } else {
+            L.r2 = r.z;
+            L.phase = PH_CAND;
+            cnt.add(C_TRIALS);
         }
-        return have;
+        ld = __ldg(addr);
+        return true;
     }
 };
 
@@ -766,12 +758,17 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     L.req = -1;
     L.phase = PH_START;
     L.flags = 0;
+    L.x = 0;
+    L.sb = 0;
+    L.sn = 0;
+    L.sd = 0;
     Counts<COUNT> cnt;
     cnt.clear();
     int4 ld = make_int4(0, 0, 0, 0);
     float ld_wmax = 0.0f;
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
-                                                    probe_words >= 4, cnt, ld, ld_wmax};
+    (void)probe_words;
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min, cnt, ld,
+                                                    ld_wmax};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);
