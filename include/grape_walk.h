@@ -136,8 +136,10 @@ typedef struct grape_tuning {
     int32_t block_threads;    /* threads per block for walk kernels (multiple of 32, <= 256) */
     int32_t blocks_per_sm;    /* resident blocks per SM for the grid size; 0 = occupancy maximum */
     int32_t chunk_walks;      /* batched and served queues: walks per queue entry */
-    int32_t probe_words;      /* membership probes read 1 list entry (binary search) or the
-                                 aligned 4-entry 16-byte block around the midpoint */
+    int32_t interp_search;    /* membership probes read the aligned 16-byte block of the list at
+                                 the position interpolated between the known value bounds (1,
+                                 default), or at the midpoint (0); an interpolated probe that
+                                 does not halve the range is followed by a bisecting one */
     int32_t l2_fetch_bytes;   /* 0: leave the L2 fetch granularity as it is; 32, 64 or 128: set
                                  it (cudaLimitMaxL2FetchGranularity, a per-context limit) when
                                  this tuning is applied */
@@ -255,7 +257,7 @@ grape_status_t grape_walks_batched_static(const grape_graph_t* graph,
 
 /*
  * Autotune the batched path for this graph: times a grid of (chunk_walks,
- * shorter_min) on the given requests with CUDA events, and stores the
+ * shorter_min, interp_search) on the given requests with CUDA events, and stores the
  * fastest pair in the graph's tuning (also returned in *best when not NULL).
  * Writes into the requests' out buffers.  Synchronises `stream`.
  */

@@ -273,7 +273,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.block_threads = 256;
     g->tuning.blocks_per_sm = 0;
     g->tuning.chunk_walks = 64;
-    g->tuning.probe_words = 4;
+    g->tuning.interp_search = 1;
     g->tuning.l2_fetch_bytes = 0;
     *out = g;
     return GRAPE_OK;
@@ -308,7 +308,7 @@ grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t)
     if (!g || !t) return GRAPE_ERR_INVALID_ARG;
     if (t->trial_cap < 0 || t->trial_cap > 0xffffffffLL || t->shorter_min < 0 ||
         t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
-        t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->probe_words != 1 && t->probe_words != 4) ||
+        t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->interp_search != 0 && t->interp_search != 1) ||
         (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&
          t->l2_fetch_bytes != 128))
         return GRAPE_ERR_INVALID_ARG;

@@ -123,7 +123,7 @@ struct StaticQueueFeed {
 template <bool W>
 __global__ void __launch_bounds__(256, 3)
 static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks, int num_reqs,
-                    int chunk_walks, unsigned trial_cap, int shorter_min, int probe_words) {
+                    int chunk_walks, unsigned trial_cap, int shorter_min, int interp_search) {
     StaticQueueFeed f;
     f.sc = sc;
     f.head = const_cast<unsigned long long*>(&sc->head);
@@ -134,7 +134,7 @@ static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks,
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true, false>(g, f, trial_cap, shorter_min, probe_words);
+    walk_loop<W, true, true, false>(g, f, trial_cap, shorter_min, interp_search);
 }
 
 // Device address of g_batch_scratch on the current device (set-up on first use).
@@ -216,10 +216,10 @@ grape_status_t grape_walks_batched_static(const grape_graph_t* g,
     const size_t sh = (size_t)s.threads * 32;
     if (g->weighted)
         static_queue_kernel<true><<<blocks, s.threads, sh, stream>>>(
-            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.probe_words);
+            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
     else
         static_queue_kernel<false><<<blocks, s.threads, sh, stream>>>(
-            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.probe_words);
+            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
     return cuda_status(cudaGetLastError());
 }
 

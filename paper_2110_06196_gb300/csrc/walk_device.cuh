@@ -14,7 +14,7 @@
 // dependent gathers.  Phases:
 //   CAND    a proposal entry arrived: classify and decide, or start a search
 //   SEARCH  a probe arrived (the aligned 16-byte block of the list around the
-//           range's midpoint, or one entry): narrow or finish
+//           interpolated position or the midpoint): narrow or finish
 //
 // Per trial (GRAPE, Methods, eq. alphaRW with the beta/gamma split of eqs. alpha, beta):
 //   Philox4x32-10(key = seed, ctr = (w, s, k)) -> r0..r3
@@ -149,10 +149,12 @@ struct Lane {
     int xdeg;
     long long xoff;
     // membership search over dsts[sb, sb + sn) for x (or for t, with F_KEY_T);
-    // sd = (start of the probe block in flight) - sb
+    // sd = (start of the probe block in flight) - sb; every value before the
+    // range is <= vlo and every value after it >= vhi (vlo < key < vhi)
     long long sb;
     int sn;
     int sd;
+    int vlo, vhi;
 };
 
 enum : unsigned {
@@ -161,6 +163,7 @@ enum : unsigned {
     F_WMAX = 4u,          // a load of wmax_v is in flight (weighted graphs)
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
+    F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
@@ -582,6 +585,7 @@ struct Engine {
     unsigned trial_cap;
     int shorter_min;             // undirected: search the shorter of N(t), N(x) when
                                  // deg_t exceeds this
+    bool interp;                 // place probes by interpolation between the value bounds
     Counts<COUNT>& cnt;
     int4& ld;                    // the gather in flight (proposal entry or probe block),
                                  // consumed next iteration
@@ -682,6 +686,7 @@ struct Engine {
         const bool srch = HAS_Q && phase == PH_SEARCH;
         const int key = (L.flags & F_KEY_T) ? L.t : L.x;
         int lo = 0, hi = L.sn;
+        int vlo = L.vlo, vhi = L.vhi;
         bool found = false;
         {
             const int vals[4] = {ld.x, ld.y, ld.z, ld.w};
@@ -690,8 +695,14 @@ struct Engine {
                 const int dj = L.sd + j;
                 const bool in = (unsigned)dj < (unsigned)L.sn;
                 found |= in && vals[j] == key;
-                if (in && vals[j] < key) lo = max(lo, dj + 1);
-                if (in && vals[j] > key) hi = min(hi, dj);
+                if (in && vals[j] < key && dj + 1 > lo) {
+                    lo = dj + 1;
+                    vlo = vals[j];
+                }
+                if (in && vals[j] > key && dj < hi) {
+                    hi = dj;
+                    vhi = vals[j];
+                }
             }
         }
         const bool s_done = srch && (found || hi <= lo);
@@ -710,12 +721,20 @@ struct Engine {
             const bool use_x = g.undirected && L.deg_t > shorter_min && degc < L.deg_t;
             L.sb = use_x ? offc : L.off_t;
             L.sn = use_x ? degc : L.deg_t;
-            L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T)) | (acc_a ? F_ACC_IN : 0u) |
-                      (acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
+            L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT)) |
+                      (acc_a ? F_ACC_IN : 0u) | (acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
+            L.vlo = -1;                      // node ids lie in [0, n)
+            L.vhi = (int)g.n;
             probe = true;
         } else if (srch && !s_done) {
+            // an interpolated probe that did not halve the range is followed
+            // by a bisecting one, so a search takes O(log deg) probes at worst
+            const bool slow = 2 * (hi - lo) > L.sn;
+            L.flags = ((L.flags & F_BISECT) || !slow) ? (L.flags & ~F_BISECT) : (L.flags | F_BISECT);
             L.sb += lo;
             L.sn = hi - lo;
+            L.vlo = vlo;
+            L.vhi = vhi;
             probe = true;
         }
         bool have = true;
@@ -734,7 +753,16 @@ struct Engine {
         const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
         const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
         const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-        const long long bi = (L.sb + (L.sn >> 1)) & ~3LL;      // aligned block around the midpoint
+        // the aligned block around the probe position: interpolated between the
+        // value bounds (ids in a row are near-uniform after relabelling), or
+        // the midpoint
+        int pos = L.sn >> 1;
+        if (interp && !(L.flags & F_BISECT)) {
+            const int kk = (L.flags & F_KEY_T) ? L.t : L.x;
+            const float f = __fdividef((float)(kk - L.vlo), (float)(L.vhi - L.vlo));
+            pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
+        }
+        const long long bi = (L.sb + pos) & ~3LL;
         const int4* addr = probe ? reinterpret_cast<const int4*>(g.dsts + bi) : g.fat + e;
         if (probe) {
             L.sd = (int)(bi - L.sb);
@@ -752,7 +780,7 @@ struct Engine {
 
 template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
-                                          int shorter_min, int probe_words) {
+                                          int shorter_min, int interp_search) {
     Lane L;
     L.t = -1;
     L.req = -1;
@@ -762,13 +790,14 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     L.sb = 0;
     L.sn = 0;
     L.sd = 0;
+    L.vlo = -1;
+    L.vhi = 0;
     Counts<COUNT> cnt;
     cnt.clear();
     int4 ld = make_int4(0, 0, 0, 0);
     float ld_wmax = 0.0f;
-    (void)probe_words;
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min, cnt, ld,
-                                                    ld_wmax};
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
+                                                    interp_search != 0, cnt, ld, ld_wmax};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);

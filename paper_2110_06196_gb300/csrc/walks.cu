@@ -30,12 +30,12 @@ constexpr int kMinBlocksQueue = 3;
 // COUNT: the instantiation that also keeps the work counters.
 template <bool W, bool P, bool Q, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
-walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min, int probe_words) {
+walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min, int interp_search) {
     GridFeed f;
     f.wc = &wc;
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
-    walk_loop<W, P, Q, COUNT>(g, f, trial_cap, shorter_min, probe_words);
+    walk_loop<W, P, Q, COUNT>(g, f, trial_cap, shorter_min, interp_search);
 }
 
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
@@ -43,7 +43,7 @@ template <bool W, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksQueue)
 queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* head,
              const unsigned long long* tail, unsigned long long ring, long long idle_spins,
-             int* exit_flag, unsigned trial_cap, int shorter_min, int probe_words) {
+             int* exit_flag, unsigned trial_cap, int shorter_min, int interp_search) {
     QueueFeed f;
     f.reqs = reqs;
     f.chunks = chunks;
@@ -56,7 +56,7 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true, COUNT>(g, f, trial_cap, shorter_min, probe_words);
+    walk_loop<W, true, true, COUNT>(g, f, trial_cap, shorter_min, interp_search);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint32_t* __restrict__ out) {
@@ -123,7 +123,7 @@ cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const W
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     walk_kernel<W, P, Q, C><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
-        g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min, t.probe_words);
+        g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
     return cudaGetLastError();
 }
 
@@ -230,7 +230,7 @@ cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
 #define GRAPE_QUEUE_LAUNCH(W, C)                                                                 \
     queue_kernel<W, C><<<nb, s.threads, sh, stream>>>(g->dev(), reqs, chunks, head, tail, ring, \
                                                       idle_spins, exit_flag, cap, t.shorter_min, \
-                                                      t.probe_words)
+                                                      t.interp_search)
     if (g->weighted) {
         if (g->counting) GRAPE_QUEUE_LAUNCH(true, true);
         else GRAPE_QUEUE_LAUNCH(true, false);
@@ -444,7 +444,7 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
     const grape_tuning_t base = tuning_of(g);
     const int chunk_grid[] = {16, 32, 64, 128, 256};
     const int shorter_grid[] = {8, 0x7fffffff};
-    const int probe_grid[] = {1, 4};
+    const int interp_grid[] = {0, 1};
     cudaEvent_t e0, e1;
     GRAPE_CUDA_TRY(cudaEventCreate(&e0));
     GRAPE_CUDA_TRY(cudaEventCreate(&e1));
@@ -452,11 +452,11 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
     grape_tuning_t best_t = base;
     grape_status_t result = GRAPE_OK;
     for (int cw : chunk_grid) {
-        for (int sm : shorter_grid) for (int pw : probe_grid) {
+        for (int sm : shorter_grid) for (int pw : interp_grid) {
             grape_tuning_t t = base;
             t.chunk_walks = cw;
             t.shorter_min = sm;
-            t.probe_words = pw;
+            t.interp_search = pw;
             grape_batch_plan* p = nullptr;
             grape_status_t st = build_plan(g, reqs, n, t, &p);
             if (st != GRAPE_OK) { result = st; break; }
@@ -483,7 +483,7 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
         std::lock_guard<std::mutex> lk(g->mu);
         g->tuning.chunk_walks = best_t.chunk_walks;
         g->tuning.shorter_min = best_t.shorter_min;
-        g->tuning.probe_words = best_t.probe_words;
+        g->tuning.interp_search = best_t.interp_search;
     }
     if (best) *best = best_t;
     return GRAPE_OK;
