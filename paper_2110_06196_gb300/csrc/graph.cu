@@ -275,6 +275,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.chunk_walks = 64;
     g->tuning.interp_search = 1;
     g->tuning.l2_fetch_bytes = 0;
+    g->tuning.speculate = 1;
     *out = g;
     return GRAPE_OK;
 }
@@ -310,7 +311,7 @@ grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t)
         t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
         t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->interp_search != 0 && t->interp_search != 1) ||
         (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&
-         t->l2_fetch_bytes != 128))
+         t->l2_fetch_bytes != 128) || t->speculate < 0 || t->speculate > 2)
         return GRAPE_ERR_INVALID_ARG;
     if (t->l2_fetch_bytes != 0) {
         // A per-context limit (released with the context): how far the L2

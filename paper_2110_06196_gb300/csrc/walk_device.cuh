@@ -68,7 +68,7 @@ struct __align__(16) WalkConst {
     int walk_len;
     double a_ret, a_out;        // 1/p and 1/q for the exact fallback
     int out_vec;                // 1 when out is 32-byte aligned (whole-sector row stores)
-    int pad;
+    int spec;                   // 1 when most proposals are expected to be rejected
     unsigned long long* done;   // served requests: finished-walk counter, else nullptr
     unsigned* done_flag;        // served requests: host-mapped completion flag, else nullptr
 };
@@ -143,6 +143,7 @@ struct Lane {
     int req;              // request index (batched / served), -1 for per-call
     int phase;
     unsigned r2;          // acceptance uniform of the proposal in flight
+    unsigned r2b;         // ... and of the second one (speculation)
     unsigned flags;       // F_* bits below
     // the proposal under a membership search
     int x;
@@ -164,6 +165,8 @@ enum : unsigned {
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
     F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
+    F_PAIR = 64u,         // proposals k (ld) and k + 1 (ld2) are both in flight
+    F_HOLDB = 128u,       // proposal k + 1 (ld2) waits while proposal k is searched
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
@@ -362,7 +365,7 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.s = 1;
     L.k = 0;
     L.phase = PH_START;
-    L.flags &= ~(F_WMAX | F_KEY_T | F_ACC_IN | F_ACC_OUT);
+    L.flags &= ~(F_WMAX | F_KEY_T | F_ACC_IN | F_ACC_OUT | F_PAIR | F_HOLDB | F_BISECT);
     if (wc.walk_len <= 1) return false;
     if (r.deg == 0) {
         fill_dead(L, L.row, 1, wc.walk_len);
@@ -578,7 +581,16 @@ struct QueueFeed {
 // ---------------------------------------------------------------------------
 // The engine
 // ---------------------------------------------------------------------------
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
+// A proposal's entry and decision.
+struct Prop {
+    int x, deg;
+    long long off;
+    bool acc_a, acc_b;    // accept if x in N(t) / if not (equal when the class is known)
+};
+
+// SPEC: proposals k and k + 1 travel together (for walks whose proposals are
+// mostly rejected); the trial order, and so the output, is unchanged.
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, bool SPEC, class Feed>
 struct Engine {
     const GraphDev& g;
     Feed& feed;
@@ -589,7 +601,9 @@ struct Engine {
     Counts<COUNT>& cnt;
     int4& ld;                    // the gather in flight (proposal entry or probe block),
                                  // consumed next iteration
+    int4& ld2;                   // SPEC: the second proposal entry
     float& ld_wmax;              // weighted: wmax of the node just moved to
+    bool spec_on;                // SPEC: this request speculates
 
     // Emit x and move to it.  Returns true while the walk continues.
     __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg) {
@@ -605,6 +619,7 @@ struct Engine {
         L.deg_v = deg;
         L.s++;
         L.k = 0;
+        L.flags &= ~(F_PAIR | F_HOLDB);      // a pending second proposal is void now
         if (L.s >= len) {
             feed.finish(L.req, cnt);
             return false;
@@ -640,30 +655,17 @@ struct Engine {
         return true;
     }
 
-    // One iteration for a lane that holds a walk.  Returns have.
-    //
-    // Every lane runs the same straight-line code: the proposal decision and
-    // the probe update are evaluated with selects; Philox is computed
-    // unconditionally (some lane of the warp almost always needs it); the
-    // next gather is one 16-byte load whose address is either the next
-    // proposal's entry or the next probe block.  Only walk ends, dead ends and
-    // the rare fallback branch.
-    __device__ __forceinline__ bool step(Lane& L) {
-        const int phase = L.phase;
-        if (WEIGHTED && (L.flags & F_WMAX) && phase == PH_CAND) {
-            L.wmax_v = ld_wmax;
-            L.flags &= ~F_WMAX;
-        }
-        // ---- proposal view of the arrived gather (phase CAND) ----
-        const int xc = ld.x;
-        const int degc = ld.y;
-        const long long offc = WEIGHTED
-            ? (long long)(unsigned)ld.z
-            : (long long)(((unsigned long long)(unsigned)ld.w << 32) | (unsigned)ld.z);
-        const float wc = WEIGHTED ? __int_as_float(ld.w) : 1.0f;
+    // Decide a proposal from its entry and acceptance uniform.
+    __device__ __forceinline__ Prop eval(const Lane& L, const int4& en, unsigned r2) {
+        Prop p;
+        p.x = en.x;
+        p.deg = en.y;
+        p.off = WEIGHTED ? (long long)(unsigned)en.z
+                         : (long long)(((unsigned long long)(unsigned)en.w << 32) | (unsigned)en.z);
+        const float w = WEIGHTED ? __int_as_float(en.w) : 1.0f;
         // thresholds of the two possible classes: (in, out), or one class twice
         const bool first = L.t < 0;
-        const bool ret = (HAS_P || HAS_Q) && !first && xc == L.t;
+        const bool ret = (HAS_P || HAS_Q) && !first && p.x == L.t;
         unsigned ta, tb;
         if (first) {
             ta = tb = 0xffffffffu;
@@ -673,15 +675,48 @@ struct Engine {
             ta = feed.tm1_in(L);
             tb = HAS_Q ? feed.tm1_out(L) : ta;
         }
-        bool acc_a, acc_b;
         if (WEIGHTED) {
-            weighted_accept2(L.r2, L.wmax_v, ta, tb, wc, acc_a, acc_b);
+            weighted_accept2(r2, L.wmax_v, ta, tb, w, p.acc_a, p.acc_b);
         } else {
-            acc_a = L.r2 <= ta;
-            acc_b = L.r2 <= tb;
+            p.acc_a = r2 <= ta;
+            p.acc_b = r2 <= tb;
         }
-        const bool cand = phase == PH_CAND;
-        const bool cand_search = HAS_Q && cand && (acc_a != acc_b);
+        return p;
+    }
+
+    // Start the membership search that decides proposal p: is x in N(t)?
+    // x in N(t) <=> t in N(x) for symmetric graphs: search the shorter row.
+    __device__ __forceinline__ void begin_search(Lane& L, const Prop& p) {
+        cnt.add(C_SEARCHES);
+        L.x = p.x;
+        L.xdeg = p.deg;
+        L.xoff = p.off;
+        const bool use_x = g.undirected && L.deg_t > shorter_min && p.deg < L.deg_t;
+        L.sb = use_x ? p.off : L.off_t;
+        L.sn = use_x ? p.deg : L.deg_t;
+        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT)) |
+                  (p.acc_a ? F_ACC_IN : 0u) | (p.acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
+        L.vlo = -1;                      // node ids lie in [0, n)
+        L.vhi = (int)g.n;
+    }
+
+    // One iteration for a lane that holds a walk.  Returns have.
+    //
+    // Every lane runs the same straight-line code: the proposal decisions and
+    // the probe update are evaluated with selects; Philox is computed
+    // unconditionally (some lane of the warp almost always needs it); the
+    // next gather is one 16-byte load (two with speculation) whose address is
+    // either the next proposal's entry or the next probe block.  Only walk
+    // ends, dead ends and the rare fallback branch.
+    __device__ __forceinline__ bool step(Lane& L) {
+        const int phase = L.phase;
+        if (WEIGHTED && (L.flags & F_WMAX) && phase == PH_CAND) {
+            L.wmax_v = ld_wmax;
+            L.flags &= ~F_WMAX;
+        }
+        const Prop A = eval(L, ld, L.r2);
+        Prop B;
+        if (SPEC) B = eval(L, ld2, L.r2b);
         // ---- probe view of the arrived gather (phase SEARCH) ----
         const bool srch = HAS_Q && phase == PH_SEARCH;
         const int key = (L.flags & F_KEY_T) ? L.t : L.x;
@@ -706,44 +741,66 @@ struct Engine {
             }
         }
         const bool s_done = srch && (found || hi <= lo);
-        // ---- outcome ----
-        const bool decided = (cand && !cand_search) || s_done;
-        const bool accept = cand ? acc_a
-                                 : (found ? (L.flags & F_ACC_IN) != 0 : (L.flags & F_ACC_OUT) != 0);
+        // ---- outcome: which proposal moves the walk, or what comes next ----
+        // take: 1 = A (this phase's proposal or the searched one), 2 = B
+        int take = 0;
         bool probe = false;
-        if (cand_search) {
-            // The class decides: is x in N(t)?  x in N(t) <=> t in N(x) for
-            // symmetric graphs: search the shorter row.
-            cnt.add(C_SEARCHES);
-            L.x = xc;
-            L.xdeg = degc;
-            L.xoff = offc;
-            const bool use_x = g.undirected && L.deg_t > shorter_min && degc < L.deg_t;
-            L.sb = use_x ? offc : L.off_t;
-            L.sn = use_x ? degc : L.deg_t;
-            L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT)) |
-                      (acc_a ? F_ACC_IN : 0u) | (acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
-            L.vlo = -1;                      // node ids lie in [0, n)
-            L.vhi = (int)g.n;
-            probe = true;
-        } else if (srch && !s_done) {
-            // an interpolated probe that did not halve the range is followed
-            // by a bisecting one, so a search takes O(log deg) probes at worst
-            const bool slow = 2 * (hi - lo) > L.sn;
-            L.flags = ((L.flags & F_BISECT) || !slow) ? (L.flags & ~F_BISECT) : (L.flags | F_BISECT);
-            L.sb += lo;
-            L.sn = hi - lo;
-            L.vlo = vlo;
-            L.vhi = vhi;
-            probe = true;
-        }
-        bool have = true;
-        if (decided) {
-            if (accept) {
-                have = advance(L, cand ? xc : L.x, cand ? offc : L.xoff, cand ? degc : L.xdeg);
+        bool search_b = false;       // start the search of B
+        bool look_b = false;         // B's decision is the next to consult
+        if (phase == PH_CAND) {
+            if (A.acc_a == A.acc_b || !HAS_Q) {
+                if (A.acc_a) take = 1;
+                else {
+                    L.k++;
+                    look_b = SPEC && (L.flags & F_PAIR);
+                }
             } else {
-                L.k++;
+                begin_search(L, A);
+                probe = true;
+                if (SPEC && (L.flags & F_PAIR)) L.flags |= F_HOLDB;
             }
+        } else if (srch) {
+            if (s_done) {
+                if ((L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0) take = 1;
+                else {
+                    L.k++;
+                    look_b = SPEC && (L.flags & F_HOLDB);
+                }
+            } else {
+                // an interpolated probe that did not halve the range is followed
+                // by a bisecting one, so a search takes O(log deg) probes at worst
+                const bool slow = 2 * (hi - lo) > L.sn;
+                L.flags = ((L.flags & F_BISECT) || !slow) ? (L.flags & ~F_BISECT)
+                                                          : (L.flags | F_BISECT);
+                L.sb += lo;
+                L.sn = hi - lo;
+                L.vlo = vlo;
+                L.vhi = vhi;
+                probe = true;
+            }
+        }
+        if (SPEC && look_b) {
+            // proposal k + 1 has arrived already: decide it in this iteration
+            L.flags &= ~(F_PAIR | F_HOLDB);
+            if (B.acc_a == B.acc_b || !HAS_Q) {
+                if (B.acc_a) take = 2;
+                else L.k++;
+            } else {
+                begin_search(L, B);
+                probe = true;
+                search_b = true;
+            }
+        }
+        (void)search_b;
+        bool have = true;
+        if (take) {
+            // the proposal decided in CAND phase lives in A or B; a searched one in L.x
+            const bool searched = (phase == PH_SEARCH) && take == 1;
+            const int x = searched ? L.x : (take == 1 ? A.x : B.x);
+            const long long off = searched ? L.xoff : (take == 1 ? A.off : B.off);
+            const int deg = searched ? L.xdeg : (take == 1 ? A.deg : B.deg);
+            L.flags &= ~(F_PAIR | F_HOLDB);
+            have = advance(L, x, off, deg);
         }
         if (!have) return false;
         if (!probe && L.k >= trial_cap) {
@@ -774,13 +831,25 @@ struct Engine {
             cnt.add(C_TRIALS);
         }
         ld = __ldg(addr);
+        if (SPEC && !probe && spec_on && L.k + 1 < trial_cap) {
+            // proposal k + 1 rides along
+            const uint4 r1 = trial_block(feed.seed(L), L.w, L.s, L.k + 1);
+            const unsigned long long q64 =
+                (unsigned long long)r1.x | ((unsigned long long)r1.y << 32);
+            const long long e1 =
+                L.off_v + (long long)__umul64hi(q64, (unsigned long long)L.deg_v);
+            L.r2b = r1.z;
+            L.flags |= F_PAIR;
+            cnt.add(C_TRIALS);
+            ld2 = __ldg(g.fat + e1);
+        }
         return true;
     }
 };
 
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, bool SPEC, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
-                                          int shorter_min, int interp_search) {
+                                          int shorter_min, int interp_search, bool spec_on) {
     Lane L;
     L.t = -1;
     L.req = -1;
@@ -794,10 +863,14 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     L.vhi = 0;
     Counts<COUNT> cnt;
     cnt.clear();
+    L.r2 = 0;
+    L.r2b = 0;
     int4 ld = make_int4(0, 0, 0, 0);
+    int4 ld2 = make_int4(0, 0, 0, 0);
     float ld_wmax = 0.0f;
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
-                                                    interp_search != 0, cnt, ld, ld_wmax};
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, SPEC, Feed> eng{g, feed, trial_cap, shorter_min,
+                                                          interp_search != 0, cnt, ld, ld2,
+                                                          ld_wmax, spec_on};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);
