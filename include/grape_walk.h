@@ -143,10 +143,10 @@ typedef struct grape_tuning {
     int32_t l2_fetch_bytes;   /* 0: leave the L2 fetch granularity as it is; 32, 64 or 128: set
                                  it (cudaLimitMaxL2FetchGranularity, a per-context limit) when
                                  this tuning is applied */
-    int32_t speculate;        /* per-call walks: 0 = one proposal in flight per walk; 2 = two
-                                 (proposals k and k + 1 travel together); 1 = two when most
-                                 proposals are expected to be rejected (weighted graphs, or both
-                                 common classes accepting at most half the time; default) */
+    int32_t speculate;        /* per-call walks: 0 = one proposal in flight per walk (default);
+                                 2 = two (proposals k and k + 1 travel together); 1 = two when
+                                 most proposals are expected to be rejected (weighted graphs, or
+                                 both common classes accepting at most half the time) */
 } grape_tuning_t;
 
 grape_status_t grape_graph_get_tuning(const grape_graph_t* graph, grape_tuning_t* tuning);

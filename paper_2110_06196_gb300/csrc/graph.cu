@@ -275,7 +275,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.chunk_walks = 64;
     g->tuning.interp_search = 1;
     g->tuning.l2_fetch_bytes = 0;
-    g->tuning.speculate = 1;
+    g->tuning.speculate = 0;
     *out = g;
     return GRAPE_OK;
 }
