@@ -60,11 +60,14 @@ struct LaunchShape {
 LaunchShape queue_launch_shape(const grape_graph* g, const grape_tuning_t& t, int weighted);
 
 // Launch the queue (batched / served) kernel.
+// ctl[0] is the queue head and ctl[1] the published tail; done / done_flags are
+// the per-request completion counters and host-mapped flags of a served queue
+// (nullptr for batched launches).
 cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
                                 const WalkConst* reqs, const Chunk* chunks,
-                                unsigned long long* head, const unsigned long long* tail,
-                                unsigned long long ring, long long idle_spins, int* exit_flag,
-                                int blocks, cudaStream_t stream);
+                                unsigned long long* ctl, unsigned long long ring,
+                                long long idle_spins, int* exit_flag, unsigned long long* done,
+                                unsigned* done_flags, int blocks, cudaStream_t stream);
 
 inline grape_status_t cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return GRAPE_OK;

@@ -207,8 +207,6 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
                                             q->r.walks_per_node, q->r.p, q->r.q, q->r.seed,
                                             reinterpret_cast<int32_t*>(base), &wc);
         if (st != GRAPE_OK) return st;
-        wc.done = d_done + q->slot;
-        wc.done_flag = d_flags + q->slot;
         h_flags[q->slot] = 0u;
         e = cudaMemcpyAsync(d_reqs + q->slot, &wc, sizeof(wc), cudaMemcpyHostToDevice, ctl);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_done + q->slot, 0, sizeof(unsigned long long), ctl);
@@ -352,9 +350,9 @@ void grape_server::run() {
                 cudaError_t e = exit_raised ? set_exit(0) : cudaSuccess;
                 if (e == cudaSuccess) exit_raised = false;
                 if (e == cudaSuccess)
-                    e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl, d_ctl + 1,
+                    e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl,
                                             (unsigned long long)cfg.max_chunks, idle_spins,
-                                            d_exit, 0, compute);
+                                            d_exit, d_done, d_flags, 0, compute);
                 if (e == cudaSuccess) e = cudaEventRecord(kernel_done, compute);
                 std::lock_guard<std::mutex> lk(mu);
                 if (e == cudaSuccess) {

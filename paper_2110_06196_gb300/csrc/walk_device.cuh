@@ -26,6 +26,7 @@
 // always, so the bytes written do not change.
 #pragma once
 #include <cstdint>
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 
 namespace grape {
@@ -69,8 +70,6 @@ struct __align__(16) WalkConst {
     double a_ret, a_out;        // 1/p and 1/q for the exact fallback
     int out_vec;                // 1 when out is 32-byte aligned (whole-sector row stores)
     int spec;                   // 1 when most proposals are expected to be rejected
-    unsigned long long* done;   // served requests: finished-walk counter, else nullptr
-    unsigned* done_flag;        // served requests: host-mapped completion flag, else nullptr
 };
 static_assert(sizeof(WalkConst) % 16 == 0, "WalkConst is loaded as int4 words");
 
@@ -440,6 +439,15 @@ __device__ __forceinline__ WalkConst load_walkconst(const WalkConst* p) {
     return w;
 }
 
+// Served queues take entries with a plain increment while the published tail
+// is more than this many entries ahead of the head.  Between a warp's read of
+// (head, tail) and its increment (about two L2 round trips) every other warp
+// can take at most a couple of entries, and there are at most 152 x 64 warps,
+// so the increment cannot pass the tail.  Should it ever do so anyway, the
+// warp waits (bounded) for the tail to cover its entry and otherwise raises
+// status bit 2.
+constexpr unsigned long long kQueueMargin = 1ull << 16;
+
 // Batched and served: a warp takes queue entries (one request's walk range) and
 // deals their walks to its lanes as lanes free up.  Served queues advance the
 // head with a compare-and-swap that never passes the published tail, so the
@@ -447,11 +455,13 @@ __device__ __forceinline__ WalkConst load_walkconst(const WalkConst* p) {
 struct QueueFeed {
     const WalkConst* reqs;       // request table (device)
     const Chunk* chunks;         // queue entries (device ring of `ring` entries)
-    unsigned long long* head;    // next entry to take
-    const volatile unsigned long long* tail;  // entries published so far
+    unsigned long long* ctl;     // ctl[0] = next entry to take (head), ctl[1] = entries published (tail)
     unsigned long long ring;     // ring capacity (entries)
     long long idle_spins;        // served: polls of an empty queue before giving up; 0 batched
     int* exit_flag;              // served: set when the kernel should stop
+    unsigned long long* done;    // served: per-request finished-walk counters, else nullptr
+    unsigned* done_flags;        // served: per-request host-mapped completion flags
+    int* status;                 // the graph's device status word
     // warp-uniform state
     long long cur_lo;
     int cur_left;
@@ -469,19 +479,16 @@ struct QueueFeed {
     template <class C>
     __device__ __forceinline__ void finish(int req, C& cnt) {
         cnt.add(C_WALKS);
-        if (idle_spins <= 0) return;                 // batched: nothing to publish
-        const WalkConst* r = reqs + req;
-        unsigned long long* done =
-            reinterpret_cast<unsigned long long*>(__ldcg(reinterpret_cast<const long long*>(&r->done)));
-        if (done == nullptr) return;
-        const long long nw = __ldcg(&r->num_walks);
-        unsigned* flag =
-            reinterpret_cast<unsigned*>(__ldcg(reinterpret_cast<const long long*>(&r->done_flag)));
-        __threadfence();   // this walk's rows are visible before it is counted
-        const unsigned long long prev = atomicAdd(done, 1ull);
+        if (done == nullptr) return;                 // batched: nothing to publish
+        // The count is acquire-release: this walk's rows are visible before it
+        // counts, and the walk that completes the request sees every other
+        // walk's rows before it raises the host-visible flag.
+        const long long nw = __ldcg(&reqs[req].num_walks);
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> c(done[req]);
+        const unsigned long long prev = c.fetch_add(1ull, cuda::memory_order_acq_rel);
         if (prev + 1 == (unsigned long long)nw) {
             __threadfence_system();
-            *(volatile unsigned*)flag = 1u;
+            *(volatile unsigned*)(done_flags + req) = 1u;
         }
     }
     __device__ __forceinline__ void alphas(int req, double& a_ret, double& a_out) const {
@@ -502,24 +509,42 @@ struct QueueFeed {
         if (lane == 0) {
             long long spins = 0;
             while (true) {
-                if (exit_flag && *(volatile int*)exit_flag) break;   // served: shutdown
-                const unsigned long long t = *tail;
                 unsigned long long h;
                 bool got = false;
                 if (idle_spins <= 0) {
                     // Batched: the tail is fixed for the launch, so a plain
                     // increment suffices (the head is reset before each launch).
-                    h = atomicAdd(head, 1ull);
-                    got = h < t;
+                    h = atomicAdd(ctl, 1ull);
+                    got = h < ctl[1];
                 } else {
-                    // Served: never move the head past the published tail.  Every
-                    // failed CAS means another warp took an entry, so the retries
-                    // are bounded by the entries available.
-                    h = *(volatile unsigned long long*)head;
-                    while (h < t) {
-                        const unsigned long long prev = atomicCAS(head, h, h + 1);
-                        if (prev == h) { got = true; break; }
-                        h = prev;
+                    if (*(volatile int*)exit_flag) break;   // served: shutdown
+                    unsigned long long h0, t;                 // head and tail in one load
+                    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+                                 : "=l"(h0), "=l"(t) : "l"(ctl));
+                    if (t > h0 + kQueueMargin) {
+                        h = atomicAdd(ctl, 1ull);
+                        got = true;
+                        if (h >= t) {
+                            long long w = 0;
+                            while (*(volatile unsigned long long*)(ctl + 1) <= h &&
+                                   ++w < idle_spins && !*(volatile int*)exit_flag)
+                                __nanosleep(1000);
+                            if (*(volatile unsigned long long*)(ctl + 1) <= h) {
+                                atomicOr(status, 2);
+                                got = false;
+                                break;
+                            }
+                        }
+                    } else {
+                        // Near the tail: never move the head past it.  Every
+                        // failed CAS means another warp took an entry, so the
+                        // retries are bounded by the entries available.
+                        h = h0;
+                        while (h < t) {
+                            const unsigned long long prev = atomicCAS(ctl, h, h + 1);
+                            if (prev == h) { got = true; break; }
+                            h = prev;
+                        }
                     }
                 }
                 if (got) {

@@ -43,17 +43,20 @@ walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min, int i
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
 template <bool W, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksQueue)
-queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* head,
-             const unsigned long long* tail, unsigned long long ring, long long idle_spins,
-             int* exit_flag, unsigned trial_cap, int shorter_min, int interp_search) {
+queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* ctl,
+             unsigned long long ring, long long idle_spins, int* exit_flag,
+             unsigned long long* done, unsigned* done_flags, unsigned trial_cap, int shorter_min,
+             int interp_search) {
     QueueFeed f;
     f.reqs = reqs;
     f.chunks = chunks;
-    f.head = head;
-    f.tail = tail;
+    f.ctl = ctl;
     f.ring = ring;
     f.idle_spins = idle_spins;
     f.exit_flag = exit_flag;
+    f.done = done;
+    f.done_flags = done_flags;
+    f.status = g.status;
     f.cur_lo = 0;
     f.cur_left = 0;
     f.cur_req = 0;
@@ -203,8 +206,6 @@ grape_status_t make_walk_const(const grape_graph* g, const int32_t* starts, int6
     // common classes (in, out) accept at most half of the time: then a second
     // proposal in flight saves latency.
     wc->spec = (g->weighted || (tm1[1] < 0x80000000u && tm1[2] < 0x80000000u)) ? 1 : 0;
-    wc->done = nullptr;
-    wc->done_flag = nullptr;
     return GRAPE_OK;
 }
 
@@ -230,17 +231,17 @@ LaunchShape queue_launch_shape(const grape_graph* g, const grape_tuning_t& t, in
 
 cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
                                 const WalkConst* reqs, const Chunk* chunks,
-                                unsigned long long* head, const unsigned long long* tail,
-                                unsigned long long ring, long long idle_spins, int* exit_flag,
-                                int blocks, cudaStream_t stream) {
+                                unsigned long long* ctl, unsigned long long ring,
+                                long long idle_spins, int* exit_flag, unsigned long long* done,
+                                unsigned* done_flags, int blocks, cudaStream_t stream) {
     const LaunchShape s = queue_launch_shape(g, t, g->weighted);
     const int nb = blocks > 0 ? blocks : s.blocks;
     const size_t sh = stage_bytes(s.threads);
     const unsigned cap = (unsigned)t.trial_cap;
 #define GRAPE_QUEUE_LAUNCH(W, C)                                                                 \
-    queue_kernel<W, C><<<nb, s.threads, sh, stream>>>(g->dev(), reqs, chunks, head, tail, ring, \
-                                                      idle_spins, exit_flag, cap, t.shorter_min, \
-                                                      t.interp_search)
+    queue_kernel<W, C><<<nb, s.threads, sh, stream>>>(g->dev(), reqs, chunks, ctl, ring,     \
+                                                      idle_spins, exit_flag, done, done_flags, \
+                                                      cap, t.shorter_min, t.interp_search)
     if (g->weighted) {
         if (g->counting) GRAPE_QUEUE_LAUNCH(true, true);
         else GRAPE_QUEUE_LAUNCH(true, false);
@@ -327,8 +328,8 @@ static grape_status_t build_plan(const grape_graph* g, const grape_walk_request_
         cudaError_t e1 = cudaMemsetAsync(p->d_ctl, 0, sizeof(unsigned long long), cap);
         cudaError_t e2 = e1 == cudaSuccess
                              ? launch_queue_kernel(g, t, p->d_reqs, p->d_chunks, p->d_ctl,
-                                                   p->d_ctl + 1, (unsigned long long)chunks.size(),
-                                                   0, nullptr, 0, cap)
+                                                   (unsigned long long)chunks.size(), 0, nullptr,
+                                                   nullptr, nullptr, 0, cap)
                              : e1;
         cudaError_t e3 = cudaStreamEndCapture(cap, &p->graph);
         e = e2 != cudaSuccess ? e2 : e3;
