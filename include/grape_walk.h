@@ -389,13 +389,16 @@ grape_status_t grape_philox4x32_10(const uint32_t* ctr_key, int64_t n, uint32_t*
 
 /*
  * Random 32-byte-sector gather probe (HBM random-access calibration): each of
- * `n_reads` reads fetches one aligned 32-byte sector of `buf` (device,
- * `buf_bytes` long, 32-byte aligned) at a position drawn by Philox from `seed`.
- * The XOR of what was read lands in *sink (device uint32) so nothing is
- * optimised away.
+ * `n_reads` reads (rounded up to whole rounds of the grid) fetches one aligned
+ * 32-byte sector of `buf` (device, `buf_bytes` long, 32-byte aligned) at a
+ * position drawn by Philox from `seed`.  mode picks the load's cache path:
+ * 0 read-only through L1 (ld.global.nc), 1 L2 only (ld.global.cg),
+ * 2 streaming (ld.global.cs).  The XOR of what was read lands in *sink
+ * (device uint32) so nothing is optimised away.
  */
 grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_reads,
-                                  uint64_t seed, uint32_t* sink, grape_stream_t stream);
+                                  uint64_t seed, int32_t mode, uint32_t* sink,
+                                  grape_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -104,7 +104,7 @@ SIGNATURES = {
     "grape_walk_server_stats": (c_i32, [c_vp, c_vp]),
     "grape_walk_server_destroy": (None, [c_vp]),
     "grape_philox4x32_10": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
-    "grape_sector_probe": (c_i32, [c_vp, c_i64, c_i64, c_u64, c_vp, c_vp]),
+    "grape_sector_probe": (c_i32, [c_vp, c_i64, c_i64, c_u64, c_i32, c_vp, c_vp]),
 }
 
 _lock = threading.Lock()

@@ -77,6 +77,9 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint
 }
 
 // Random-sector gather probe: 8 independent sector reads in flight per thread.
+// mode selects the load's cache path: 0 ld.global.nc (read-only path through
+// L1), 1 ld.global.cg (L2 only), 2 ld.global.cs (streaming).
+template <int MODE>
 __global__ void __launch_bounds__(256)
 sector_probe_kernel(const int4* __restrict__ buf, unsigned long long nsec, long long reads_per_thread,
                     unsigned long long seed, uint32_t* sink) {
@@ -94,7 +97,10 @@ sector_probe_kernel(const int4* __restrict__ buf, unsigned long long nsec, long 
         }
         int4 v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcs(buf + 2 * idx[u]);
+        for (int u = 0; u < 8; ++u) {
+            const int4* p = buf + 2 * idx[u];
+            v[u] = MODE == 0 ? __ldg(p) : (MODE == 1 ? __ldcg(p) : __ldcs(p));
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc ^= (unsigned)(v[u].x ^ v[u].w);
     }
@@ -510,8 +516,9 @@ grape_status_t grape_philox4x32_10(const uint32_t* ctr_key, int64_t n, uint32_t*
 }
 
 grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_reads,
-                                  uint64_t seed, uint32_t* sink, grape_stream_t stream) {
-    if (!buf || !sink || buf_bytes < 32 || n_reads < 1 ||
+                                  uint64_t seed, int32_t mode, uint32_t* sink,
+                                  grape_stream_t stream) {
+    if (!buf || !sink || buf_bytes < 32 || n_reads < 1 || mode < 0 || mode > 2 ||
         (reinterpret_cast<uintptr_t>(buf) & 31u))
         return GRAPE_ERR_INVALID_ARG;
     int dev = 0, sms = 0;
@@ -523,8 +530,11 @@ grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_
     long long per_thread = (n_reads + total_threads - 1) / total_threads;
     per_thread = ((per_thread + 7) / 8) * 8;
     const unsigned long long nsec = (unsigned long long)(buf_bytes / 32);
-    sector_probe_kernel<<<(unsigned)blocks, threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        reinterpret_cast<const int4*>(buf), nsec, per_thread, seed, sink);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int4* b4 = reinterpret_cast<const int4*>(buf);
+    if (mode == 0) sector_probe_kernel<0><<<(unsigned)blocks, threads, 0, st>>>(b4, nsec, per_thread, seed, sink);
+    else if (mode == 1) sector_probe_kernel<1><<<(unsigned)blocks, threads, 0, st>>>(b4, nsec, per_thread, seed, sink);
+    else sector_probe_kernel<2><<<(unsigned)blocks, threads, 0, st>>>(b4, nsec, per_thread, seed, sink);
     return grape::cuda_status(cudaGetLastError());
 }
 

@@ -312,12 +312,13 @@ def philox4x32_10(ctr_key: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
-def sector_probe(buf: torch.Tensor, n_reads: int, seed: int, stream=None) -> int:
-    """Random 32-byte-sector gathers over `buf`; returns the read count issued."""
+def sector_probe(buf: torch.Tensor, n_reads: int, seed: int, mode: int = 0, stream=None) -> int:
+    """Random 32-byte-sector gathers over `buf` (mode: 0 ld.global.nc, 1 .cg,
+    2 .cs); returns the read count issued."""
     lib = _lib.load()
     sink = torch.zeros(1, dtype=torch.int32, device=buf.device)
     check(lib.grape_sector_probe(_ptr(buf), buf.numel() * buf.element_size(), int(n_reads),
-                                 int(seed), _ptr(sink), _stream_ptr(stream)))
+                                 int(seed), int(mode), _ptr(sink), _stream_ptr(stream)))
     props = torch.cuda.get_device_properties(buf.device)
     threads = props.multi_processor_count * 8 * 256
     per = -(-int(n_reads) // threads)

@@ -100,7 +100,7 @@ def test_argument_errors_return_before_cuda(lib):
     assert lib.grape_graph_info(None, None) == INVALID
     assert lib.grape_walk_server_create(None, None, ctypes.byref(h)) == INVALID
     assert lib.grape_philox4x32_10(None, -1, None, None) == INVALID
-    assert lib.grape_sector_probe(None, 0, 0, 0, None, None) == INVALID
+    assert lib.grape_sector_probe(None, 0, 0, 0, 0, None, None) == INVALID
     lib.grape_graph_destroy(None)
     lib.grape_walk_server_destroy(None)
     lib.grape_batch_plan_destroy(None)
