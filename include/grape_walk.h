@@ -93,10 +93,11 @@ typedef struct grape_graph grape_graph_t;
  *   offsets, dsts, weights: device pointers laid out as in Conventions.  The
  *       caller keeps ownership; they may be freed once `stream` has reached
  *       this call's work (the copies are enqueued on it).
- *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62], and below 2^32 for
- *   weighted graphs.  The graph holds 16 * num_nodes + 20 * num_entries bytes
- *   (node records, sorted rows, and one 16-byte proposal entry per CSR entry
- *   that carries the target's degree and row offset).
+ *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62].  The graph holds
+ *   16 * num_nodes + 20 * num_entries bytes (36 for weighted graphs): node
+ *   records, sorted rows, and per CSR entry one proposal entry of 16 (32)
+ *   bytes that carries the target's degree and row offset (and the weight
+ *   and the target's largest row weight).
  *   flags: GRAPE_UNDIRECTED | GRAPE_VALIDATE.  With GRAPE_VALIDATE the call
  *       synchronises `stream` and returns GRAPE_ERR_INVALID_GRAPH for:
  *       non-monotone offsets, wrong first or last offset, ids out of range,
@@ -136,17 +137,14 @@ typedef struct grape_tuning {
     int32_t block_threads;    /* threads per block for walk kernels (multiple of 32, <= 256) */
     int32_t blocks_per_sm;    /* resident blocks per SM for the grid size; 0 = occupancy maximum */
     int32_t chunk_walks;      /* batched and served queues: walks per queue entry */
-    int32_t interp_search;    /* membership probes read the aligned 16-byte block of the list at
+    int32_t interp_search;    /* membership probes read the aligned 32-byte sector of the list at
                                  the position interpolated between the known value bounds (1,
                                  default), or at the midpoint (0); an interpolated probe that
                                  does not halve the range is followed by a bisecting one */
     int32_t l2_fetch_bytes;   /* 0: leave the L2 fetch granularity as it is; 32, 64 or 128: set
                                  it (cudaLimitMaxL2FetchGranularity, a per-context limit) when
                                  this tuning is applied */
-    int32_t speculate;        /* per-call walks: 0 = one proposal in flight per walk (default);
-                                 2 = two (proposals k and k + 1 travel together); 1 = two when
-                                 most proposals are expected to be rejected (weighted graphs, or
-                                 both common classes accepting at most half the time) */
+    int32_t pad;
 } grape_tuning_t;
 
 grape_status_t grape_graph_get_tuning(const grape_graph_t* graph, grape_tuning_t* tuning);

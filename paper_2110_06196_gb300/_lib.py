@@ -39,7 +39,7 @@ class GraphInfo(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("trial_cap", c_i64), ("shorter_min", c_i32), ("block_threads", c_i32),
                 ("blocks_per_sm", c_i32), ("chunk_walks", c_i32), ("interp_search", c_i32),
-                ("l2_fetch_bytes", c_i32), ("speculate", c_i32)]
+                ("l2_fetch_bytes", c_i32), ("pad", c_i32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}

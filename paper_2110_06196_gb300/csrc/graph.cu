@@ -5,10 +5,13 @@
 // CSR with each adjacency list sorted), re-laid out for the walk kernels:
 //   rec[v]   16-byte record {row offset (int64), degree (int32), max row weight (fp32)}
 //            so that one aligned 16-byte load gives everything a step needs about v;
-//   dsts[e]  int32 sorted rows, read by the membership searches (padded by 4);
-//   fat[e]   16-byte proposal entry {x, deg_x, off_x, w_vx}: a proposal reads
-//            its target, the target's row and its weight from one sector, so an
-//            accepted step needs no further gather (edge-inlined records).
+//   dsts[e]  int32 sorted rows, read by the membership searches (padded by 8);
+//   fat      proposal entries, one sector's worth per CSR entry: {x, deg_x,
+//            off_x} (16 bytes), and for weighted graphs also {w_vx, wmax_x} in
+//            the second half of a 32-byte entry.  A proposal reads its target,
+//            the target's row, the weight and the target's row maximum from one
+//            sector, so an accepted step needs no further gather
+//            (edge-inlined records).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -84,7 +87,8 @@ __global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
 }
 
 // Proposal entries: fat[e] = {x, deg_x, off_x lo, off_x hi} or, weighted,
-// {x, deg_x, off_x (32-bit), w_vx bits}.  Ids were checked by build_rows_kernel.
+// fat[2e] = the same and fat[2e + 1] = {w_vx bits, wmax_x bits, 0, 0}.  Ids
+// were checked by build_rows_kernel.
 __global__ void build_fat_kernel(const int32_t* __restrict__ dsts, const float* __restrict__ weights,
                                  const int4* __restrict__ rec, long long m,
                                  int4* __restrict__ fat) {
@@ -92,8 +96,12 @@ __global__ void build_fat_kernel(const int32_t* __restrict__ dsts, const float* 
          e += (long long)gridDim.x * blockDim.x) {
         const int x = dsts[e];
         const int4 r = rec[x];
-        fat[e] = weights ? make_int4(x, r.z, r.x, __float_as_int(weights[e]))
-                         : make_int4(x, r.z, r.x, r.y);
+        if (weights) {
+            fat[2 * e] = make_int4(x, r.z, r.x, r.y);
+            fat[2 * e + 1] = make_int4(__float_as_int(weights[e]), r.w, 0, 0);
+        } else {
+            fat[e] = make_int4(x, r.z, r.x, r.y);
+        }
     }
 }
 
@@ -121,7 +129,7 @@ __global__ void check_symmetry_kernel(const int4* __restrict__ rec, const int32_
             }
             if (lo >= xa + rx.z || dsts[lo] != v) {
                 flags |= BAD_SYMMETRY;
-            } else if (weighted && fat[lo].w != fat[e].w) {
+            } else if (weighted && fat[2 * lo + 1].x != fat[2 * e + 1].x) {
                 flags |= BAD_SYMMETRY;
             }
         }
@@ -176,7 +184,6 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     *out = nullptr;
     if (!offsets || num_nodes < 1 || num_nodes > 0x7fffffffLL || num_entries < 0 ||
         num_entries > (1LL << 62) || (num_entries > 0 && !dsts) ||
-        (weights && num_entries >= (1LL << 32)) ||
         (flags & ~(GRAPE_UNDIRECTED | GRAPE_VALIDATE)))
         return GRAPE_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
@@ -192,10 +199,11 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
         e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     // dsts is padded by four entries so that a search probe, which reads the
     // aligned 16-byte block around a list position, never leaves the allocation.
-    const size_t m_alloc = (size_t)num_entries + 4;
+    const size_t m_alloc = (size_t)num_entries + 8;
+    const size_t fat_words = (num_entries > 0 ? (size_t)num_entries : 1) * (weights ? 2 : 1);
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
-    if (e == cudaSuccess) e = cudaMalloc(&g->fat, sizeof(int4) * (num_entries > 0 ? (size_t)num_entries : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->fat, sizeof(int4) * fat_words);
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * grape::C_COUNT);
     if (e != cudaSuccess) {
@@ -203,7 +211,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
         return grape::cuda_status(e);
     }
     g->device_bytes = (int64_t)(sizeof(int4) * num_nodes + sizeof(int32_t) * m_alloc +
-                                sizeof(int4) * (size_t)num_entries);
+                                sizeof(int4) * fat_words);
     int* scratch = g->status;   // [0] status word, [1] bad flags, [2] max degree
     int host[4] = {0, 0, 0, 0};
     e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
@@ -226,6 +234,8 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     if (num_entries > 0)
         e = cudaMemcpyAsync(g->dsts, dsts, sizeof(int32_t) * (size_t)num_entries,
                             cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(g->dsts + num_entries, 0, sizeof(int32_t) * 8, stream);   // padding
     if (e == cudaSuccess) {
         build_rows_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
             offsets, dsts, weights, num_nodes, (flags & GRAPE_VALIDATE) ? 1 : 0, g->rec,
@@ -275,7 +285,6 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.chunk_walks = 64;
     g->tuning.interp_search = 1;
     g->tuning.l2_fetch_bytes = 0;
-    g->tuning.speculate = 0;
     *out = g;
     return GRAPE_OK;
 }
@@ -311,7 +320,7 @@ grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t)
         t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
         t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->interp_search != 0 && t->interp_search != 1) ||
         (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&
-         t->l2_fetch_bytes != 128) || t->speculate < 0 || t->speculate > 2)
+         t->l2_fetch_bytes != 128))
         return GRAPE_ERR_INVALID_ARG;
     if (t->l2_fetch_bytes != 0) {
         // A per-context limit (released with the context): how far the L2

@@ -134,7 +134,7 @@ static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks,
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true, false, false>(g, f, trial_cap, shorter_min, interp_search, false);
+    walk_loop<W, true, true, false>(g, f, trial_cap, shorter_min, interp_search);
 }
 
 // Device address of g_batch_scratch on the current device (set-up on first use).

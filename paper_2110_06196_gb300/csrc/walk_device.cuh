@@ -6,14 +6,15 @@
 // kernel runs).
 //
 // The engine is a per-lane state machine that issues at most one dependent
-// gather per lane per loop iteration and consumes it in the next iteration.
+// gather per lane per loop iteration (one 32-byte sector at most) and
+// consumes it in the next iteration.
 // A lane deep in a membership search on a hub list therefore does not hold up
 // the other 31 lanes of its warp.  Proposal entries carry the proposed node's
 // degree and row offset ("edge-inlined records", see GraphDev::fat), so an
 // accepted proposal needs no second gather: a step is (proposals + probes)
 // dependent gathers.  Phases:
 //   CAND    a proposal entry arrived: classify and decide, or start a search
-//   SEARCH  a probe arrived (the aligned 16-byte block of the list around the
+//   SEARCH  a probe arrived (the aligned 32-byte sector of the list around the
 //           interpolated position or the midpoint): narrow or finish
 //
 // Per trial (GRAPE, Methods, eq. alphaRW with the beta/gamma split of eqs. alpha, beta):
@@ -45,10 +46,11 @@ enum Counter : int { C_STEPS = 0, C_TRIALS, C_SEARCHES, C_PROBES, C_FALLBACKS, C
 
 struct GraphDev {
     const int4* rec;            // [n] NodeRec viewed as int4
-    const int* dsts;            // [m + 4] sorted rows (membership search, fallback)
-    // [m] proposal entries, one 16-byte word per CSR entry e (row v, target x):
-    //   unweighted: {x, deg_x, off_x lo, off_x hi}
-    //   weighted:   {x, deg_x, off_x (32-bit), w_vx bits}   (needs m < 2^32)
+    const int* dsts;            // [m + 8] sorted rows (membership search, fallback)
+    // proposal entries, one per CSR entry e (row v, target x), one sector each:
+    //   unweighted: fat[e]      = {x, deg_x, off_x lo, off_x hi}
+    //   weighted:   fat[2e]     = {x, deg_x, off_x lo, off_x hi},
+    //               fat[2e + 1] = {w_vx bits, wmax_x bits, 0, 0}
     const int4* fat;
     long long n;
     int* status;                // device status word (1 = bad start id)
@@ -69,7 +71,7 @@ struct __align__(16) WalkConst {
     int walk_len;
     double a_ret, a_out;        // 1/p and 1/q for the exact fallback
     int out_vec;                // 1 when out is 32-byte aligned (whole-sector row stores)
-    int spec;                   // 1 when most proposals are expected to be rejected
+    int pad;
 };
 static_assert(sizeof(WalkConst) % 16 == 0, "WalkConst is loaded as int4 words");
 
@@ -142,12 +144,12 @@ struct Lane {
     int req;              // request index (batched / served), -1 for per-call
     int phase;
     unsigned r2;          // acceptance uniform of the proposal in flight
-    unsigned r2b;         // ... and of the second one (speculation)
     unsigned flags;       // F_* bits below
     // the proposal under a membership search
     int x;
     int xdeg;
     long long xoff;
+    float xwmax;          // weighted: wmax of x
     // membership search over dsts[sb, sb + sn) for x (or for t, with F_KEY_T);
     // sd = (start of the probe block in flight) - sb; every value before the
     // range is <= vlo and every value after it >= vhi (vlo < key < vhi)
@@ -160,12 +162,9 @@ struct Lane {
 enum : unsigned {
     F_ACC_IN = 1u,        // accept if x is in N(t)
     F_ACC_OUT = 2u,       // accept if x is not in N(t)
-    F_WMAX = 4u,          // a load of wmax_v is in flight (weighted graphs)
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
     F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
-    F_PAIR = 64u,         // proposals k (ld) and k + 1 (ld2) are both in flight
-    F_HOLDB = 128u,       // proposal k + 1 (ld2) waits while proposal k is searched
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
@@ -309,7 +308,7 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
             if (x == L.t) a = a_ret;
             else if (!lane_search(g.dsts + L.off_t, L.deg_t, x)) a = a_out;
         }
-        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[e].w)) : 1.0;
+        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
         total = __dadd_rn(total, __dmul_rn(a, w));
     }
     const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
@@ -323,7 +322,7 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
             if (x == L.t) a = a_ret;
             else if (!lane_search(g.dsts + L.off_t, L.deg_t, x)) a = a_out;
         }
-        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[e].w)) : 1.0;
+        const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
         run = __dadd_rn(run, __dmul_rn(a, w));
         if (run > u) return x;
     }
@@ -364,7 +363,7 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.s = 1;
     L.k = 0;
     L.phase = PH_START;
-    L.flags &= ~(F_WMAX | F_KEY_T | F_ACC_IN | F_ACC_OUT | F_PAIR | F_HOLDB | F_BISECT);
+    L.flags &= ~(F_KEY_T | F_ACC_IN | F_ACC_OUT | F_BISECT);
     if (wc.walk_len <= 1) return false;
     if (r.deg == 0) {
         fill_dead(L, L.row, 1, wc.walk_len);
@@ -610,12 +609,11 @@ struct QueueFeed {
 struct Prop {
     int x, deg;
     long long off;
+    float wmax;           // weighted: wmax of x (for the walk's next step)
     bool acc_a, acc_b;    // accept if x in N(t) / if not (equal when the class is known)
 };
 
-// SPEC: proposals k and k + 1 travel together (for walks whose proposals are
-// mostly rejected); the trial order, and so the output, is unchanged.
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, bool SPEC, class Feed>
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
 struct Engine {
     const GraphDev& g;
     Feed& feed;
@@ -624,14 +622,12 @@ struct Engine {
                                  // deg_t exceeds this
     bool interp;                 // place probes by interpolation between the value bounds
     Counts<COUNT>& cnt;
-    int4& ld;                    // the gather in flight (proposal entry or probe block),
-                                 // consumed next iteration
-    int4& ld2;                   // SPEC: the second proposal entry
-    float& ld_wmax;              // weighted: wmax of the node just moved to
-    bool spec_on;                // SPEC: this request speculates
+    int4& ld;                    // the gather in flight, first 16 bytes: a proposal entry
+                                 // or the first half of a probe sector
+    int4& ld2;                   // ... its second 16 bytes (weighted entry / probe sector)
 
     // Emit x and move to it.  Returns true while the walk continues.
-    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg) {
+    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg, float wmax) {
         const int len = feed.len(L);
         int* const row = feed.row(L);
         put(L, row, L.s, x, len);
@@ -642,9 +638,9 @@ struct Engine {
         L.v = x;
         L.off_v = off;
         L.deg_v = deg;
+        L.wmax_v = wmax;
         L.s++;
         L.k = 0;
-        L.flags &= ~(F_PAIR | F_HOLDB);      // a pending second proposal is void now
         if (L.s >= len) {
             feed.finish(L.req, cnt);
             return false;
@@ -654,12 +650,6 @@ struct Engine {
             feed.finish(L.req, cnt);
             return false;
         }
-        if (WEIGHTED) {
-            // wmax of the new v is needed by the next proposal's decision: it
-            // travels alongside that proposal's gather.
-            ld_wmax = __ldg(reinterpret_cast<const float*>(g.rec + x) + 3);
-            L.flags |= F_WMAX;
-        }
         return true;
     }
 
@@ -667,27 +657,23 @@ struct Engine {
     __device__ __forceinline__ bool fallback_steps(Lane& L) {
         while (L.k >= trial_cap) {
             cnt.add(C_FALLBACKS);
-            if (WEIGHTED && (L.flags & F_WMAX)) {
-                L.wmax_v = ld_wmax;
-                L.flags &= ~F_WMAX;
-            }
             double a_ret, a_out;
             feed.alphas(L.req, a_ret, a_out);
             const int xf = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
             const NodeRec rf = load_rec(g, xf);
-            if (!advance(L, xf, rf.off, rf.deg)) return false;
+            if (!advance(L, xf, rf.off, rf.deg, rf.wmax)) return false;
         }
         return true;
     }
 
     // Decide a proposal from its entry and acceptance uniform.
-    __device__ __forceinline__ Prop eval(const Lane& L, const int4& en, unsigned r2) {
+    __device__ __forceinline__ Prop eval(const Lane& L, unsigned r2) {
         Prop p;
-        p.x = en.x;
-        p.deg = en.y;
-        p.off = WEIGHTED ? (long long)(unsigned)en.z
-                         : (long long)(((unsigned long long)(unsigned)en.w << 32) | (unsigned)en.z);
-        const float w = WEIGHTED ? __int_as_float(en.w) : 1.0f;
+        p.x = ld.x;
+        p.deg = ld.y;
+        p.off = (long long)(((unsigned long long)(unsigned)ld.w << 32) | (unsigned)ld.z);
+        const float w = WEIGHTED ? __int_as_float(ld2.x) : 1.0f;
+        p.wmax = WEIGHTED ? __int_as_float(ld2.y) : 0.0f;
         // thresholds of the two possible classes: (in, out), or one class twice
         const bool first = L.t < 0;
         const bool ret = (HAS_P || HAS_Q) && !first && p.x == L.t;
@@ -716,6 +702,7 @@ struct Engine {
         L.x = p.x;
         L.xdeg = p.deg;
         L.xoff = p.off;
+        L.xwmax = p.wmax;
         const bool use_x = g.undirected && L.deg_t > shorter_min && p.deg < L.deg_t;
         L.sb = use_x ? p.off : L.off_t;
         L.sn = use_x ? p.deg : L.deg_t;
@@ -727,31 +714,25 @@ struct Engine {
 
     // One iteration for a lane that holds a walk.  Returns have.
     //
-    // Every lane runs the same straight-line code: the proposal decisions and
+    // Every lane runs the same straight-line code: the proposal decision and
     // the probe update are evaluated with selects; Philox is computed
-    // unconditionally (some lane of the warp almost always needs it); the
-    // next gather is one 16-byte load (two with speculation) whose address is
-    // either the next proposal's entry or the next probe block.  Only walk
+    // unconditionally (some lane of the warp almost always needs it); the next
+    // gather is one 32-byte sector (or a 16-byte unweighted entry) whose address
+    // is either the next proposal's entry or the next probe sector.  Only walk
     // ends, dead ends and the rare fallback branch.
     __device__ __forceinline__ bool step(Lane& L) {
         const int phase = L.phase;
-        if (WEIGHTED && (L.flags & F_WMAX) && phase == PH_CAND) {
-            L.wmax_v = ld_wmax;
-            L.flags &= ~F_WMAX;
-        }
-        const Prop A = eval(L, ld, L.r2);
-        Prop B;
-        if (SPEC) B = eval(L, ld2, L.r2b);
-        // ---- probe view of the arrived gather (phase SEARCH) ----
+        const Prop A = eval(L, L.r2);
+        // ---- probe view of the arrived sector (phase SEARCH) ----
         const bool srch = HAS_Q && phase == PH_SEARCH;
         const int key = (L.flags & F_KEY_T) ? L.t : L.x;
         int lo = 0, hi = L.sn;
         int vlo = L.vlo, vhi = L.vhi;
         bool found = false;
         {
-            const int vals[4] = {ld.x, ld.y, ld.z, ld.w};
+            const int vals[8] = {ld.x, ld.y, ld.z, ld.w, ld2.x, ld2.y, ld2.z, ld2.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 8; ++j) {
                 const int dj = L.sd + j;
                 const bool in = (unsigned)dj < (unsigned)L.sn;
                 found |= in && vals[j] == key;
@@ -766,31 +747,21 @@ struct Engine {
             }
         }
         const bool s_done = srch && (found || hi <= lo);
-        // ---- outcome: which proposal moves the walk, or what comes next ----
-        // take: 1 = A (this phase's proposal or the searched one), 2 = B
-        int take = 0;
+        // ---- outcome ----
+        bool take = false;           // the walk moves to A (or to the searched proposal)
         bool probe = false;
-        bool search_b = false;       // start the search of B
-        bool look_b = false;         // B's decision is the next to consult
         if (phase == PH_CAND) {
             if (A.acc_a == A.acc_b || !HAS_Q) {
-                if (A.acc_a) take = 1;
-                else {
-                    L.k++;
-                    look_b = SPEC && (L.flags & F_PAIR);
-                }
+                if (A.acc_a) take = true;
+                else L.k++;
             } else {
                 begin_search(L, A);
                 probe = true;
-                if (SPEC && (L.flags & F_PAIR)) L.flags |= F_HOLDB;
             }
         } else if (srch) {
             if (s_done) {
-                if ((L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0) take = 1;
-                else {
-                    L.k++;
-                    look_b = SPEC && (L.flags & F_HOLDB);
-                }
+                if ((L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0) take = true;
+                else L.k++;
             } else {
                 // an interpolated probe that did not halve the range is followed
                 // by a bisecting one, so a search takes O(log deg) probes at worst
@@ -804,48 +775,31 @@ struct Engine {
                 probe = true;
             }
         }
-        if (SPEC && look_b) {
-            // proposal k + 1 has arrived already: decide it in this iteration
-            L.flags &= ~(F_PAIR | F_HOLDB);
-            if (B.acc_a == B.acc_b || !HAS_Q) {
-                if (B.acc_a) take = 2;
-                else L.k++;
-            } else {
-                begin_search(L, B);
-                probe = true;
-                search_b = true;
-            }
-        }
-        (void)search_b;
-        bool have = true;
         if (take) {
-            // the proposal decided in CAND phase lives in A or B; a searched one in L.x
-            const bool searched = (phase == PH_SEARCH) && take == 1;
-            const int x = searched ? L.x : (take == 1 ? A.x : B.x);
-            const long long off = searched ? L.xoff : (take == 1 ? A.off : B.off);
-            const int deg = searched ? L.xdeg : (take == 1 ? A.deg : B.deg);
-            L.flags &= ~(F_PAIR | F_HOLDB);
-            have = advance(L, x, off, deg);
+            const bool cand = phase == PH_CAND;
+            if (!advance(L, cand ? A.x : L.x, cand ? A.off : L.xoff, cand ? A.deg : L.xdeg,
+                         cand ? A.wmax : L.xwmax))
+                return false;
         }
-        if (!have) return false;
         if (!probe && L.k >= trial_cap) {
             if (!fallback_steps(L)) return false;
         }
-        // ---- the next gather: a probe block or the next proposal's entry ----
+        // ---- the next gather: a probe sector or the next proposal's entry ----
         const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
         const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
         const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-        // the aligned block around the probe position: interpolated between the
-        // value bounds (ids in a row are near-uniform after relabelling), or
-        // the midpoint
+        // the aligned sector around the probe position: interpolated between the
+        // value bounds (ids in a row are near-uniform after relabelling), or the
+        // midpoint
         int pos = L.sn >> 1;
         if (interp && !(L.flags & F_BISECT)) {
             const int kk = (L.flags & F_KEY_T) ? L.t : L.x;
             const float f = __fdividef((float)(kk - L.vlo), (float)(L.vhi - L.vlo));
             pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
         }
-        const long long bi = (L.sb + pos) & ~3LL;
-        const int4* addr = probe ? reinterpret_cast<const int4*>(g.dsts + bi) : g.fat + e;
+        const long long bi = (L.sb + pos) & ~7LL;
+        const int4* addr = probe ? reinterpret_cast<const int4*>(g.dsts + bi)
+                                 : (WEIGHTED ? g.fat + 2 * e : g.fat + e);
         if (probe) {
             L.sd = (int)(bi - L.sb);
             L.phase = PH_SEARCH;
@@ -856,25 +810,14 @@ struct Engine {
             cnt.add(C_TRIALS);
         }
         ld = __ldg(addr);
-        if (SPEC && !probe && spec_on && L.k + 1 < trial_cap) {
-            // proposal k + 1 rides along
-            const uint4 r1 = trial_block(feed.seed(L), L.w, L.s, L.k + 1);
-            const unsigned long long q64 =
-                (unsigned long long)r1.x | ((unsigned long long)r1.y << 32);
-            const long long e1 =
-                L.off_v + (long long)__umul64hi(q64, (unsigned long long)L.deg_v);
-            L.r2b = r1.z;
-            L.flags |= F_PAIR;
-            cnt.add(C_TRIALS);
-            ld2 = __ldg(g.fat + e1);
-        }
+        if (WEIGHTED || probe) ld2 = __ldg(addr + 1);    // same 32-byte sector
         return true;
     }
 };
 
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, bool SPEC, class Feed>
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
-                                          int shorter_min, int interp_search, bool spec_on) {
+                                          int shorter_min, int interp_search) {
     Lane L;
     L.t = -1;
     L.req = -1;
@@ -886,16 +829,13 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     L.sd = 0;
     L.vlo = -1;
     L.vhi = 0;
+    L.r2 = 0;
     Counts<COUNT> cnt;
     cnt.clear();
-    L.r2 = 0;
-    L.r2b = 0;
     int4 ld = make_int4(0, 0, 0, 0);
     int4 ld2 = make_int4(0, 0, 0, 0);
-    float ld_wmax = 0.0f;
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, SPEC, Feed> eng{g, feed, trial_cap, shorter_min,
-                                                          interp_search != 0, cnt, ld, ld2,
-                                                          ld_wmax, spec_on};
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
+                                                    interp_search != 0, cnt, ld, ld2};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);

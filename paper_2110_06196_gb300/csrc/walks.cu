@@ -27,17 +27,15 @@ constexpr int kMinBlocksQueue = 3;
 
 // Per-call walk kernel: the eight specialisations of GRAPE ("Implementation of
 // second-order RWs": p == 1, q == 1, weighted or not) as template arguments.
-// COUNT: the instantiation that also keeps the work counters.  SPEC: two
-// proposals in flight per lane (for requests whose proposals are mostly
-// rejected).
-template <bool W, bool P, bool Q, bool COUNT, bool SPEC>
+// COUNT: the instantiation that also keeps the work counters.
+template <bool W, bool P, bool Q, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
 walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min, int interp_search) {
     GridFeed f;
     f.wc = &wc;
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
-    walk_loop<W, P, Q, COUNT, SPEC>(g, f, trial_cap, shorter_min, interp_search, SPEC);
+    walk_loop<W, P, Q, COUNT>(g, f, trial_cap, shorter_min, interp_search);
 }
 
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
@@ -61,7 +59,7 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true, COUNT, false>(g, f, trial_cap, shorter_min, interp_search, false);
+    walk_loop<W, true, true, COUNT>(g, f, trial_cap, shorter_min, interp_search);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint32_t* __restrict__ out) {
@@ -123,17 +121,17 @@ int occupancy_blocks(K kernel, int threads) {
     return nb;
 }
 
-template <bool W, bool P, bool Q, bool C, bool S>
+template <bool W, bool P, bool Q, bool C>
 cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
                           cudaStream_t stream) {
     const int threads = std::min(t.block_threads, kMaxThreads);
     int per_sm = t.blocks_per_sm;
-    if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q, C, S>, threads);
+    if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q, C>, threads);
     long long blocks = (wc.num_walks + threads - 1) / threads;
     const long long cap = (long long)g->num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    walk_kernel<W, P, Q, C, S><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
+    walk_kernel<W, P, Q, C><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
         g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
     return cudaGetLastError();
 }
@@ -141,12 +139,8 @@ cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const W
 template <bool W, bool P, bool Q>
 cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
                         cudaStream_t stream) {
-    const bool spec = t.speculate == 2 || (t.speculate == 1 && wc.spec);
-    if (spec)
-        return g->counting ? launch_walk_c<W, P, Q, true, true>(g, t, wc, stream)
-                           : launch_walk_c<W, P, Q, false, true>(g, t, wc, stream);
-    return g->counting ? launch_walk_c<W, P, Q, true, false>(g, t, wc, stream)
-                       : launch_walk_c<W, P, Q, false, false>(g, t, wc, stream);
+    return g->counting ? launch_walk_c<W, P, Q, true>(g, t, wc, stream)
+                       : launch_walk_c<W, P, Q, false>(g, t, wc, stream);
 }
 
 cudaError_t dispatch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
@@ -208,10 +202,6 @@ grape_status_t make_walk_const(const grape_graph* g, const int32_t* starts, int6
     wc->a_ret = alpha[0];
     wc->a_out = alpha[2];
     wc->out_vec = ((reinterpret_cast<uintptr_t>(out) & 31u) == 0) ? 1 : 0;
-    // Most proposals are rejected when the weights thin them out, or when both
-    // common classes (in, out) accept at most half of the time: then a second
-    // proposal in flight saves latency.
-    wc->spec = (g->weighted || (tm1[1] < 0x80000000u && tm1[2] < 0x80000000u)) ? 1 : 0;
     return GRAPE_OK;
 }
 
