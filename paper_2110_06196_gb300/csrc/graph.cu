@@ -200,7 +200,9 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     // dsts is padded by four entries so that a search probe, which reads the
     // aligned 16-byte block around a list position, never leaves the allocation.
     const size_t m_alloc = (size_t)num_entries + 8;
-    const size_t fat_words = (num_entries > 0 ? (size_t)num_entries : 1) * (weights ? 2 : 1);
+    // proposal entries, padded to a whole sector: a proposal reads the aligned
+    // 32-byte sector that holds its entry
+    const size_t fat_words = (num_entries > 0 ? (size_t)num_entries : 1) * (weights ? 2 : 1) + 2;
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
     if (e == cudaSuccess) e = cudaMalloc(&g->fat, sizeof(int4) * fat_words);

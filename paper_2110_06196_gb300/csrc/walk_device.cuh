@@ -111,6 +111,15 @@ __device__ __forceinline__ uint4 trial_block(unsigned long long seed, long long 
                          make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
 }
 
+// One 32-byte sector in a single 256-bit read-only load (sm_100 and later):
+// the first 16 bytes to a, the last 16 to b.  p must be 32-byte aligned.
+__device__ __forceinline__ void ld_sector(const void* p, int4& a, int4& b) {
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z),
+                   "=r"(b.w)
+                 : "l"(p));
+}
+
 // Is key in the sorted list a[0, n)?  Lane-local binary search (used by the
 // exact fallback, which runs outside the pipelined state machine).
 __device__ __forceinline__ bool lane_search(const int* __restrict__ a, int n, int key) {
@@ -165,6 +174,7 @@ enum : unsigned {
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
     F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
+    F_HALF = 64u,         // unweighted: the proposal entry is the second half of its sector
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
@@ -669,9 +679,11 @@ struct Engine {
     // Decide a proposal from its entry and acceptance uniform.
     __device__ __forceinline__ Prop eval(const Lane& L, unsigned r2) {
         Prop p;
-        p.x = ld.x;
-        p.deg = ld.y;
-        p.off = (long long)(((unsigned long long)(unsigned)ld.w << 32) | (unsigned)ld.z);
+        // unweighted entries are 16 bytes: the sector holds two of them
+        const int4 en = (!WEIGHTED && (L.flags & F_HALF)) ? ld2 : ld;
+        p.x = en.x;
+        p.deg = en.y;
+        p.off = (long long)(((unsigned long long)(unsigned)en.w << 32) | (unsigned)en.z);
         const float w = WEIGHTED ? __int_as_float(ld2.x) : 1.0f;
         p.wmax = WEIGHTED ? __int_as_float(ld2.y) : 0.0f;
         // thresholds of the two possible classes: (in, out), or one class twice
@@ -798,8 +810,9 @@ struct Engine {
             pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
         }
         const long long bi = (L.sb + pos) & ~7LL;
+        // every gather is one aligned 32-byte sector, read by one 256-bit load
         const int4* addr = probe ? reinterpret_cast<const int4*>(g.dsts + bi)
-                                 : (WEIGHTED ? g.fat + 2 * e : g.fat + e);
+                                 : (WEIGHTED ? g.fat + 2 * e : g.fat + (e & ~1LL));
         if (probe) {
             L.sd = (int)(bi - L.sb);
             L.phase = PH_SEARCH;
@@ -807,10 +820,10 @@ struct Engine {
         } else {
             L.r2 = r.z;
             L.phase = PH_CAND;
+            if (!WEIGHTED) L.flags = (e & 1) ? (L.flags | F_HALF) : (L.flags & ~F_HALF);
             cnt.add(C_TRIALS);
         }
-        ld = __ldg(addr);
-        if (WEIGHTED || probe) ld2 = __ldg(addr + 1);    // same 32-byte sector
+        ld_sector(addr, ld, ld2);
         return true;
     }
 };
