@@ -197,12 +197,13 @@ def count_steps(out: torch.Tensor) -> int:
 
 def algorithmic_bytes(c: dict, rows: int, walk_len: int) -> int:
     """Sector-granular lower bound on the DRAM bytes of one launch: one 32-byte
-    sector per proposal (its entry holds the candidate, its weight and the
-    candidate's row offset and degree, so an accepted step needs nothing more),
-    one per acceptance-deciding membership test (the least any search structure
-    can read), one per walk start (the start's record), plus the 4-byte output
-    entries."""
-    return SECTOR * (c["trials"] + c["searches"] + c["walks"]) + 4 * rows * walk_len
+    sector per proposal whose entry has to be read (the entry holds the
+    candidate, its weight and the candidate's row offset and degree, so an
+    accepted step needs nothing more; returns and certain rejections are decided
+    without one), one per acceptance-deciding membership test (the least any
+    search structure can read), one per walk start (the start's record), plus
+    the 4-byte output entries."""
+    return SECTOR * (c["gathers"] + c["searches"] + c["walks"]) + 4 * rows * walk_len
 
 
 def random_sector_peak(dev, gib=16, reads=1 << 31):
@@ -389,6 +390,7 @@ def run_ours(args, dist):
                      "random_sector_peak": rs_peak,
                      "frac_of_random_sector_peak": achieved / rs_peak},
         "counters": {"trials_per_step": cnt["trials"] / max(1, cnt["steps"]),
+                     "gathers_per_step": cnt["gathers"] / max(1, cnt["steps"]),
                      "searches_per_step": cnt["searches"] / max(1, cnt["steps"]),
                      "probes_per_search": cnt["probes"] / max(1, cnt["searches"]),
                      "fallbacks": cnt["fallbacks"]},

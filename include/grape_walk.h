@@ -94,10 +94,10 @@ typedef struct grape_graph grape_graph_t;
  *       caller keeps ownership; they may be freed once `stream` has reached
  *       this call's work (the copies are enqueued on it).
  *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62].  The graph holds
- *   16 * num_nodes + 20 * num_entries bytes (36 for weighted graphs): node
- *   records, sorted rows, and per CSR entry one proposal entry of 16 (32)
- *   bytes that carries the target's degree and row offset (and the weight
- *   and the target's largest row weight).
+ *   16 * num_nodes + 36 * num_entries bytes: node records, sorted rows, and
+ *   per CSR entry one 32-byte proposal entry that carries the target's degree,
+ *   row offset and largest row weight, the weight, and the position of the
+ *   row's node in the target's row.
  *   flags: GRAPE_UNDIRECTED | GRAPE_VALIDATE.  With GRAPE_VALIDATE the call
  *       synchronises `stream` and returns GRAPE_ERR_INVALID_GRAPH for:
  *       non-monotone offsets, wrong first or last offset, ids out of range,
@@ -281,6 +281,8 @@ grape_status_t grape_stream_status(const grape_graph_t* graph, grape_stream_t st
 typedef struct grape_walk_counters {
     int64_t steps;        /* transitions taken */
     int64_t trials;       /* proposals drawn */
+    int64_t gathers;      /* proposals whose entry had to be read (the rest were decided
+                             without a read: rejected whatever the target, or the return) */
     int64_t searches;     /* membership tests whose outcome decided acceptance */
     int64_t probes;       /* list entries loaded by those tests */
     int64_t fallbacks;    /* steps drawn by the exact inverse-transform fallback */

@@ -6,12 +6,13 @@
 //   rec[v]   16-byte record {row offset (int64), degree (int32), max row weight (fp32)}
 //            so that one aligned 16-byte load gives everything a step needs about v;
 //   dsts[e]  int32 sorted rows, read by the membership searches (padded by 8);
-//   fat      proposal entries, one sector's worth per CSR entry: {x, deg_x,
-//            off_x} (16 bytes), and for weighted graphs also {w_vx, wmax_x} in
-//            the second half of a 32-byte entry.  A proposal reads its target,
+//   fat      one 32-byte proposal entry per CSR entry e (row v, target x):
+//            {x, deg_x, off_x lo, off_x hi} {w_vx, wmax_x, rev, w_xv}, rev being
+//            the position of v in N(x) (-1 when absent) and w_xv its weight.  A proposal reads its target,
 //            the target's row, the weight and the target's row maximum from one
-//            sector, so an accepted step needs no further gather
-//            (edge-inlined records).
+//            sector, so an accepted step needs no further gather (edge-inlined
+//            records); rev tells the walk where its previous node sits in the
+//            next row, so proposals of the return class need no gather at all.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -86,21 +87,37 @@ __global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
     }
 }
 
-// Proposal entries: fat[e] = {x, deg_x, off_x lo, off_x hi} or, weighted,
-// fat[2e] = the same and fat[2e + 1] = {w_vx bits, wmax_x bits, 0, 0}.  Ids
-// were checked by build_rows_kernel.
+// Proposal entries: fat[2e] = {x, deg_x, off_x lo, off_x hi},
+// fat[2e + 1] = {w_vx bits, wmax_x bits, rev, w_xv bits} (weights 1.0 when
+// unweighted).  One warp per row v, so the row's own bounds are known; ids were
+// checked by build_rows_kernel.  rev = position of v in N(x) (binary search),
+// or -1, and then w_xv = 0.
 __global__ void build_fat_kernel(const int32_t* __restrict__ dsts, const float* __restrict__ weights,
-                                 const int4* __restrict__ rec, long long m,
+                                 const int4* __restrict__ rec, long long n,
                                  int4* __restrict__ fat) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int x = dsts[e];
-        const int4 r = rec[x];
-        if (weights) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
+         v += warps) {
+        const int4 rv = rec[v];
+        const long long a = (long long)(((unsigned long long)(unsigned)rv.y << 32) | (unsigned)rv.x);
+        const long long b = a + rv.z;
+        for (long long e = a + lane; e < b; e += 32) {
+            const int x = dsts[e];
+            const int4 r = rec[x];
+            const long long xa = (long long)(((unsigned long long)(unsigned)r.y << 32) | (unsigned)r.x);
+            long long lo = xa, hi = xa + r.z;
+            while (lo < hi) {
+                const long long mid = lo + (hi - lo) / 2;
+                if (dsts[mid] < v) lo = mid + 1; else hi = mid;
+            }
+            const bool back = lo < xa + r.z && dsts[lo] == v;
+            const int rev = back ? (int)(lo - xa) : -1;
+            const int one = __float_as_int(1.0f);
+            const int w = weights ? __float_as_int(weights[e]) : one;
+            const int wrev = back ? (weights ? __float_as_int(weights[lo]) : one) : 0;
             fat[2 * e] = make_int4(x, r.z, r.x, r.y);
-            fat[2 * e + 1] = make_int4(__float_as_int(weights[e]), r.w, 0, 0);
-        } else {
-            fat[e] = make_int4(x, r.z, r.x, r.y);
+            fat[2 * e + 1] = make_int4(w, r.w, rev, wrev);
         }
     }
 }
@@ -202,7 +219,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     const size_t m_alloc = (size_t)num_entries + 8;
     // proposal entries, padded to a whole sector: a proposal reads the aligned
     // 32-byte sector that holds its entry
-    const size_t fat_words = (num_entries > 0 ? (size_t)num_entries : 1) * (weights ? 2 : 1) + 2;
+    const size_t fat_words = (num_entries > 0 ? (size_t)num_entries : 1) * 2;
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
     if (e == cudaSuccess) e = cudaMalloc(&g->fat, sizeof(int4) * fat_words);
@@ -252,8 +269,8 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     }
     // 3. Proposal entries (ids are known in range now).
     if (num_entries > 0) {
-        build_fat_kernel<<<grid_for(g->num_sms, num_entries, 256), 256, 0, stream>>>(
-            g->dsts, weights, g->rec, num_entries, g->fat);
+        build_fat_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+            g->dsts, weights, g->rec, num_nodes, g->fat);
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             free_graph(g);
@@ -361,12 +378,13 @@ grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out)
     GRAPE_CUDA_TRY(cudaMemcpy(c, g->counters, sizeof(c), cudaMemcpyDeviceToHost));
     GRAPE_CUDA_TRY(cudaMemset(g->counters, 0, sizeof(c)));
     GRAPE_CUDA_TRY(cudaDeviceSynchronize());
-    out->steps = (int64_t)c[0];
-    out->trials = (int64_t)c[1];
-    out->searches = (int64_t)c[2];
-    out->probes = (int64_t)c[3];
-    out->fallbacks = (int64_t)c[4];
-    out->walks = (int64_t)c[5];
+    out->steps = (int64_t)c[grape::C_STEPS];
+    out->trials = (int64_t)c[grape::C_TRIALS];
+    out->gathers = (int64_t)c[grape::C_GATHERS];
+    out->searches = (int64_t)c[grape::C_SEARCHES];
+    out->probes = (int64_t)c[grape::C_PROBES];
+    out->fallbacks = (int64_t)c[grape::C_FALLBACKS];
+    out->walks = (int64_t)c[grape::C_WALKS];
     return GRAPE_OK;
 }
 

@@ -207,13 +207,13 @@ grape_status_t grape_walks_batched_static(const grape_graph_t* g,
     int per_sm = 0;
     if (g->weighted)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_queue_kernel<true>, s.threads,
-                                                      (size_t)s.threads * 32);
+                                                      (size_t)s.threads * kLaneSharedBytes);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_queue_kernel<false>,
-                                                      s.threads, (size_t)s.threads * 32);
+                                                      s.threads, (size_t)s.threads * kLaneSharedBytes);
     if (per_sm < 1) per_sm = 1;
     const int blocks = g->num_sms * per_sm;
-    const size_t sh = (size_t)s.threads * 32;
+    const size_t sh = (size_t)s.threads * kLaneSharedBytes;
     if (g->weighted)
         static_queue_kernel<true><<<blocks, s.threads, sh, stream>>>(
             g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);

@@ -11,8 +11,12 @@
 // A lane deep in a membership search on a hub list therefore does not hold up
 // the other 31 lanes of its warp.  Proposal entries carry the proposed node's
 // degree and row offset ("edge-inlined records", see GraphDev::fat), so an
-// accepted proposal needs no second gather: a step is (proposals + probes)
-// dependent gathers.  Phases:
+// accepted proposal needs no second gather.  Two kinds of proposal need no
+// gather at all: the return (the lane knows the position of t in N(v) and the
+// weight of that entry) and, once the return is ruled out, a proposal whose
+// acceptance uniform is at or above every other class's threshold (rejected
+// whatever its target and weight, since w <= wmax).  A step is therefore
+// (read proposals + probes) dependent gathers.  Phases:
 //   CAND    a proposal entry arrived: classify and decide, or start a search
 //   SEARCH  a probe arrived (the aligned 32-byte sector of the list around the
 //           interpolated position or the midpoint): narrow or finish
@@ -42,15 +46,17 @@ struct __align__(16) NodeRec {
     float wmax;
 };
 
-enum Counter : int { C_STEPS = 0, C_TRIALS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_COUNT };
+enum Counter : int {
+    C_STEPS = 0, C_TRIALS, C_GATHERS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_COUNT
+};
 
 struct GraphDev {
     const int4* rec;            // [n] NodeRec viewed as int4
     const int* dsts;            // [m + 8] sorted rows (membership search, fallback)
-    // proposal entries, one per CSR entry e (row v, target x), one sector each:
-    //   unweighted: fat[e]      = {x, deg_x, off_x lo, off_x hi}
-    //   weighted:   fat[2e]     = {x, deg_x, off_x lo, off_x hi},
-    //               fat[2e + 1] = {w_vx bits, wmax_x bits, 0, 0}
+    // proposal entries, one 32-byte sector per CSR entry e (row v, target x):
+    //   fat[2e]     = {x, deg_x, off_x lo, off_x hi}
+    //   fat[2e + 1] = {w_vx bits (1.0 unweighted), wmax_x bits, rev, w_xv bits}
+    // rev = position of v in N(x) (-1 when absent), w_xv the weight there
     const int4* fat;
     long long n;
     int* status;                // device status word (1 = bad start id)
@@ -136,11 +142,18 @@ __device__ __forceinline__ bool lane_search(const int* __restrict__ a, int n, in
 // ---------------------------------------------------------------------------
 // Lane state
 // ---------------------------------------------------------------------------
-enum Phase : int { PH_START = 0, PH_CAND = 1, PH_SEARCH = 2 };
+//   PH_DRAW  nothing arrived: draw the next proposal
+//   PH_RET   the return was drawn and accepted (no read): move back to t
+enum Phase : int { PH_START = 0, PH_CAND = 1, PH_SEARCH = 2, PH_DRAW = 3, PH_RET = 4 };
+
+// Proposals a lane may draw in one iteration.  Those decided without a read
+// (returns, certain rejections) let the lane go on to the next one; the bound
+// keeps the lanes of a warp in step.
+constexpr int kDrawsPerIter = 2;
 
 struct Lane {
     long long w;          // walk id (Philox counter words 0-1)
-    long long off_v, off_t;
+    long long off_v;
     int* row;             // this walk's output row (batched / served)
     unsigned long long seed;
     unsigned tm1_ret, tm1_in, tm1_out;
@@ -148,17 +161,18 @@ struct Lane {
     int s;                // index of the entry being produced (1 .. len-1)
     int len;
     int v, t;             // current and previous node (t < 0 on the first step)
-    int deg_v, deg_t;
+    int deg_v;
     float wmax_v;
+    int rt;               // position of t in N(v); -1 when t is not in N(v) or there is no t
+    float wr;             // weighted: the weight of that entry (v -> t)
+    int pidx;             // position in N(v) of the proposal in flight or under search
+    // the rest of t's state lives in shared memory (TRec)
     int req;              // request index (batched / served), -1 for per-call
     int phase;
     unsigned r2;          // acceptance uniform of the proposal in flight
     unsigned flags;       // F_* bits below
-    // the proposal under a membership search
+    // the proposal under a membership search (its entry waits in shared memory)
     int x;
-    int xdeg;
-    long long xoff;
-    float xwmax;          // weighted: wmax of x
     // membership search over dsts[sb, sb + sn) for x (or for t, with F_KEY_T);
     // sd = (start of the probe block in flight) - sb; every value before the
     // range is <= vlo and every value after it >= vhi (vlo < key < vhi)
@@ -174,7 +188,6 @@ enum : unsigned {
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
     F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
-    F_HALF = 64u,         // unweighted: the proposal entry is the second half of its sector
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
@@ -195,6 +208,22 @@ struct Counts<false> {
     __device__ __forceinline__ void add(int) {}
 };
 
+// The previous node's record and the entry the walk arrived by.  Read only
+// by membership searches, returns and the fallback, so it waits in shared
+// memory instead of registers.
+struct __align__(16) TRec {
+    long long off_t;
+    int deg_t;
+    float wmax_t;
+    int jv;               // position of v in N(t)
+    float wj;             // weighted: the weight there (t -> v)
+    int pad[2];
+};
+
+// Dynamic shared memory per lane: a 32-byte output staging slot, the 32-byte
+// entry of the proposal under a membership search, and the lane's TRec.
+constexpr int kLaneSharedBytes = 96;
+
 // Row writer.  Each lane stages its row's entries in its own 32-byte slot of
 // shared memory; when an entry completes a 32-byte sector that lies inside the
 // row, the sector leaves as two 16-byte stores, so DRAM sees whole sectors.
@@ -203,6 +232,16 @@ struct Counts<false> {
 __device__ __forceinline__ int* out_stage() {
     extern __shared__ int4 stage_words[];
     return reinterpret_cast<int*>(stage_words) + 8 * threadIdx.x;
+}
+
+__device__ __forceinline__ int4* parked_entry() {
+    extern __shared__ int4 stage_words[];
+    return stage_words + 2 * blockDim.x + 2 * threadIdx.x;
+}
+
+__device__ __forceinline__ TRec* trec() {
+    extern __shared__ int4 stage_words[];
+    return reinterpret_cast<TRec*>(stage_words + 4 * blockDim.x) + threadIdx.x;
 }
 
 __device__ __forceinline__ void put(const Lane& L, int* row, int s, int val, int len) {
@@ -304,11 +343,15 @@ __device__ __forceinline__ bool accept_test(unsigned r2, float wmax, unsigned tm
 // Exact fallback after trial_cap rejections: inverse transform over the
 // cumulative sum of pi in row order (GRAPE, "Efficient sampling for Node2Vec
 // RWs"), in fp64 with every product and sum rounded separately.
+// Returns the position of the drawn node in N(v).
 template <bool WEIGHTED>
 __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long long seed,
                               double a_ret, double a_out, unsigned trial_cap) {
     const uint4 r = trial_block(seed, L.w, L.s, trial_cap);
     const bool first = (L.t < 0);
+    const TRec* tr = trec();
+    const int* const nt = first ? g.dsts : g.dsts + tr->off_t;
+    const int deg_t = first ? 0 : tr->deg_t;
     double total = 0.0;
     for (int j = 0; j < L.deg_v; ++j) {
         const long long e = L.off_v + j;
@@ -316,7 +359,7 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
         double a = 1.0;
         if (!first) {
             if (x == L.t) a = a_ret;
-            else if (!lane_search(g.dsts + L.off_t, L.deg_t, x)) a = a_out;
+            else if (!lane_search(nt, deg_t, x)) a = a_out;
         }
         const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
         total = __dadd_rn(total, __dmul_rn(a, w));
@@ -330,13 +373,13 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
         double a = 1.0;
         if (!first) {
             if (x == L.t) a = a_ret;
-            else if (!lane_search(g.dsts + L.off_t, L.deg_t, x)) a = a_out;
+            else if (!lane_search(nt, deg_t, x)) a = a_out;
         }
         const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
         run = __dadd_rn(run, __dmul_rn(a, w));
-        if (run > u) return x;
+        if (run > u) return j;
     }
-    return __ldg(g.dsts + L.off_v + L.deg_v - 1);
+    return L.deg_v - 1;
 }
 
 // Start the walk of row `row` (walk id walk_base + row) of request wc on this
@@ -367,6 +410,7 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     const NodeRec r = load_rec(g, (int)v0);
     L.v = (int)v0;
     L.t = -1;
+    L.rt = -1;
     L.off_v = r.off;
     L.deg_v = r.deg;
     L.wmax_v = r.wmax;
@@ -619,7 +663,6 @@ struct QueueFeed {
 struct Prop {
     int x, deg;
     long long off;
-    float wmax;           // weighted: wmax of x (for the walk's next step)
     bool acc_a, acc_b;    // accept if x in N(t) / if not (equal when the class is known)
 };
 
@@ -632,23 +675,31 @@ struct Engine {
                                  // deg_t exceeds this
     bool interp;                 // place probes by interpolation between the value bounds
     Counts<COUNT>& cnt;
-    int4& ld;                    // the gather in flight, first 16 bytes: a proposal entry
-                                 // or the first half of a probe sector
-    int4& ld2;                   // ... its second 16 bytes (weighted entry / probe sector)
+    int4& ld;                    // the gather in flight: a proposal entry or a probe
+    int4& ld2;                   // sector, first and second 16 bytes
 
-    // Emit x and move to it.  Returns true while the walk continues.
-    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg, float wmax) {
+    // Emit x and move to it.  rt, wr: position of v in N(x) and the weight there;
+    // jv, wj: position of x in N(v) and the weight there.  Returns true while the
+    // walk continues.
+    __device__ __forceinline__ bool advance(Lane& L, int x, long long off, int deg, float wmax,
+                                            int rt, float wr, int jv, float wj) {
         const int len = feed.len(L);
         int* const row = feed.row(L);
         put(L, row, L.s, x, len);
         cnt.add(C_STEPS);
+        TRec* tr = trec();
+        tr->off_t = L.off_v;
+        tr->deg_t = L.deg_v;
+        tr->wmax_t = L.wmax_v;
+        tr->jv = jv;
+        tr->wj = wj;
         L.t = L.v;
-        L.off_t = L.off_v;
-        L.deg_t = L.deg_v;
         L.v = x;
         L.off_v = off;
         L.deg_v = deg;
         L.wmax_v = wmax;
+        L.rt = rt;
+        L.wr = wr;
         L.s++;
         L.k = 0;
         if (L.s >= len) {
@@ -663,15 +714,23 @@ struct Engine {
         return true;
     }
 
+    // Move along the proposal whose entry is (a, b), at position idx of N(v).
+    __device__ __forceinline__ bool advance_entry(Lane& L, int4 a, int4 b, int idx) {
+        const long long off = (long long)(((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.z);
+        return advance(L, a.x, off, a.y, __int_as_float(b.y), b.z, __int_as_float(b.w), idx,
+                       __int_as_float(b.x));
+    }
+
     // Steps drawn by the exact fallback while the trial cap is spent.  Returns have.
     __device__ __forceinline__ bool fallback_steps(Lane& L) {
         while (L.k >= trial_cap) {
             cnt.add(C_FALLBACKS);
             double a_ret, a_out;
             feed.alphas(L.req, a_ret, a_out);
-            const int xf = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
-            const NodeRec rf = load_rec(g, xf);
-            if (!advance(L, xf, rf.off, rf.deg, rf.wmax)) return false;
+            const int j = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
+            int4 a, b;
+            ld_sector(g.fat + 2 * (L.off_v + j), a, b);
+            if (!advance_entry(L, a, b, j)) return false;
         }
         return true;
     }
@@ -679,13 +738,10 @@ struct Engine {
     // Decide a proposal from its entry and acceptance uniform.
     __device__ __forceinline__ Prop eval(const Lane& L, unsigned r2) {
         Prop p;
-        // unweighted entries are 16 bytes: the sector holds two of them
-        const int4 en = (!WEIGHTED && (L.flags & F_HALF)) ? ld2 : ld;
-        p.x = en.x;
-        p.deg = en.y;
-        p.off = (long long)(((unsigned long long)(unsigned)en.w << 32) | (unsigned)en.z);
+        p.x = ld.x;
+        p.deg = ld.y;
+        p.off = (long long)(((unsigned long long)(unsigned)ld.w << 32) | (unsigned)ld.z);
         const float w = WEIGHTED ? __int_as_float(ld2.x) : 1.0f;
-        p.wmax = WEIGHTED ? __int_as_float(ld2.y) : 0.0f;
         // thresholds of the two possible classes: (in, out), or one class twice
         const bool first = L.t < 0;
         const bool ret = (HAS_P || HAS_Q) && !first && p.x == L.t;
@@ -711,13 +767,15 @@ struct Engine {
     // x in N(t) <=> t in N(x) for symmetric graphs: search the shorter row.
     __device__ __forceinline__ void begin_search(Lane& L, const Prop& p) {
         cnt.add(C_SEARCHES);
+        int4* pe = parked_entry();
+        pe[0] = ld;
+        pe[1] = ld2;
         L.x = p.x;
-        L.xdeg = p.deg;
-        L.xoff = p.off;
-        L.xwmax = p.wmax;
-        const bool use_x = g.undirected && L.deg_t > shorter_min && p.deg < L.deg_t;
-        L.sb = use_x ? p.off : L.off_t;
-        L.sn = use_x ? p.deg : L.deg_t;
+        const TRec* tr = trec();
+        const int deg_t = tr->deg_t;
+        const bool use_x = g.undirected && deg_t > shorter_min && p.deg < deg_t;
+        L.sb = use_x ? p.off : tr->off_t;
+        L.sn = use_x ? p.deg : deg_t;
         L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT)) |
                   (p.acc_a ? F_ACC_IN : 0u) | (p.acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
         L.vlo = -1;                      // node ids lie in [0, n)
@@ -726,12 +784,10 @@ struct Engine {
 
     // One iteration for a lane that holds a walk.  Returns have.
     //
-    // Every lane runs the same straight-line code: the proposal decision and
-    // the probe update are evaluated with selects; Philox is computed
-    // unconditionally (some lane of the warp almost always needs it); the next
-    // gather is one 32-byte sector (or a 16-byte unweighted entry) whose address
-    // is either the next proposal's entry or the next probe sector.  Only walk
-    // ends, dead ends and the rare fallback branch.
+    // The proposal decision and the probe update are evaluated with selects;
+    // then a lane that is not probing draws proposals until one needs its entry
+    // read, deciding returns and certain rejections on the way.  The next gather
+    // is one 32-byte sector: the next proposal's entry or the next probe sector.
     __device__ __forceinline__ bool step(Lane& L) {
         const int phase = L.phase;
         const Prop A = eval(L, L.r2);
@@ -787,43 +843,86 @@ struct Engine {
                 probe = true;
             }
         }
+        take = take || phase == PH_RET;
         if (take) {
-            const bool cand = phase == PH_CAND;
-            if (!advance(L, cand ? A.x : L.x, cand ? A.off : L.xoff, cand ? A.deg : L.xdeg,
-                         cand ? A.wmax : L.xwmax))
-                return false;
+            // one advance per iteration: along the arrived entry, the parked one
+            // (after a search), or back to t (an accepted return)
+            int4 a = ld, b = ld2;
+            int jv = L.pidx;
+            if (phase == PH_SEARCH) {
+                const int4* pe = parked_entry();
+                a = pe[0];
+                b = pe[1];
+            } else if (phase == PH_RET) {
+                const TRec tr = *trec();
+                a = make_int4(L.t, tr.deg_t, (int)(unsigned)tr.off_t,
+                              (int)(unsigned)((unsigned long long)tr.off_t >> 32));
+                b = make_int4(__float_as_int(L.wr), __float_as_int(tr.wmax_t), tr.jv,
+                              __float_as_int(tr.wj));
+                jv = L.rt;
+            }
+            if (!advance_entry(L, a, b, jv)) return false;
         }
-        if (!probe && L.k >= trial_cap) {
-            if (!fallback_steps(L)) return false;
-        }
-        // ---- the next gather: a probe sector or the next proposal's entry ----
-        const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
-        const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
-        const long long e = L.off_v + (long long)__umul64hi(r64, (unsigned long long)L.deg_v);
-        // the aligned sector around the probe position: interpolated between the
-        // value bounds (ids in a row are near-uniform after relabelling), or the
-        // midpoint
-        int pos = L.sn >> 1;
-        if (interp && !(L.flags & F_BISECT)) {
-            const int kk = (L.flags & F_KEY_T) ? L.t : L.x;
-            const float f = __fdividef((float)(kk - L.vlo), (float)(L.vhi - L.vlo));
-            pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
-        }
-        const long long bi = (L.sb + pos) & ~7LL;
-        // every gather is one aligned 32-byte sector, read by one 256-bit load
-        const int4* addr = probe ? reinterpret_cast<const int4*>(g.dsts + bi)
-                                 : (WEIGHTED ? g.fat + 2 * e : g.fat + (e & ~1LL));
+        const int4* addr = nullptr;
         if (probe) {
+            // the aligned sector around the probe position: interpolated between
+            // the value bounds (ids in a row are near-uniform after relabelling),
+            // or the midpoint
+            int pos = L.sn >> 1;
+            if (interp && !(L.flags & F_BISECT)) {
+                const int kk = (L.flags & F_KEY_T) ? L.t : L.x;   // begin_search may have set it
+                const float f = __fdividef((float)(kk - L.vlo), (float)(L.vhi - L.vlo));
+                pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
+            }
+            const long long bi = (L.sb + pos) & ~7LL;
+            addr = reinterpret_cast<const int4*>(g.dsts + bi);
             L.sd = (int)(bi - L.sb);
             L.phase = PH_SEARCH;
             cnt.add(C_PROBES);
         } else {
-            L.r2 = r.z;
-            L.phase = PH_CAND;
-            if (!WEIGHTED) L.flags = (e & 1) ? (L.flags | F_HALF) : (L.flags & ~F_HALF);
-            cnt.add(C_TRIALS);
+            // Draw proposals until one needs its entry read, at most
+            // kDrawsPerIter of them.  Past the first step the lane knows where t
+            // sits in N(v): that proposal is the return, decided with the weight
+            // of the entry it arrived by.  Any other proposal is rejected without
+            // a read when r2 fails the larger of the in and out thresholds
+            // (w <= wmax_v).
+            const unsigned tin = feed.tm1_in(L);
+            const unsigned tout = HAS_Q ? feed.tm1_out(L) : tin;
+            const unsigned tmax = tin > tout ? tin : tout;
+            L.phase = PH_DRAW;
+#pragma unroll 1
+            for (int d = 0; d < kDrawsPerIter; ++d) {
+                if (L.k >= trial_cap) {
+                    if (!fallback_steps(L)) return false;
+                }
+                const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
+                const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+                const int idx = (int)__umul64hi(r64, (unsigned long long)L.deg_v);
+                cnt.add(C_TRIALS);
+                if (L.t >= 0) {
+                    if (idx == L.rt) {
+                        if (accept_test<WEIGHTED>(r.z, L.wmax_v, feed.tm1_ret(L), L.wr)) {
+                            L.phase = PH_RET;       // taken at the next iteration
+                            break;
+                        }
+                        L.k++;
+                        continue;
+                    }
+                    if (r.z > tmax) {
+                        L.k++;
+                        continue;
+                    }
+                }
+                L.r2 = r.z;
+                L.pidx = idx;
+                L.phase = PH_CAND;
+                addr = g.fat + 2 * (L.off_v + idx);
+                cnt.add(C_GATHERS);
+                break;
+            }
         }
-        ld_sector(addr, ld, ld2);
+        // every gather is one aligned 32-byte sector, read by one 256-bit load
+        if (addr) ld_sector(addr, ld, ld2);
         return true;
     }
 };

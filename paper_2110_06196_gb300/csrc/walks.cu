@@ -109,7 +109,7 @@ sector_probe_kernel(const int4* __restrict__ buf, unsigned long long nsec, long 
 // Launch helpers
 // ---------------------------------------------------------------------------
 // Dynamic shared memory of the walk kernels: one 32-byte output staging slot per thread.
-inline size_t stage_bytes(int threads) { return (size_t)threads * 32; }
+inline size_t stage_bytes(int threads) { return (size_t)threads * kLaneSharedBytes; }
 
 template <class K>
 int occupancy_blocks(K kernel, int threads) {

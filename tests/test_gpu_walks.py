@@ -127,6 +127,34 @@ def test_exact_fallback_paths(cap):
     check_parity(csr, None, 15, 20, 0.5, 2.0, seed=4, undirected=False, graph=g)
 
 
+@pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
+def test_work_counters_match_the_oracle(weighted):
+    """Transitions, proposals drawn and fallback steps are the oracle's counts
+    exactly (the kernel takes the same decisions); proposals whose entry was
+    read are a subset of those drawn, and strictly fewer once returns or the
+    larger non-return threshold let the kernel decide without a read."""
+    csr = rmat12(weighted)
+    g = Graph.from_csr(csr)
+    og = oracle.Graph(*csr.numpy())
+    cap = g.get_tuning().trial_cap
+    g.counters(enable=True)
+    try:
+        for (p, q) in [(1.0, 1.0), (0.5, 2.0), (0.25, 1.0), (4.0, 0.25)]:
+            walks(g, None, 20, 2, p, q, 17)
+            c = g.counters()
+            st = oracle.OracleStats()
+            _, rc = oracle.walks(og, None, 20, 2, p, q, 17, trial_cap=cap, stats=st)
+            assert rc == 0
+            assert (c["steps"], c["trials"], c["fallbacks"]) == (st.steps, st.trials, st.fallbacks)
+            assert c["walks"] == 2 * csr.num_nodes
+            assert c["gathers"] <= c["trials"]
+            if p < min(1.0, q):
+                # half or more of the non-return proposals fail 1/(p amax)
+                assert c["gathers"] < 0.75 * c["trials"]
+    finally:
+        g.counters(enable=False)
+
+
 @pytest.mark.parametrize("walk_len", [1, 2, 3, 5, 33])
 @pytest.mark.parametrize("wpn", [1, 3])
 def test_ragged_lengths_and_counts(walk_len, wpn):
