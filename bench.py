@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import dataclasses
 import hashlib
 import glob
 import json
@@ -50,6 +51,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="rmat20w", choices=["er1k", "rmat20w", "rmat22", "rmat24"])
     ap.add_argument("--mode", choices=["walks", "serve"], default="walks")
+    ap.add_argument("--walks-per-node", type=int, default=0,
+                    help="override the workload's walks per node (a smaller case of the same "
+                         "graph, for profiling); 0 keeps the workload's own")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -277,6 +281,8 @@ def run_ours(args, dist):
     dev = torch.device("cuda", dist.local)
     spec = synth.WORKLOADS[args.workload]
     job = spec["job"]
+    if args.walks_per_node > 0:
+        job = dataclasses.replace(job, walks_per_node=args.walks_per_node)
     csr = synth.workload_graph(args.workload, device=dev)
     g = Graph.from_csr(csr, validate=False, device=dev)
     lib = g._lib

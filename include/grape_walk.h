@@ -302,7 +302,9 @@ typedef struct grape_server grape_server_t;
 typedef struct grape_server_config {
     int64_t output_cap_bytes;   /* device bytes for admitted requests' rows and starts (e.g. 40 GB) */
     int32_t max_inflight;       /* requests admitted at once (ring slots), <= 65536 */
-    int32_t chunk_walks;        /* walks per work-queue entry (0 = graph tuning) */
+    int32_t chunk_walks;        /* walks per work-queue entry; 0 = per request: the graph's
+                                   tuned size, raised for a large request so that its
+                                   entries give each resident lane up to 16 walks */
     int64_t max_chunks;         /* capacity of the device work queue, in entries */
     int64_t idle_exit_us;       /* the resident kernel is stopped once the server has had nothing
                                    in flight for this long (relaunched with the next request) */

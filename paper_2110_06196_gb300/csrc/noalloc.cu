@@ -52,12 +52,12 @@ struct StaticQueueFeed {
     int cur_req;
     bool drained;
 
-    __device__ __forceinline__ unsigned long long seed(const Lane& L) const { return L.seed; }
-    __device__ __forceinline__ int len(const Lane& L) const { return L.len; }
-    __device__ __forceinline__ unsigned tm1_ret(const Lane& L) const { return L.tm1_ret; }
-    __device__ __forceinline__ unsigned tm1_in(const Lane& L) const { return L.tm1_in; }
-    __device__ __forceinline__ unsigned tm1_out(const Lane& L) const { return L.tm1_out; }
-    __device__ __forceinline__ int* row(const Lane& L) const { return L.row; }
+    __device__ __forceinline__ unsigned long long seed(const Lane&) const { return wrec()->seed; }
+    __device__ __forceinline__ int len(const Lane&) const { return wrec()->len; }
+    __device__ __forceinline__ unsigned tm1_ret(const Lane&) const { return wrec()->tm1_ret; }
+    __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wrec()->tm1_in; }
+    __device__ __forceinline__ unsigned tm1_out(const Lane&) const { return wrec()->tm1_out; }
+    __device__ __forceinline__ int* row(const Lane&) const { return wrec()->row; }
 
     template <class C>
     __device__ __forceinline__ void finish(int, C& cnt) { cnt.add(C_WALKS); }
@@ -111,7 +111,8 @@ struct StaticQueueFeed {
             const int give = n_need < cur_left ? n_need : cur_left;
             if (!have && rank < give) {
                 have = begin_walk(g, sc->reqs[cur_req], cur_req, cur_lo + rank, L);
-                if (!have) finish(cur_req, cnt);
+                if (have) set_wrec(sc->reqs[cur_req], cur_lo + rank);
+                else finish(cur_req, cnt);
             }
             cur_lo += give;
             cur_left -= give;
@@ -121,7 +122,7 @@ struct StaticQueueFeed {
 };
 
 template <bool W>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks, int num_reqs,
                     int chunk_walks, unsigned trial_cap, int shorter_min, int interp_search) {
     StaticQueueFeed f;

@@ -101,6 +101,7 @@ struct Req {
     int slot = -1;
     uint64_t first_chunk = 0;
     uint64_t num_chunks = 0;
+    int chunk = 0;                  // walks per queue entry of this request
     St st = St::Pending;
     bool cancel = false;
     bool retired = false;
@@ -112,11 +113,15 @@ struct Req {
 
 }  // namespace
 
+// Queue entries staged in pinned host memory per copy (4 MiB).
+constexpr int64_t kChunkStage = 1 << 18;
+
 struct grape_server {
     const grape_graph* g = nullptr;
     grape_server_config_t cfg{};
     grape_tuning_t tuning{};
-    int chunk_walks = 64;
+    int chunk_walks = 64;              // 0: chosen per request (chunk_for)
+    int resident_warps = 1;            // warps of one resident-kernel launch
 
     // device state
     char* arena_base = nullptr;
@@ -127,6 +132,9 @@ struct grape_server {
     int* d_exit = nullptr;
     unsigned* h_flags = nullptr;           // mapped host memory
     unsigned* d_flags = nullptr;           // its device address
+    WalkConst* h_wc = nullptr;             // pinned staging of request descriptors, per slot
+    Chunk* h_chunks = nullptr;             // pinned staging of queue entries (driver thread)
+    size_t h_chunks_cap = 0;               // min(max_chunks, kChunkStage)
     cudaStream_t compute = nullptr, copy = nullptr, ctl = nullptr;
     cudaEvent_t kernel_done = nullptr;
     bool kernel_launched = false;
@@ -141,6 +149,8 @@ struct grape_server {
     std::unordered_map<uint64_t, std::shared_ptr<Req>> live;   // not yet retired
     std::vector<std::shared_ptr<Req>> by_slot;
     std::vector<int> free_slots;
+    std::vector<int> active;          // slots in use, in no particular order
+    std::vector<int> active_pos;      // slot -> index in active, or -1
     std::deque<uint64_t> finished;    // completed, not retired (for wait_any)
     uint64_t next_ticket = 1;
     uint64_t tail = 0;                // queue entries published
@@ -153,20 +163,38 @@ struct grape_server {
     bool admit_locked(const std::shared_ptr<Req>& q);
     grape_status_t publish(const std::vector<std::shared_ptr<Req>>& reqs);
     uint64_t oldest_live_chunk_locked() const;
+    int chunk_for(int64_t num_walks) const;
     // q is taken by value: callers may pass an element of by_slot, which this resets.
     void finish_locked(std::shared_ptr<Req> q, St st, grape_status_t res);
 };
 
 uint64_t grape_server::oldest_live_chunk_locked() const {
     uint64_t oldest = tail;
-    for (const auto& q : by_slot)
+    for (const int slot : active) {
+        const auto& q = by_slot[(size_t)slot];
         if (q && q->first_chunk < oldest) oldest = q->first_chunk;
+    }
     return oldest;
+}
+
+// Walks per queue entry for a request of num_walks walks: the configured size,
+// or (configured 0) the graph's tuned size raised so that the request's
+// entries give each resident lane up to 16 walks: a large request is then cut
+// into about one entry per resident warp instead of thousands of small ones.
+int grape_server::chunk_for(int64_t num_walks) const {
+    if (chunk_walks > 0) return chunk_walks;
+    const int64_t lanes = 32LL * resident_warps;
+    int64_t per_lane = (num_walks + lanes - 1) / lanes;
+    if (per_lane < 1) per_lane = 1;
+    if (per_lane > 16) per_lane = 16;
+    const int64_t c = 32 * per_lane;
+    return (int)std::max<int64_t>(c, tuning.chunk_walks);
 }
 
 bool grape_server::admit_locked(const std::shared_ptr<Req>& q) {
     if (free_slots.empty()) return false;
-    const uint64_t nch = (uint64_t)((q->num_walks + chunk_walks - 1) / chunk_walks);
+    const int chunk = chunk_for(q->num_walks);
+    const uint64_t nch = (uint64_t)((q->num_walks + chunk - 1) / chunk);
     const uint64_t used = tail - oldest_live_chunk_locked();
     if (used + nch > (uint64_t)cfg.max_chunks) return false;
     int64_t off = 0;
@@ -176,8 +204,11 @@ bool grape_server::admit_locked(const std::shared_ptr<Req>& q) {
     free_slots.pop_back();
     q->first_chunk = tail;
     q->num_chunks = nch;
+    q->chunk = chunk;
     tail += nch;
     by_slot[q->slot] = q;
+    active_pos[(size_t)q->slot] = (int)active.size();
+    active.push_back(q->slot);
     q->st = St::Admitted;
     q->t_admit = now_ns();
     q->inflight = true;
@@ -189,9 +220,31 @@ bool grape_server::admit_locked(const std::shared_ptr<Req>& q) {
 
 grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& reqs) {
     // Descriptors, starts and queue entries first, the new tail last, all on one
-    // stream, so a worker that sees the tail also sees what it covers.
-    std::vector<Chunk> chunks;
+    // stream, so a worker that sees the tail also sees what it covers.  The
+    // descriptors and entries are staged in pinned memory allocated with the
+    // server (no allocation here: freeing or allocating pinned memory may
+    // synchronise the device, and the resident kernel may be waiting for
+    // exactly this work).  A full entry stage is copied out and waited for on
+    // the control stream before it is refilled.
+    if (reqs.empty()) return GRAPE_OK;
+    const uint64_t ring = (uint64_t)cfg.max_chunks;
+    uint64_t pos = reqs.front()->first_chunk;     // ring position of the first staged entry
+    size_t nstaged = 0;
     cudaError_t e = cudaSuccess;
+    auto flush = [&]() -> cudaError_t {
+        size_t i = 0;
+        while (i < nstaged) {
+            const uint64_t slot = pos % ring;
+            const size_t n = (size_t)std::min<uint64_t>(nstaged - i, ring - slot);
+            const cudaError_t ec = cudaMemcpyAsync(d_chunks + slot, h_chunks + i,
+                                                   sizeof(Chunk) * n, cudaMemcpyHostToDevice, ctl);
+            if (ec != cudaSuccess) return ec;
+            i += n;
+            pos += n;
+        }
+        nstaged = 0;
+        return cudaStreamSynchronize(ctl);
+    };
     uint64_t new_tail = 0;
     for (const auto& q : reqs) {
         char* base = arena_base + q->arena_off;
@@ -202,41 +255,29 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
                                 cudaMemcpyHostToDevice, ctl);
             if (e != cudaSuccess) return cuda_status(e);
         }
-        WalkConst wc;
+        WalkConst* wc = h_wc + q->slot;
         grape_status_t st = make_walk_const(g, d_starts, q->r.num_starts, q->r.walk_len,
                                             q->r.walks_per_node, q->r.p, q->r.q, q->r.seed,
-                                            reinterpret_cast<int32_t*>(base), &wc);
+                                            reinterpret_cast<int32_t*>(base), wc);
         if (st != GRAPE_OK) return st;
         h_flags[q->slot] = 0u;
-        e = cudaMemcpyAsync(d_reqs + q->slot, &wc, sizeof(wc), cudaMemcpyHostToDevice, ctl);
+        e = cudaMemcpyAsync(d_reqs + q->slot, wc, sizeof(WalkConst), cudaMemcpyHostToDevice, ctl);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_done + q->slot, 0, sizeof(unsigned long long), ctl);
         if (e != cudaSuccess) return cuda_status(e);
-        // the WalkConst lives on this stack frame: wait for it before reuse
-        e = cudaStreamSynchronize(ctl);
-        if (e != cudaSuccess) return cuda_status(e);
         for (uint64_t c = 0; c < q->num_chunks; ++c) {
-            Chunk ch;
-            ch.walk_lo = (long long)(c * (uint64_t)chunk_walks);
-            ch.count = (int)std::min<int64_t>(chunk_walks, q->num_walks - ch.walk_lo);
+            if (nstaged == h_chunks_cap) {
+                e = flush();
+                if (e != cudaSuccess) return cuda_status(e);
+            }
+            Chunk& ch = h_chunks[nstaged++];
+            ch.walk_lo = (long long)(c * (uint64_t)q->chunk);
+            ch.count = (int)std::min<int64_t>(q->chunk, q->num_walks - ch.walk_lo);
             ch.req = q->slot;
-            chunks.push_back(ch);
         }
         new_tail = q->first_chunk + q->num_chunks;
     }
-    if (reqs.empty()) return GRAPE_OK;
-    // Copy entries into the ring (possibly wrapping).
-    const uint64_t ring = (uint64_t)cfg.max_chunks;
-    uint64_t pos = reqs.front()->first_chunk;
-    size_t i = 0;
-    while (i < chunks.size()) {
-        const uint64_t slot = pos % ring;
-        const size_t n = (size_t)std::min<uint64_t>(chunks.size() - i, ring - slot);
-        e = cudaMemcpyAsync(d_chunks + slot, chunks.data() + i, sizeof(Chunk) * n,
-                            cudaMemcpyHostToDevice, ctl);
-        if (e != cudaSuccess) return cuda_status(e);
-        i += n;
-        pos += n;
-    }
+    e = flush();
+    if (e != cudaSuccess) return cuda_status(e);
     static thread_local unsigned long long tail_host;
     tail_host = new_tail;
     e = cudaMemcpyAsync(d_ctl + 1, &tail_host, sizeof(tail_host), cudaMemcpyHostToDevice, ctl);
@@ -252,6 +293,14 @@ void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t r
     if (q->slot >= 0) {
         by_slot[q->slot].reset();
         free_slots.push_back(q->slot);
+        const int i = active_pos[(size_t)q->slot];
+        if (i >= 0) {
+            const int last = active.back();
+            active[(size_t)i] = last;
+            active_pos[(size_t)last] = i;
+            active.pop_back();
+            active_pos[(size_t)q->slot] = -1;
+        }
         q->slot = -1;
     }
     if (q->inflight) {
@@ -359,17 +408,19 @@ void grape_server::run() {
                     kernel_launched = true;
                     stats.kernel_launches++;
                 } else {
-                    const auto snapshot = by_slot;
-                    for (const auto& q : snapshot)
-                        if (q) finish_locked(q, St::Failed, GRAPE_ERR_CUDA);
+                    const std::vector<int> snapshot = active;   // finish_locked edits active
+                    for (const int slot : snapshot)
+                        if (by_slot[(size_t)slot])
+                            finish_locked(by_slot[(size_t)slot], St::Failed, GRAPE_ERR_CUDA);
                 }
             }
         }
         // Completions: flag -> copy out -> done.
         {
             std::lock_guard<std::mutex> lk(mu);
-            const auto snapshot = by_slot;       // finish_locked edits by_slot
-            for (const auto& q : snapshot) {
+            const std::vector<int> snapshot = active;   // finish_locked edits active
+            for (const int slot : snapshot) {
+                const std::shared_ptr<Req> q = by_slot[(size_t)slot];
                 if (!q) continue;
                 if (q->st == St::Admitted && ((volatile unsigned*)h_flags)[q->slot] != 0u) {
                     busy = true;
@@ -436,10 +487,16 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     s->g = g;
     s->cfg = *cfg;
     grape_graph_get_tuning(g, &s->tuning);
-    s->chunk_walks = cfg->chunk_walks > 0 ? cfg->chunk_walks : s->tuning.chunk_walks;
+    s->chunk_walks = cfg->chunk_walks;
+    {
+        const LaunchShape ls = queue_launch_shape(g, s->tuning, g->weighted);
+        s->resident_warps = std::max(1, ls.blocks * (ls.threads / 32));
+    }
     s->arena.reset(new Arena(cfg->output_cap_bytes));
     const int slots = cfg->max_inflight;
     s->by_slot.resize((size_t)slots);
+    s->active_pos.assign((size_t)slots, -1);
+    s->active.reserve((size_t)slots);
     for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = cudaMalloc(&s->arena_base, (size_t)cfg->output_cap_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_reqs, sizeof(WalkConst) * (size_t)slots);
@@ -450,6 +507,12 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     if (e == cudaSuccess)
         e = cudaHostAlloc(&s->h_flags, sizeof(unsigned) * (size_t)slots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->d_flags, s->h_flags, 0);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&s->h_wc, sizeof(WalkConst) * (size_t)slots, cudaHostAllocDefault);
+    if (e == cudaSuccess) {
+        s->h_chunks_cap = (size_t)std::min<int64_t>(cfg->max_chunks, kChunkStage);
+        e = cudaHostAlloc(&s->h_chunks, sizeof(Chunk) * s->h_chunks_cap, cudaHostAllocDefault);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking);
@@ -611,6 +674,8 @@ void grape_walk_server_destroy(grape_server_t* s) {
     if (s->copy) cudaStreamDestroy(s->copy);
     if (s->ctl) cudaStreamDestroy(s->ctl);
     if (s->h_flags) cudaFreeHost(s->h_flags);
+    if (s->h_wc) cudaFreeHost(s->h_wc);
+    if (s->h_chunks) cudaFreeHost(s->h_chunks);
     cudaFree(s->arena_base);
     cudaFree(s->d_reqs);
     cudaFree(s->d_done);

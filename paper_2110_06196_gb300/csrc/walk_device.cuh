@@ -154,12 +154,8 @@ constexpr int kDrawsPerIter = 2;
 struct Lane {
     long long w;          // walk id (Philox counter words 0-1)
     long long off_v;
-    int* row;             // this walk's output row (batched / served)
-    unsigned long long seed;
-    unsigned tm1_ret, tm1_in, tm1_out;
     unsigned k;           // trial index within the step
     int s;                // index of the entry being produced (1 .. len-1)
-    int len;
     int v, t;             // current and previous node (t < 0 on the first step)
     int deg_v;
     float wmax_v;
@@ -220,9 +216,19 @@ struct __align__(16) TRec {
     int pad[2];
 };
 
+// The constants of the request a lane's walk belongs to (batched and served
+// launches, where lanes of one warp may serve different requests).  Kept in
+// shared memory instead of registers.
+struct __align__(16) WRec {
+    unsigned long long seed;
+    int* row;             // this walk's output row
+    unsigned tm1_ret, tm1_in, tm1_out;
+    int len;
+};
+
 // Dynamic shared memory per lane: a 32-byte output staging slot, the 32-byte
-// entry of the proposal under a membership search, and the lane's TRec.
-constexpr int kLaneSharedBytes = 96;
+// entry of the proposal under a membership search, the lane's TRec and its WRec.
+constexpr int kLaneSharedBytes = 128;
 
 // Row writer.  Each lane stages its row's entries in its own 32-byte slot of
 // shared memory; when an entry completes a 32-byte sector that lies inside the
@@ -242,6 +248,11 @@ __device__ __forceinline__ int4* parked_entry() {
 __device__ __forceinline__ TRec* trec() {
     extern __shared__ int4 stage_words[];
     return reinterpret_cast<TRec*>(stage_words + 4 * blockDim.x) + threadIdx.x;
+}
+
+__device__ __forceinline__ WRec* wrec() {
+    extern __shared__ int4 stage_words[];
+    return reinterpret_cast<WRec*>(stage_words + 6 * blockDim.x) + threadIdx.x;
 }
 
 __device__ __forceinline__ void put(const Lane& L, int* row, int s, int val, int len) {
@@ -389,24 +400,19 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
 __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& wc, int req,
                                            long long row, Lane& L) {
     const long long w = wc.walk_base + row;
+    int* const rowp = wc.out + row * (long long)wc.walk_len;
     L.w = w;
     L.req = req;
-    L.row = wc.out + row * (long long)wc.walk_len;
-    L.len = wc.walk_len;
-    L.seed = wc.seed;
-    L.tm1_ret = wc.tm1_ret;
-    L.tm1_in = wc.tm1_in;
-    L.tm1_out = wc.tm1_out;
     L.flags = (wc.out_vec ? F_VEC : 0u) |
               ((unsigned)((row * (long long)wc.walk_len) & 7) << F_PHASE_SHIFT);
     const long long i = w % wc.num_starts;
     const long long v0 = wc.starts ? (long long)__ldg(wc.starts + i) : i;
     if (v0 < 0 || v0 >= g.n) {
         atomicOr(g.status, 1);
-        fill_dead(L, L.row, 0, wc.walk_len);
+        fill_dead(L, rowp, 0, wc.walk_len);
         return false;
     }
-    put(L, L.row, 0, (int)v0, wc.walk_len);
+    put(L, rowp, 0, (int)v0, wc.walk_len);
     const NodeRec r = load_rec(g, (int)v0);
     L.v = (int)v0;
     L.t = -1;
@@ -420,7 +426,7 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.flags &= ~(F_KEY_T | F_ACC_IN | F_ACC_OUT | F_BISECT);
     if (wc.walk_len <= 1) return false;
     if (r.deg == 0) {
-        fill_dead(L, L.row, 1, wc.walk_len);
+        fill_dead(L, rowp, 1, wc.walk_len);
         return false;
     }
     return true;
@@ -442,6 +448,18 @@ __device__ __forceinline__ void flush_counts(const GraphDev& g, Counts<true>& c)
 // ---------------------------------------------------------------------------
 // Walk sources
 // ---------------------------------------------------------------------------
+
+// Record the request constants of row `row` of wc for this lane (queue feeds).
+__device__ __forceinline__ void set_wrec(const WalkConst& wc, long long row) {
+    WRec r;
+    r.seed = wc.seed;
+    r.row = wc.out + row * (long long)wc.walk_len;
+    r.tm1_ret = wc.tm1_ret;
+    r.tm1_in = wc.tm1_in;
+    r.tm1_out = wc.tm1_out;
+    r.len = wc.walk_len;
+    *wrec() = r;
+}
 
 // Per call: lane j of the grid takes walks j, j + stride, j + 2 * stride, ...
 struct GridFeed {
@@ -522,12 +540,12 @@ struct QueueFeed {
     bool drained;
 
     // Per-request constants differ between lanes: held in the lane.
-    __device__ __forceinline__ unsigned long long seed(const Lane& L) const { return L.seed; }
-    __device__ __forceinline__ int len(const Lane& L) const { return L.len; }
-    __device__ __forceinline__ unsigned tm1_ret(const Lane& L) const { return L.tm1_ret; }
-    __device__ __forceinline__ unsigned tm1_in(const Lane& L) const { return L.tm1_in; }
-    __device__ __forceinline__ unsigned tm1_out(const Lane& L) const { return L.tm1_out; }
-    __device__ __forceinline__ int* row(const Lane& L) const { return L.row; }
+    __device__ __forceinline__ unsigned long long seed(const Lane&) const { return wrec()->seed; }
+    __device__ __forceinline__ int len(const Lane&) const { return wrec()->len; }
+    __device__ __forceinline__ unsigned tm1_ret(const Lane&) const { return wrec()->tm1_ret; }
+    __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wrec()->tm1_in; }
+    __device__ __forceinline__ unsigned tm1_out(const Lane&) const { return wrec()->tm1_out; }
+    __device__ __forceinline__ int* row(const Lane&) const { return wrec()->row; }
 
     template <class C>
     __device__ __forceinline__ void finish(int req, C& cnt) {
@@ -647,7 +665,8 @@ struct QueueFeed {
             if (!have && rank < give) {
                 const WalkConst wc = load_walkconst(reqs + cur_req);
                 have = begin_walk(g, wc, cur_req, cur_lo + rank, L);
-                if (!have) finish(cur_req, cnt);
+                if (have) set_wrec(wc, cur_lo + rank);
+                else finish(cur_req, cnt);
             }
             cur_lo += give;
             cur_left -= give;

@@ -19,7 +19,7 @@ constexpr int kMaxThreads = 256;
 // more independent gathers in flight, which is what this latency-bound loop
 // needs (4 x 256 threads -> at most 64 registers per thread).
 constexpr int kMinBlocksWalk = 4;
-constexpr int kMinBlocksQueue = 3;
+constexpr int kMinBlocksQueue = 4;
 
 // ---------------------------------------------------------------------------
 // Kernels

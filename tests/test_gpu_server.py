@@ -152,3 +152,26 @@ def test_concurrent_submitters(graph):
     assert not errors
     for (k, j), (s, rows) in results.items():
         assert np.array_equal(rows, _alone(g, s, 25, 1.0, 0.5, 1000 * k + j))
+
+
+def test_burst_larger_than_the_entry_stage_keeps_one_kernel(graph):
+    """One burst whose queue entries exceed the host staging of a single copy
+    (2^18 entries): the server publishes it in pieces without synchronising the
+    device, so the resident kernel never runs out of work and is launched
+    once; rows equal the requests run alone."""
+    csr, g = graph
+    rng = np.random.default_rng(12)
+    reqs = [(rng.integers(0, csr.num_nodes, n).astype(np.int32), 6, 0.5, 2.0, 100 + j)
+            for j, n in enumerate((300000, 5000, 70000))]
+    srv = Server(g, output_cap_bytes=1 << 30, max_inflight=16, chunk_walks=1,
+                 max_chunks=1 << 20, idle_exit_us=200000)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(st, L, p, q, seed) for (st, L, p, q, seed) in reqs]
+    got = [srv.wait(t, timeout_ms=60000) for t in tickets]
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    assert st["kernel_launches"] == 1, st
+    assert elapsed < 1.5, elapsed        # the kernel's idle bound is about 2 s
+    for (starts, L, p, q, seed), rows in zip(reqs, got):
+        assert np.array_equal(rows, _alone(g, starts, L, p, q, seed))
