@@ -117,6 +117,14 @@ __device__ __forceinline__ uint4 trial_block(unsigned long long seed, long long 
                          make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
 }
 
+// floor((hi:lo) * n / 2^64) for n < 2^31: the high word of a 64 x 32-bit
+// product, from two 32 x 32 -> 64 products (exact: the sum stays below 2^64).
+__device__ __forceinline__ int scale_index(unsigned lo, unsigned hi, int n) {
+    const unsigned long long a = (unsigned long long)lo * (unsigned)n;
+    const unsigned long long b = (unsigned long long)hi * (unsigned)n + (a >> 32);
+    return (int)(b >> 32);
+}
+
 // One 32-byte sector in a single 256-bit read-only load (sm_100 and later):
 // the first 16 bytes to a, the last 16 to b.  p must be 32-byte aligned.
 __device__ __forceinline__ void ld_sector(const void* p, int4& a, int4& b) {
@@ -311,7 +319,7 @@ __device__ __forceinline__ bool weighted_accept(unsigned r2, float wmax, unsigne
     const unsigned long long m2 = (b2 & 0x7fffffu) | (e2 ? 0x800000u : 0u);
     const int d = (int)(e1 ? e1 : 1u) - (int)(e2 ? e2 : 1u);   // >= 0 since w <= wmax
     const unsigned long long lhs = (unsigned long long)r2 * m1;        // < 2^56
-    const unsigned long long rhs = ((unsigned long long)tm1 + 1ull) * m2;  // <= 2^56
+    const unsigned long long rhs = (unsigned long long)tm1 * m2 + m2;      // (tm1 + 1) m2 <= 2^56
     if (lhs == 0) return rhs != 0;
     if (d >= 64) return false;
     if (d > 0 && (lhs >> (64 - d)) != 0) return false;
@@ -329,8 +337,8 @@ __device__ __forceinline__ void weighted_accept2(unsigned r2, float wmax, unsign
     const unsigned long long m2 = (b2 & 0x7fffffu) | (e2 ? 0x800000u : 0u);
     const int d = (int)(e1 ? e1 : 1u) - (int)(e2 ? e2 : 1u);
     const unsigned long long lhs = (unsigned long long)r2 * m1;
-    const unsigned long long rhs_a = ((unsigned long long)tm1_a + 1ull) * m2;
-    const unsigned long long rhs_b = ((unsigned long long)tm1_b + 1ull) * m2;
+    const unsigned long long rhs_a = (unsigned long long)tm1_a * m2 + m2;
+    const unsigned long long rhs_b = (unsigned long long)tm1_b * m2 + m2;
     if (lhs == 0) {
         acc_a = rhs_a != 0;
         acc_b = rhs_b != 0;
@@ -915,8 +923,7 @@ struct Engine {
                     if (!fallback_steps(L)) return false;
                 }
                 const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
-                const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
-                const int idx = (int)__umul64hi(r64, (unsigned long long)L.deg_v);
+                const int idx = scale_index(r.x, r.y, L.deg_v);
                 cnt.add(C_TRIALS);
                 if (L.t >= 0) {
                     if (idx == L.rt) {
