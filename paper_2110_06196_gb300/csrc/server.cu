@@ -128,11 +128,14 @@ struct grape_server {
     WalkConst* d_reqs = nullptr;
     unsigned long long* d_done = nullptr;
     Chunk* d_chunks = nullptr;
-    unsigned long long* d_ctl = nullptr;   // [0] head, [1] tail
+    unsigned long long* d_ctl = nullptr;   // [0] head (next ticket), [1] tail, [2] heartbeat
     int* d_exit = nullptr;
     unsigned* h_flags = nullptr;           // mapped host memory
     unsigned* d_flags = nullptr;           // its device address
     WalkConst* h_wc = nullptr;             // pinned staging of request descriptors, per slot
+    unsigned long long* h_tail = nullptr;  // pinned queue-tail values, per slot
+    unsigned long long* h_misc = nullptr;  // pinned: [0] head at launch, [1] heartbeat
+    uint64_t pub_tail = 0;                 // queue entries published to the device
     Chunk* h_chunks = nullptr;             // pinned staging of queue entries (driver thread)
     size_t h_chunks_cap = 0;               // min(max_chunks, kChunkStage)
     cudaStream_t compute = nullptr, copy = nullptr, ctl = nullptr;
@@ -166,6 +169,7 @@ struct grape_server {
     int chunk_for(int64_t num_walks) const;
     // q is taken by value: callers may pass an element of by_slot, which this resets.
     void finish_locked(std::shared_ptr<Req> q, St st, grape_status_t res);
+    void release_slot_locked(Req& q);
 };
 
 uint64_t grape_server::oldest_live_chunk_locked() const {
@@ -219,33 +223,32 @@ bool grape_server::admit_locked(const std::shared_ptr<Req>& q) {
 }
 
 grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& reqs) {
-    // Descriptors, starts and queue entries first, the new tail last, all on one
-    // stream, so a worker that sees the tail also sees what it covers.  The
-    // descriptors and entries are staged in pinned memory allocated with the
-    // server (no allocation here: freeing or allocating pinned memory may
-    // synchronise the device, and the resident kernel may be waiting for
-    // exactly this work).  A full entry stage is copied out and waited for on
-    // the control stream before it is refilled.
+    // Per request: its descriptor, starts and queue entries, then the tail
+    // that covers them, all on one stream, so a worker that sees a tail also
+    // sees what it covers, and the resident kernel starts on the first request
+    // while later ones are still being copied.  Descriptors, entries and tail
+    // values are staged in pinned memory allocated with the server (no
+    // allocation here: freeing or allocating pinned memory may synchronise the
+    // device, and the resident kernel may be waiting for exactly this work).
+    // A full entry stage is waited for on the control stream before reuse.
     if (reqs.empty()) return GRAPE_OK;
     const uint64_t ring = (uint64_t)cfg.max_chunks;
     uint64_t pos = reqs.front()->first_chunk;     // ring position of the first staged entry
-    size_t nstaged = 0;
+    size_t nstaged = 0;       // entries in the stage
+    size_t ncopied = 0;       // of which already enqueued for copy
     cudaError_t e = cudaSuccess;
-    auto flush = [&]() -> cudaError_t {
-        size_t i = 0;
-        while (i < nstaged) {
+    auto copy_staged = [&]() -> cudaError_t {
+        while (ncopied < nstaged) {
             const uint64_t slot = pos % ring;
-            const size_t n = (size_t)std::min<uint64_t>(nstaged - i, ring - slot);
-            const cudaError_t ec = cudaMemcpyAsync(d_chunks + slot, h_chunks + i,
+            const size_t n = (size_t)std::min<uint64_t>(nstaged - ncopied, ring - slot);
+            const cudaError_t ec = cudaMemcpyAsync(d_chunks + slot, h_chunks + ncopied,
                                                    sizeof(Chunk) * n, cudaMemcpyHostToDevice, ctl);
             if (ec != cudaSuccess) return ec;
-            i += n;
+            ncopied += n;
             pos += n;
         }
-        nstaged = 0;
-        return cudaStreamSynchronize(ctl);
+        return cudaSuccess;
     };
-    uint64_t new_tail = 0;
     for (const auto& q : reqs) {
         char* base = arena_base + q->arena_off;
         int32_t* d_starts = nullptr;
@@ -266,23 +269,43 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
         if (e != cudaSuccess) return cuda_status(e);
         for (uint64_t c = 0; c < q->num_chunks; ++c) {
             if (nstaged == h_chunks_cap) {
-                e = flush();
+                e = copy_staged();
+                if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
                 if (e != cudaSuccess) return cuda_status(e);
+                nstaged = ncopied = 0;
             }
             Chunk& ch = h_chunks[nstaged++];
             ch.walk_lo = (long long)(c * (uint64_t)q->chunk);
             ch.count = (int)std::min<int64_t>(q->chunk, q->num_walks - ch.walk_lo);
             ch.req = q->slot;
         }
-        new_tail = q->first_chunk + q->num_chunks;
+        e = copy_staged();
+        if (e != cudaSuccess) return cuda_status(e);
+        h_tail[q->slot] = q->first_chunk + q->num_chunks;
+        e = cudaMemcpyAsync(d_ctl + 1, h_tail + q->slot, sizeof(unsigned long long),
+                            cudaMemcpyHostToDevice, ctl);
+        if (e != cudaSuccess) return cuda_status(e);
+        pub_tail = h_tail[q->slot];
     }
-    e = flush();
-    if (e != cudaSuccess) return cuda_status(e);
-    static thread_local unsigned long long tail_host;
-    tail_host = new_tail;
-    e = cudaMemcpyAsync(d_ctl + 1, &tail_host, sizeof(tail_host), cudaMemcpyHostToDevice, ctl);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
+    e = cudaStreamSynchronize(ctl);
     return cuda_status(e);
+}
+
+// Return q's slot to the free list and drop it from the active list.
+void grape_server::release_slot_locked(Req& q) {
+    if (q.slot < 0) return;
+    const size_t slot = (size_t)q.slot;
+    by_slot[slot].reset();
+    free_slots.push_back(q.slot);
+    const int i = active_pos[slot];
+    if (i >= 0) {
+        const int last = active.back();
+        active[(size_t)i] = last;
+        active_pos[(size_t)last] = i;
+        active.pop_back();
+        active_pos[slot] = -1;
+    }
+    q.slot = -1;
 }
 
 void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t res) {
@@ -290,19 +313,7 @@ void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t r
         arena->release(q->arena_off, q->alloc_bytes);
         q->arena_off = -1;
     }
-    if (q->slot >= 0) {
-        by_slot[q->slot].reset();
-        free_slots.push_back(q->slot);
-        const int i = active_pos[(size_t)q->slot];
-        if (i >= 0) {
-            const int last = active.back();
-            active[(size_t)i] = last;
-            active_pos[(size_t)last] = i;
-            active.pop_back();
-            active_pos[(size_t)q->slot] = -1;
-        }
-        q->slot = -1;
-    }
+    release_slot_locked(*q);
     if (q->inflight) {
         q->inflight = false;
         stats.inflight--;
@@ -330,7 +341,7 @@ void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t r
 // safety bound of about two seconds of polling for the case that the host
 // never raises the flag.
 void grape_server::run() {
-    const long long idle_spins = 2000000;   // ~2 s of 1 us sleeps per idle warp
+    const long long idle_spins = 2000000;   // an idle warp sleeps about 2 s in total before leaving
     auto set_exit = [&](int v) {
         static thread_local int word;
         word = v;
@@ -338,6 +349,42 @@ void grape_server::run() {
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
         return e;
     };
+    // Launch the resident kernel unless one is running.
+    // Entries are only ever published to a kernel that will take them: once
+    // the exit flag is raised (with nothing in flight), the kernel is let go
+    // before anything new is published.  The queue head is a ticket counter
+    // that waiting warps may have run past the tail; when no kernel runs every
+    // published entry has been taken, so the next kernel starts its tickets at
+    // the published tail.
+    auto ensure_kernel = [&]() {
+        if (kernel_launched && cudaEventQuery(kernel_done) == cudaErrorNotReady) {
+            if (!exit_raised) return;            // running, and staying
+            cudaEventSynchronize(kernel_done);   // leaving: its warps are on their way out
+        }
+        cudaError_t e = exit_raised ? set_exit(0) : cudaSuccess;
+        if (e == cudaSuccess) exit_raised = false;
+        if (e == cudaSuccess) {
+            h_misc[0] = pub_tail;
+            e = cudaMemcpyAsync(d_ctl, h_misc, sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                                compute);
+        }
+        if (e == cudaSuccess)
+            e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl,
+                                    (unsigned long long)cfg.max_chunks, idle_spins, d_exit, d_done,
+                                    d_flags, 0, compute);
+        if (e == cudaSuccess) e = cudaEventRecord(kernel_done, compute);
+        std::lock_guard<std::mutex> lk(mu);
+        if (e == cudaSuccess) {
+            kernel_launched = true;
+            stats.kernel_launches++;
+        } else {
+            const std::vector<int> snapshot = active;   // finish_locked edits active
+            for (const int slot : snapshot)
+                if (by_slot[(size_t)slot])
+                    finish_locked(by_slot[(size_t)slot], St::Failed, GRAPE_ERR_CUDA);
+        }
+    };
+    int64_t last_beat = 0;
     while (true) {
         bool busy = false;
         std::vector<std::shared_ptr<Req>> admitted;
@@ -372,6 +419,9 @@ void grape_server::run() {
         }
         if (!admitted.empty()) {
             busy = true;
+            // a resident kernel first, so it starts on the first request while
+            // later ones are still being published
+            ensure_kernel();
             grape_status_t st = publish(admitted);
             if (st != GRAPE_OK) {
                 std::lock_guard<std::mutex> lk(mu);
@@ -385,6 +435,14 @@ void grape_server::run() {
             inflight = stats.inflight > 0;
         }
         const bool running = kernel_launched && cudaEventQuery(kernel_done) == cudaErrorNotReady;
+        // Heartbeat for the kernel's waiting warps: their bounded wait only runs
+        // out if the host stops beating (about every 100 ms while a kernel runs).
+        if (running && now_ns() - last_beat > 100000000) {
+            last_beat = now_ns();
+            h_misc[1] += 1;
+            cudaMemcpyAsync(d_ctl + 2, h_misc + 1, sizeof(unsigned long long),
+                            cudaMemcpyHostToDevice, ctl);
+        }
         if (!inflight) {
             if (idle_since == 0) idle_since = now_ns();
             if (running && !exit_raised &&
@@ -394,27 +452,7 @@ void grape_server::run() {
         } else {
             idle_since = 0;
         }
-        if (inflight && !running) {
-            {
-                cudaError_t e = exit_raised ? set_exit(0) : cudaSuccess;
-                if (e == cudaSuccess) exit_raised = false;
-                if (e == cudaSuccess)
-                    e = launch_queue_kernel(g, tuning, d_reqs, d_chunks, d_ctl,
-                                            (unsigned long long)cfg.max_chunks, idle_spins,
-                                            d_exit, d_done, d_flags, 0, compute);
-                if (e == cudaSuccess) e = cudaEventRecord(kernel_done, compute);
-                std::lock_guard<std::mutex> lk(mu);
-                if (e == cudaSuccess) {
-                    kernel_launched = true;
-                    stats.kernel_launches++;
-                } else {
-                    const std::vector<int> snapshot = active;   // finish_locked edits active
-                    for (const int slot : snapshot)
-                        if (by_slot[(size_t)slot])
-                            finish_locked(by_slot[(size_t)slot], St::Failed, GRAPE_ERR_CUDA);
-                }
-            }
-        }
+        if (inflight && !running) ensure_kernel();
         // Completions: flag -> copy out -> done.
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -502,13 +540,18 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     if (e == cudaSuccess) e = cudaMalloc(&s->d_reqs, sizeof(WalkConst) * (size_t)slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_done, sizeof(unsigned long long) * (size_t)slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_chunks, sizeof(Chunk) * (size_t)cfg->max_chunks);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_ctl, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ctl, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_exit, sizeof(int));
     if (e == cudaSuccess)
         e = cudaHostAlloc(&s->h_flags, sizeof(unsigned) * (size_t)slots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->d_flags, s->h_flags, 0);
     if (e == cudaSuccess)
         e = cudaHostAlloc(&s->h_wc, sizeof(WalkConst) * (size_t)slots, cudaHostAllocDefault);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&s->h_tail, sizeof(unsigned long long) * (size_t)slots,
+                          cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_misc, sizeof(unsigned long long) * 2, 0);
+    if (e == cudaSuccess) std::memset(s->h_misc, 0, sizeof(unsigned long long) * 2);
     if (e == cudaSuccess) {
         s->h_chunks_cap = (size_t)std::min<int64_t>(cfg->max_chunks, kChunkStage);
         e = cudaHostAlloc(&s->h_chunks, sizeof(Chunk) * s->h_chunks_cap, cudaHostAllocDefault);
@@ -517,7 +560,7 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMemset(s->d_ctl, 0, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMemset(s->d_ctl, 0, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMemset(s->d_exit, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -583,11 +626,7 @@ static grape_status_t retire_locked(grape_server* s, const std::shared_ptr<Req>&
             s->arena->release(q->arena_off, q->alloc_bytes);
             q->arena_off = -1;
         }
-        if (q->slot >= 0) {
-            s->by_slot[q->slot].reset();
-            s->free_slots.push_back(q->slot);
-            q->slot = -1;
-        }
+        s->release_slot_locked(*q);
         s->stats.bytes_reserved = s->arena->used();
         s->cv.notify_all();
     }
@@ -675,6 +714,8 @@ void grape_walk_server_destroy(grape_server_t* s) {
     if (s->ctl) cudaStreamDestroy(s->ctl);
     if (s->h_flags) cudaFreeHost(s->h_flags);
     if (s->h_wc) cudaFreeHost(s->h_wc);
+    if (s->h_tail) cudaFreeHost(s->h_tail);
+    if (s->h_misc) cudaFreeHost(s->h_misc);
     if (s->h_chunks) cudaFreeHost(s->h_chunks);
     cudaFree(s->arena_base);
     cudaFree(s->d_reqs);

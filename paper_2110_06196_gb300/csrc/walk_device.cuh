@@ -221,7 +221,7 @@ struct __align__(16) TRec {
     float wmax_t;
     int jv;               // position of v in N(t)
     float wj;             // weighted: the weight there (t -> v)
-    int pad[2];
+    unsigned long long ticket;   // lane 0 only: the warp's served-queue ticket (QueueFeed)
 };
 
 // The constants of the request a lane's walk belongs to (batched and served
@@ -256,6 +256,14 @@ __device__ __forceinline__ int4* parked_entry() {
 __device__ __forceinline__ TRec* trec() {
     extern __shared__ int4 stage_words[];
     return reinterpret_cast<TRec*>(stage_words + 4 * blockDim.x) + threadIdx.x;
+}
+
+constexpr unsigned long long kNoTicket = ~0ull;
+
+// The warp's pending served-queue ticket, kept by lane 0 in its TRec.
+__device__ __forceinline__ unsigned long long* warp_ticket() {
+    extern __shared__ int4 stage_words[];
+    return &(reinterpret_cast<TRec*>(stage_words + 4 * blockDim.x) + (threadIdx.x & ~31u))->ticket;
 }
 
 __device__ __forceinline__ WRec* wrec() {
@@ -518,23 +526,19 @@ __device__ __forceinline__ WalkConst load_walkconst(const WalkConst* p) {
     return w;
 }
 
-// Served queues take entries with a plain increment while the published tail
-// is more than this many entries ahead of the head.  Between a warp's read of
-// (head, tail) and its increment (about two L2 round trips) every other warp
-// can take at most a couple of entries, and there are at most 152 x 64 warps,
-// so the increment cannot pass the tail.  Should it ever do so anyway, the
-// warp waits (bounded) for the tail to cover its entry and otherwise raises
-// status bit 2.
-constexpr unsigned long long kQueueMargin = 1ull << 16;
+// Iterations a warp with live walks lets pass before polling an empty served
+// queue again (about 10-20 us: far below the latency a request sees anyway).
+constexpr int kIdlePollSkip = 8;
 
 // Batched and served: a warp takes queue entries (one request's walk range) and
-// deals their walks to its lanes as lanes free up.  Served queues advance the
-// head with a compare-and-swap that never passes the published tail, so the
-// queue can keep growing while the kernel runs.
+// deals their walks to its lanes as lanes free up.  Served queues are ticket
+// queues (see take_chunk), so the queue can keep growing while the kernel runs
+// and no warp ever retries a contended compare-and-swap.
 struct QueueFeed {
     const WalkConst* reqs;       // request table (device)
     const Chunk* chunks;         // queue entries (device ring of `ring` entries)
-    unsigned long long* ctl;     // ctl[0] = next entry to take (head), ctl[1] = entries published (tail)
+    unsigned long long* ctl;     // ctl[0] = next ticket (head), ctl[1] = entries published
+                                 // (tail), ctl[2] = the host's heartbeat (served)
     unsigned long long ring;     // ring capacity (entries)
     long long idle_spins;        // served: polls of an empty queue before giving up; 0 batched
     int* exit_flag;              // served: set when the kernel should stop
@@ -545,7 +549,8 @@ struct QueueFeed {
     long long cur_lo;
     int cur_left;
     int cur_req;
-    bool drained;
+    int idle_polls;              // served: iterations to skip before polling an empty queue
+                                 // again; < 0 once the queue is drained for good
 
     // Per-request constants differ between lanes: held in the lane.
     __device__ __forceinline__ unsigned long long seed(const Lane&) const { return wrec()->seed; }
@@ -559,13 +564,14 @@ struct QueueFeed {
     __device__ __forceinline__ void finish(int req, C& cnt) {
         cnt.add(C_WALKS);
         if (done == nullptr) return;                 // batched: nothing to publish
-        // The count is acquire-release: this walk's rows are visible before it
-        // counts, and the walk that completes the request sees every other
-        // walk's rows before it raises the host-visible flag.
+        // Each walk's count is a release: its rows are visible before it counts.
+        // The walk that completes the request adds an acquire fence, so it has
+        // seen every other walk's rows before it raises the host-visible flag.
         const long long nw = __ldcg(&reqs[req].num_walks);
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> c(done[req]);
-        const unsigned long long prev = c.fetch_add(1ull, cuda::memory_order_acq_rel);
+        const unsigned long long prev = c.fetch_add(1ull, cuda::memory_order_release);
         if (prev + 1 == (unsigned long long)nw) {
+            cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
             __threadfence_system();
             *(volatile unsigned*)(done_flags + req) = 1u;
         }
@@ -576,72 +582,87 @@ struct QueueFeed {
     }
 
     // Take one queue entry for the warp (lane 0 decides, then broadcast).
-    // Returns 1 with an entry; 0 when a served queue is empty right now (only
-    // when `wait` is false); -1 when the queue is drained (batched), the server
-    // is shutting down, or a waiting warp stayed idle for idle_spins polls.
-    // Only a warp that holds no walk at all waits: a warp with walks in flight
-    // polls once and carries on, so an empty queue never stalls live walks.
+    // Returns 1 with an entry; 0 when a served queue has nothing for this warp
+    // right now (only when `wait` is false); -1 when the queue is drained
+    // (batched), the server is shutting down, or a waiting warp's bounded wait
+    // ran out.  Only a warp that holds no walk at all waits: a warp with walks
+    // in flight looks once and carries on, so an empty queue never stalls live
+    // walks.
+    //
+    // Served queues are ticket queues.  A warp draws a ticket h with one atomic
+    // increment of the head and owns entry h once the published tail passes h.
+    // The head runs ahead of the tail by at most one ticket per warp (a warp
+    // keeps its ticket, in shared memory, until the ticket is served); the
+    // server resets the head to the tail before each launch, when every
+    // published entry has been taken.  A warp with live walks draws a ticket
+    // only when the queue looks non-empty, so new work goes to waiting warps
+    // first.  The waiting warp's wait is bounded: about idle_spins microseconds
+    // of sleep without a new host heartbeat (ctl[2]), after which it raises
+    // status bit 2 and leaves.
     __device__ __forceinline__ int take_chunk(int lane, bool wait) {
         long long lo = 0;
         int cnt = 0, rq = -1;
         int ok = -1;
         if (lane == 0) {
-            long long spins = 0;
-            while (true) {
-                unsigned long long h;
-                bool got = false;
-                if (idle_spins <= 0) {
-                    // Batched: the tail is fixed for the launch, so a plain
-                    // increment suffices (the head is reset before each launch).
-                    h = atomicAdd(ctl, 1ull);
-                    got = h < ctl[1];
-                } else {
-                    if (*(volatile int*)exit_flag) break;   // served: shutdown
-                    unsigned long long h0, t;                 // head and tail in one load
-                    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
-                                 : "=l"(h0), "=l"(t) : "l"(ctl));
-                    if (t > h0 + kQueueMargin) {
-                        h = atomicAdd(ctl, 1ull);
-                        got = true;
-                        if (h >= t) {
-                            long long w = 0;
-                            while (*(volatile unsigned long long*)(ctl + 1) <= h &&
-                                   ++w < idle_spins && !*(volatile int*)exit_flag)
-                                __nanosleep(1000);
-                            if (*(volatile unsigned long long*)(ctl + 1) <= h) {
-                                atomicOr(status, 2);
-                                got = false;
-                                break;
-                            }
+            unsigned long long h = 0;
+            bool got = false;
+            if (idle_spins <= 0) {
+                // Batched: the tail is fixed for the launch (the head is reset
+                // before each launch).
+                h = atomicAdd(ctl, 1ull);
+                got = h < ctl[1];
+            } else {
+                unsigned long long* const slot = warp_ticket();
+                unsigned long long tk = *slot;
+                long long slept = 0;
+                unsigned long long beat = 0;
+                unsigned nap = 1024u;                        // ns
+                while (true) {
+                    if (wait && *(volatile int*)exit_flag) break;     // shutdown
+                    if (tk == kNoTicket) {
+                        unsigned long long h0, t0;               // head and tail in one load
+                        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+                                     : "=l"(h0), "=l"(t0) : "l"(ctl));
+                        if (!wait && h0 >= t0) {                 // nothing for a busy warp
+                            ok = 0;
+                            break;
                         }
-                    } else {
-                        // Near the tail: never move the head past it.  Every
-                        // failed CAS means another warp took an entry, so the
-                        // retries are bounded by the entries available.
-                        h = h0;
-                        while (h < t) {
-                            const unsigned long long prev = atomicCAS(ctl, h, h + 1);
-                            if (prev == h) { got = true; break; }
-                            h = prev;
-                        }
+                        tk = atomicAdd(ctl, 1ull);
                     }
+                    if (tk < *(volatile unsigned long long*)(ctl + 1)) {
+                        h = tk;
+                        tk = kNoTicket;
+                        got = true;
+                        break;
+                    }
+                    if (!wait) {                                 // keep the ticket
+                        ok = 0;
+                        break;
+                    }
+                    // Back off (1 us doubling to 32 us), so thousands of waiting
+                    // warps do not hammer the queue words while others work.
+                    const unsigned long long b = *(volatile unsigned long long*)(ctl + 2);
+                    if (b != beat) {
+                        beat = b;
+                        slept = 0;
+                    }
+                    slept += nap >> 10;
+                    if (slept > idle_spins) {
+                        atomicOr(status, 2);
+                        break;
+                    }
+                    __nanosleep(nap);
+                    nap = nap < 32768u ? 2u * nap : nap;
                 }
-                if (got) {
-                    __threadfence();     // the entry is read after the tail that covers it
-                    const int4 c = __ldcg(reinterpret_cast<const int4*>(chunks + (h % ring)));
-                    lo = (long long)(((unsigned long long)(unsigned)c.y << 32) | (unsigned)c.x);
-                    cnt = c.z;
-                    rq = c.w;
-                    ok = 1;
-                    break;
-                }
-                if (idle_spins <= 0) break;                  // batched: queue drained
-                if (!wait) {                                 // served, walks in flight
-                    ok = 0;
-                    break;
-                }
-                if (++spins > idle_spins) break;             // served: bounded idle wait
-                __nanosleep(1000);
+                *slot = tk;
+            }
+            if (got) {
+                __threadfence();     // the entry is read after the tail that covers it
+                const int4 c = __ldcg(reinterpret_cast<const int4*>(chunks + (h % ring)));
+                lo = (long long)(((unsigned long long)(unsigned)c.y << 32) | (unsigned)c.x);
+                cnt = c.z;
+                rq = c.w;
+                ok = 1;
             }
         }
         ok = __shfl_sync(FULL, ok, 0);
@@ -658,14 +679,26 @@ struct QueueFeed {
         const int lane = threadIdx.x & 31;
         while (true) {
             const unsigned need = __ballot_sync(FULL, !have);
-            if (need == 0 || drained) break;
+            if (need == 0 || idle_polls < 0) break;
             if (cur_left == 0) {
-                const int got = take_chunk(lane, need == FULL);
-                if (got == 0) break;          // nothing queued yet: live walks go on
-                if (got < 0) {
-                    drained = true;
+                // A warp with live walks that found the served queue empty polls
+                // again only after kIdlePollSkip iterations: each poll is a
+                // dependent L2 round trip that would otherwise slow every
+                // iteration of the warp while the queue stays empty.
+                if (idle_polls > 0 && need != FULL) {
+                    --idle_polls;
                     break;
                 }
+                const int got = take_chunk(lane, need == FULL);
+                if (got == 0) {               // nothing queued yet: live walks go on
+                    idle_polls = kIdlePollSkip;
+                    break;
+                }
+                if (got < 0) {
+                    idle_polls = -1;
+                    break;
+                }
+                idle_polls = 0;
             }
             const int rank = __popc(need & ((1u << lane) - 1u));
             const int n_need = __popc(need);

@@ -58,7 +58,9 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.cur_lo = 0;
     f.cur_left = 0;
     f.cur_req = 0;
-    f.drained = false;
+    f.idle_polls = 0;
+    if ((threadIdx.x & 31) == 0) *warp_ticket() = kNoTicket;
+    __syncwarp();
     walk_loop<W, true, true, COUNT>(g, f, trial_cap, shorter_min, interp_search);
 }
 

@@ -249,37 +249,55 @@ class Server:
         self._outs = {}
         _live_servers.add(self)
 
-    def submit(self, starts, walk_len, p, q, seed, walks_per_node=1, out=None):
+    def submit(self, starts, walk_len, p, q, seed, walks_per_node=1, out=None, hold=False):
         """Host starts (copied at once); `out` a host int32 buffer (numpy or pinned
-        torch) of [walks_per_node * len(starts), walk_len], allocated if None."""
+        torch) of [walks_per_node * len(starts), walk_len], allocated if None.
+        hold=True: no buffer now; the rows wait in the server's device arena and
+        wait() copies them into a buffer it allocates."""
         st = np.ascontiguousarray(starts, dtype=np.int32)
-        if out is None:
-            out = np.empty((st.size * walks_per_node, walk_len), dtype=np.int32)
-        op = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
+        shape = (st.size * walks_per_node, walk_len)
+        if hold:
+            op = None
+        else:
+            if out is None:
+                out = np.empty(shape, dtype=np.int32)
+            op = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
         req = _lib.WalkRequest(st.ctypes.data, st.size, walk_len, walks_per_node, float(p),
                                float(q), int(seed) & (2**64 - 1), op)
         t = ctypes.c_uint64()
         check(self._lib.grape_walk_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
               "grape_walk_server_submit")
-        self._outs[t.value] = out
+        self._outs[t.value] = ("held", shape) if hold else out
         return t.value
 
     def wait(self, ticket, timeout_ms=-1):
-        code = self._lib.grape_walk_server_wait(self._h, ticket, int(timeout_ms), None)
+        held = self._outs.get(ticket)
+        host = None
+        if isinstance(held, tuple):
+            host = np.empty(held[1], dtype=np.int32)
+        code = self._lib.grape_walk_server_wait(self._h, ticket, int(timeout_ms),
+                                                None if host is None else host.ctypes.data)
         out = self._outs.pop(ticket, None) if code != _lib.CODES["GRAPE_ERR_TIMEOUT"] else None
         check(code, "grape_walk_server_wait")
-        return out
+        return host if host is not None else out
 
     def wait_any(self, timeout_ms=-1):
-        """(ticket, latency_s, rows) of the next finished request."""
+        """(ticket, latency_s, rows) of the next finished request.  Held rows
+        land in a buffer as large as the largest held request, returned as
+        that request's view of it."""
         t = ctypes.c_uint64()
         lat = ctypes.c_int64()
+        held = [v[1] for v in self._outs.values() if isinstance(v, tuple)]
+        host = np.empty(max(a * b for a, b in held), dtype=np.int32) if held else None
         code = self._lib.grape_walk_server_wait_any(self._h, int(timeout_ms), ctypes.byref(t),
-                                                    ctypes.byref(lat), None)
+                                                    ctypes.byref(lat),
+                                                    None if host is None else host.ctypes.data)
         if code == _lib.CODES["GRAPE_ERR_TIMEOUT"]:
             raise GrapeError(code, "grape_walk_server_wait_any")
         out = self._outs.pop(t.value, None)
         check(code, f"ticket {t.value}")
+        if isinstance(out, tuple):
+            out = host[:out[1][0] * out[1][1]].reshape(out[1])
         return t.value, lat.value * 1e-9, out
 
     def cancel(self, ticket):

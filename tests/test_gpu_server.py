@@ -94,7 +94,7 @@ def test_idle_exit_and_relaunch(graph):
     srv = Server(g, output_cap_bytes=64 << 20, max_inflight=8, idle_exit_us=200)
     s = np.arange(500, dtype=np.int32)
     a = srv.wait(srv.submit(s, 20, 2.0, 0.5, 1), timeout_ms=30000)
-    time.sleep(0.05)                     # the resident kernel's idle wait runs out
+    time.sleep(0.05)                     # the server stops the idle resident kernel
     b = srv.wait(srv.submit(s, 20, 2.0, 0.5, 2), timeout_ms=30000)
     st = srv.stats()
     srv.close()
@@ -175,3 +175,49 @@ def test_burst_larger_than_the_entry_stage_keeps_one_kernel(graph):
     assert elapsed < 1.5, elapsed        # the kernel's idle bound is about 2 s
     for (starts, L, p, q, seed), rows in zip(reqs, got):
         assert np.array_equal(rows, _alone(g, starts, L, p, q, seed))
+
+
+def test_held_rows_reuse_slots(graph):
+    """Requests submitted without a host buffer keep their rows in the device
+    arena until wait (or wait_any) hands them over; with two slots, every later
+    request reuses the slot of a retired one.  Rows equal the requests alone."""
+    csr, g = graph
+    rng = np.random.default_rng(4)
+    reqs = [(rng.integers(0, csr.num_nodes, int(rng.integers(1, 3000))).astype(np.int32),
+             int(rng.integers(2, 40)), float(rng.choice([0.25, 1.0, 4.0])),
+             float(rng.choice([0.5, 1.0, 2.0])), 500 + j) for j in range(24)]
+    srv = Server(g, output_cap_bytes=64 << 20, max_inflight=2, chunk_walks=0,
+                 idle_exit_us=1000)
+    got = {}
+    for j in range(0, len(reqs), 4):
+        batch = reqs[j:j + 4]
+        tks = [srv.submit(st, L, p, q, seed, hold=True) for (st, L, p, q, seed) in batch]
+        for k, t in enumerate(tks[:2]):
+            got[j + k] = srv.wait(t, timeout_ms=60000)
+        for _ in range(2):
+            t, _, rows = srv.wait_any(timeout_ms=60000)
+            got[j + 2 + tks[2:].index(t)] = rows
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["inflight"] == 0
+    for j, (starts, L, p, q, seed) in enumerate(reqs):
+        assert np.array_equal(got[j], _alone(g, starts, L, p, q, seed)), j
+
+
+def test_requests_around_the_idle_exit(graph):
+    """Requests arriving just before, at and after the moment the server stops
+    an idle resident kernel: each is served by the leaving kernel or by the
+    next one, never lost, and its rows equal the request alone."""
+    csr, g = graph
+    srv = Server(g, output_cap_bytes=64 << 20, max_inflight=8, idle_exit_us=300)
+    rng = np.random.default_rng(8)
+    got = []
+    for j in range(40):
+        st = rng.integers(0, csr.num_nodes, int(rng.integers(1, 200))).astype(np.int32)
+        got.append((st, srv.wait(srv.submit(st, 12, 1.0, 0.5, 900 + j), timeout_ms=30000)))
+        time.sleep(float(rng.uniform(0.0, 0.005)))   # the driver looks every <= 2 ms
+    s = srv.stats()
+    srv.close()
+    assert s["completed"] == 40 and s["kernel_launches"] >= 2, s
+    for j, (st, rows) in enumerate(got):
+        assert np.array_equal(rows, _alone(g, st, 12, 1.0, 0.5, 900 + j)), j
