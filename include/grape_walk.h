@@ -188,9 +188,12 @@ grape_status_t grape_walks_range(const grape_graph_t* graph, const int32_t* star
  * The same walks as grape_walks, with `starts` and `out` in HOST memory
  * (pageable or pinned).  The call copies the starts in, runs the walks and
  * copies the rows out, and returns once `out` holds them (it synchronises
- * `stream`).  Device scratch for the starts and rows is taken from, and given
- * back to, the device's default stream-ordered memory pool inside the call.
- * Pinned host buffers let both copies run at full link speed.
+ * `stream`).  Rows above 64 MB are walked in up to 16 slices of walk ids, and
+ * each slice is copied out on a per-device copy stream of the library while
+ * the later slices are walked.  Device scratch for the starts and rows is
+ * taken from, and given back to, the device's default stream-ordered memory
+ * pool inside the call.  Pinned host buffers let the copies run at full link
+ * speed.
  */
 grape_status_t grape_walks_host(const grape_graph_t* graph, const int32_t* starts,
                                 int64_t num_starts, int32_t walk_len, int32_t walks_per_node,

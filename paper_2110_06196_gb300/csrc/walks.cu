@@ -161,6 +161,27 @@ cudaError_t dispatch_walk(const grape_graph* g, const grape_tuning_t& t, const W
 
 bool valid_pq(double x) { return std::isfinite(x) && x > 0.0; }
 
+// grape_walks_host: at most this many slices, of at least this many bytes.
+constexpr size_t kHostSlices = 16;
+constexpr size_t kHostSliceBytes = 64u << 20;
+
+// One non-blocking stream per device for grape_walks_host's copies out.
+cudaError_t host_copy_stream(cudaStream_t* out) {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev]) {
+        e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *out = streams[dev];
+    return cudaSuccess;
+}
+
 grape_tuning_t tuning_of(const grape_graph* g) {
     std::lock_guard<std::mutex> lk(const_cast<grape_graph*>(g)->mu);
     return g->tuning;
@@ -381,9 +402,13 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
     grape_status_t st = make_walk_const(g, starts, num_starts, walk_len, walks_per_node, p, q,
                                         seed, out, &probe);
     if (st != GRAPE_OK) return st;
+    cudaStream_t copy = nullptr;
+    if (host_copy_stream(&copy) != cudaSuccess) return GRAPE_ERR_CUDA;
     int32_t* d_starts = nullptr;
     int32_t* d_out = nullptr;
-    const size_t out_bytes = sizeof(int32_t) * (size_t)probe.num_walks * (size_t)walk_len;
+    const int64_t nw = probe.num_walks;
+    const size_t row_bytes = sizeof(int32_t) * (size_t)walk_len;
+    const size_t out_bytes = row_bytes * (size_t)nw;
     // Scratch comes from the device's stream-ordered pool, which keeps freed
     // blocks for reuse, so repeated calls do not pay for fresh allocations.
     static std::once_flag pool_once;
@@ -395,22 +420,57 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     });
-    cudaError_t e = cudaSuccess;
-    if (starts) e = cudaMallocAsync(&d_starts, sizeof(int32_t) * (size_t)num_starts, stream);
+    // The rows leave in slices of walk ids: slice i is copied to the host on a
+    // copy stream while the later slices are still being walked, so only the
+    // last slice's copy is exposed.  Slice bounds are multiples of 8 rows, which
+    // keeps every slice's device rows 32-byte aligned.
+    const int64_t want = (int64_t)std::min<size_t>(kHostSlices, std::max<size_t>(1, out_bytes / kHostSliceBytes));
+    const int64_t per = ((nw + want - 1) / want + 7) / 8 * 8;
+    const int nslices = (int)((nw + per - 1) / per);
+    std::vector<cudaEvent_t> walked((size_t)nslices, nullptr);
+    cudaEvent_t copied = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
+    for (int i = 0; i < nslices && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&walked[(size_t)i], cudaEventDisableTiming);
+    if (e == cudaSuccess && starts)
+        e = cudaMallocAsync(&d_starts, sizeof(int32_t) * (size_t)num_starts, stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_out, out_bytes, stream);
     if (e == cudaSuccess && starts)
         e = cudaMemcpyAsync(d_starts, starts, sizeof(int32_t) * (size_t)num_starts,
                             cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) {
-        st = grape_walks(g, d_starts, num_starts, walk_len, walks_per_node, p, q, seed, d_out,
-                         stream_);
-        if (st == GRAPE_OK)
-            e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, stream);
+    int launched = 0;
+    for (int i = 0; i < nslices && e == cudaSuccess && st == GRAPE_OK; ++i) {
+        const int64_t b = (int64_t)i * per;
+        const int64_t c = std::min<int64_t>(per, nw - b);
+        st = grape_walks_range(g, d_starts, num_starts, walk_len, walks_per_node, p, q, seed, b, c,
+                               d_out + (size_t)b * (size_t)walk_len, stream_);
+        if (st == GRAPE_OK) e = cudaEventRecord(walked[(size_t)i], stream);
+        if (st == GRAPE_OK && e == cudaSuccess) ++launched;
     }
+    // Copies after all launches, so that a pageable destination (whose copies
+    // block the host) still overlaps the walks of later slices.
+    for (int i = 0; i < launched && e == cudaSuccess; ++i) {
+        const int64_t b = (int64_t)i * per;
+        const int64_t c = std::min<int64_t>(per, nw - b);
+        e = cudaStreamWaitEvent(copy, walked[(size_t)i], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + (size_t)b * (size_t)walk_len,
+                                d_out + (size_t)b * (size_t)walk_len, row_bytes * (size_t)c,
+                                cudaMemcpyDeviceToHost, copy);
+    }
+    // the scratch is freed on `stream` after the copies that read it
+    cudaError_t e2 = cudaEventRecord(copied, copy);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(stream, copied, 0);
+    if (e2 != cudaSuccess) cudaStreamSynchronize(copy);
     if (d_starts) cudaFreeAsync(d_starts, stream);
     if (d_out) cudaFreeAsync(d_out, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    const cudaError_t e3 = cudaStreamSynchronize(stream);
+    for (cudaEvent_t ev : walked)
+        if (ev) cudaEventDestroy(ev);
+    if (copied) cudaEventDestroy(copied);
     if (st != GRAPE_OK) return st;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = e3;
     return grape::cuda_status(e);
 }
 

@@ -242,6 +242,21 @@ def test_host_buffer_entry_point_matches_device_path():
     assert np.array_equal(dev, host)
 
 
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
+def test_host_buffer_entry_point_in_slices(pinned):
+    """Outputs above the slice size leave in several slices whose copies
+    overlap the walks of later slices; rows equal the device path's."""
+    csr = rmat12(False)
+    g = Graph.from_csr(csr)
+    wpn, L = 131, 67                      # 4096 * 131 rows of 268 bytes: 144 MB, 3 slices
+    dev = walks(g, None, L, wpn, 0.5, 2.0, seed=8).cpu().numpy()
+    out = torch.empty(dev.shape, dtype=torch.int32)
+    if pinned:
+        out = out.pin_memory()
+    host = walks_host(g, None, L, wpn, 0.5, 2.0, seed=8, out=out)
+    assert np.array_equal(dev, host.numpy())
+
+
 def test_er1k_workload_full_parity():
     csr = synth.workload_graph("er1k")
     job = synth.WORKLOADS["er1k"]["job"]
