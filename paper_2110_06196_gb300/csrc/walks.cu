@@ -422,9 +422,14 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
     });
     // The rows leave in slices of walk ids: slice i is copied to the host on a
     // copy stream while the later slices are still being walked, so only the
-    // last slice's copy is exposed.  Slice bounds are multiples of 8 rows, which
-    // keeps every slice's device rows 32-byte aligned.
-    const int64_t want = (int64_t)std::min<size_t>(kHostSlices, std::max<size_t>(1, out_bytes / kHostSliceBytes));
+    // last slice's copy is exposed.  A slice holds at least kHostSliceBytes of
+    // rows and at least 16 walks per resident lane (each launch ends in a tail
+    // of lanes finishing unevenly).  Slice bounds are multiples of 8 rows,
+    // which keeps every slice's device rows 32-byte aligned.
+    const int64_t lanes = (int64_t)g->num_sms * kMinBlocksWalk * kMaxThreads;
+    const int64_t want = std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)kHostSlices, (int64_t)(out_bytes / kHostSliceBytes),
+                              nw / (16 * lanes)}));
     const int64_t per = ((nw + want - 1) / want + 7) / 8 * 8;
     const int nslices = (int)((nw + per - 1) / per);
     std::vector<cudaEvent_t> walked((size_t)nslices, nullptr);

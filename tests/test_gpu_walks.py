@@ -248,7 +248,7 @@ def test_host_buffer_entry_point_in_slices(pinned):
     overlap the walks of later slices; rows equal the device path's."""
     csr = rmat12(False)
     g = Graph.from_csr(csr)
-    wpn, L = 131, 67                      # 4096 * 131 rows of 268 bytes: 144 MB, 3 slices
+    wpn, L = 1300, 9                      # 5.3 M rows of 36 bytes (191 MB): 2 slices
     dev = walks(g, None, L, wpn, 0.5, 2.0, seed=8).cpu().numpy()
     out = torch.empty(dev.shape, dtype=torch.int32)
     if pinned:
