@@ -397,6 +397,7 @@ def run_ours(args, dist):
                      "frac_of_random_sector_peak": achieved / rs_peak},
         "counters": {"trials_per_step": cnt["trials"] / max(1, cnt["steps"]),
                      "gathers_per_step": cnt["gathers"] / max(1, cnt["steps"]),
+                     "filtered_per_step": cnt["filtered"] / max(1, cnt["steps"]),
                      "searches_per_step": cnt["searches"] / max(1, cnt["steps"]),
                      "probes_per_search": cnt["probes"] / max(1, cnt["searches"]),
                      "fallbacks": cnt["fallbacks"]},

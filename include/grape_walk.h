@@ -97,7 +97,10 @@ typedef struct grape_graph grape_graph_t;
  *   16 * num_nodes + 36 * num_entries bytes: node records, sorted rows, and
  *   per CSR entry one 32-byte proposal entry that carries the target's degree,
  *   row offset and largest row weight, the weight, and the position of the
- *   row's node in the target's row.
+ *   row's node in the target's row (unweighted graphs: a 96-bit filter of the
+ *   target's row in place of the weights).  Unweighted graphs need another
+ *   16 * num_nodes bytes of scratch from the device's stream-ordered pool
+ *   during the call.
  *   flags: GRAPE_UNDIRECTED | GRAPE_VALIDATE.  With GRAPE_VALIDATE the call
  *       synchronises `stream` and returns GRAPE_ERR_INVALID_GRAPH for:
  *       non-monotone offsets, wrong first or last offset, ids out of range,
@@ -286,10 +289,12 @@ typedef struct grape_walk_counters {
     int64_t trials;       /* proposals drawn */
     int64_t gathers;      /* proposals whose entry had to be read (the rest were decided
                              without a read: rejected whatever the target, or the return) */
-    int64_t searches;     /* membership tests whose outcome decided acceptance */
-    int64_t probes;       /* list entries loaded by those tests */
+    int64_t searches;     /* membership tests, deciding acceptance, run on the sorted rows */
+    int64_t probes;       /* 32-byte row sectors read by those tests */
     int64_t fallbacks;    /* steps drawn by the exact inverse-transform fallback */
     int64_t walks;        /* rows written */
+    int64_t filtered;     /* membership tests settled by the neighbour filters of an
+                             unweighted graph, without reading a row */
 } grape_walk_counters_t;
 
 grape_status_t grape_counters_enable(grape_graph_t* graph, int32_t enable);

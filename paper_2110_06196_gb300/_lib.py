@@ -53,7 +53,8 @@ class WalkRequest(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [("steps", c_i64), ("trials", c_i64), ("gathers", c_i64), ("searches", c_i64),
-                ("probes", c_i64), ("fallbacks", c_i64), ("walks", c_i64)]
+                ("probes", c_i64), ("fallbacks", c_i64), ("walks", c_i64),
+                ("filtered", c_i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

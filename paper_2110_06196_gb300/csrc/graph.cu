@@ -8,7 +8,9 @@
 //   dsts[e]  int32 sorted rows, read by the membership searches (padded by 8);
 //   fat      one 32-byte proposal entry per CSR entry e (row v, target x):
 //            {x, deg_x, off_x lo, off_x hi} {w_vx, wmax_x, rev, w_xv}, rev being
-//            the position of v in N(x) (-1 when absent) and w_xv its weight.  A proposal reads its target,
+//            the position of v in N(x) (-1 when absent) and w_xv its weight;
+//            unweighted graphs hold a 96-bit filter of N(x) in place of the
+//            three weights.  A proposal reads its target,
 //            the target's row, the weight and the target's row maximum from one
 //            sector, so an accepted step needs no further gather (edge-inlined
 //            records); rev tells the walk where its previous node sits in the
@@ -87,14 +89,36 @@ __global__ void build_rows_kernel(const int64_t* __restrict__ offsets,
     }
 }
 
-// Proposal entries: fat[2e] = {x, deg_x, off_x lo, off_x hi},
-// fat[2e + 1] = {w_vx bits, wmax_x bits, rev, w_xv bits} (weights 1.0 when
-// unweighted).  One warp per row v, so the row's own bounds are known; ids were
-// checked by build_rows_kernel.  rev = position of v in N(x) (binary search),
-// or -1, and then w_xv = 0.
+// Unweighted graphs: the 96-bit neighbour filter of every row (one warp per
+// row), filt[v] = {bits 0-31, 32-63, 64-95, 0}.
+__global__ void build_filters_kernel(const int32_t* __restrict__ dsts, const int4* __restrict__ rec,
+                                     long long n, int4* __restrict__ filt) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
+         v += warps) {
+        const int4 rv = rec[v];
+        const long long a = (long long)(((unsigned long long)(unsigned)rv.y << 32) | (unsigned)rv.x);
+        unsigned f[3] = {0u, 0u, 0u};
+        for (long long e = a + lane; e < a + rv.z; e += 32) {
+            const int b = grape::filter_bit(dsts[e]);
+            f[b >> 5] |= 1u << (b & 31);
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f[j] = __reduce_or_sync(grape::FULL, f[j]);
+        if (lane == 0) filt[v] = make_int4((int)f[0], (int)f[1], (int)f[2], 0);
+    }
+}
+
+// Proposal entries: fat[2e] = {x, deg_x, off_x lo, off_x hi}, and
+// fat[2e + 1] = {w_vx bits, wmax_x bits, rev, w_xv bits} (weighted) or
+// {filter of N(x) words 0, 1, rev, word 2} (unweighted, filt given).  One warp
+// per row v, so the row's own bounds are known; ids were checked by
+// build_rows_kernel.  rev = position of v in N(x) (binary search), or -1, and
+// then w_xv = 0.
 __global__ void build_fat_kernel(const int32_t* __restrict__ dsts, const float* __restrict__ weights,
-                                 const int4* __restrict__ rec, long long n,
-                                 int4* __restrict__ fat) {
+                                 const int4* __restrict__ rec, const int4* __restrict__ filt,
+                                 long long n, int4* __restrict__ fat) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n;
@@ -113,11 +137,15 @@ __global__ void build_fat_kernel(const int32_t* __restrict__ dsts, const float* 
             }
             const bool back = lo < xa + r.z && dsts[lo] == v;
             const int rev = back ? (int)(lo - xa) : -1;
-            const int one = __float_as_int(1.0f);
-            const int w = weights ? __float_as_int(weights[e]) : one;
-            const int wrev = back ? (weights ? __float_as_int(weights[lo]) : one) : 0;
             fat[2 * e] = make_int4(x, r.z, r.x, r.y);
-            fat[2 * e + 1] = make_int4(w, r.w, rev, wrev);
+            if (weights) {
+                const int w = __float_as_int(weights[e]);
+                const int wrev = back ? __float_as_int(weights[lo]) : 0;
+                fat[2 * e + 1] = make_int4(w, r.w, rev, wrev);
+            } else {
+                const int4 f = filt[x];
+                fat[2 * e + 1] = make_int4(f.x, f.y, rev, f.z);
+            }
         }
     }
 }
@@ -267,11 +295,27 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
         free_graph(g);
         return e != cudaSuccess ? grape::cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
     }
-    // 3. Proposal entries (ids are known in range now).
+    // 3. Proposal entries (ids are known in range now); unweighted graphs first
+    //    build the neighbour filters, in scratch freed once the entries hold them.
     if (num_entries > 0) {
-        build_fat_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
-            g->dsts, weights, g->rec, num_nodes, g->fat);
-        e = cudaGetLastError();
+        int4* filt = nullptr;
+        if (!weights) {
+            e = cudaMallocAsync(&filt, sizeof(int4) * (size_t)num_nodes, stream);
+            if (e == cudaSuccess) {
+                build_filters_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+                    g->dsts, g->rec, num_nodes, filt);
+                e = cudaGetLastError();
+            }
+        }
+        if (e == cudaSuccess) {
+            build_fat_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+                g->dsts, weights, g->rec, filt, num_nodes, g->fat);
+            e = cudaGetLastError();
+        }
+        if (filt) {
+            const cudaError_t ef = cudaFreeAsync(filt, stream);
+            if (e == cudaSuccess) e = ef;
+        }
         if (e != cudaSuccess) {
             free_graph(g);
             return grape::cuda_status(e);
@@ -385,6 +429,7 @@ grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out)
     out->probes = (int64_t)c[grape::C_PROBES];
     out->fallbacks = (int64_t)c[grape::C_FALLBACKS];
     out->walks = (int64_t)c[grape::C_WALKS];
+    out->filtered = (int64_t)c[grape::C_FILTERED];
     return GRAPE_OK;
 }
 

@@ -47,15 +47,31 @@ struct __align__(16) NodeRec {
 };
 
 enum Counter : int {
-    C_STEPS = 0, C_TRIALS, C_GATHERS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_COUNT
+    C_STEPS = 0, C_TRIALS, C_GATHERS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_FILTERED,
+    C_COUNT
 };
+
+// Neighbour filters (unweighted graphs): a 96-bit one-hash Bloom filter of each
+// row, bit filter_bit(y) set for every y in the row.  A clear bit proves that y
+// is not in the row.  Built once with the graph; the proposal entry of x
+// carries the filter of N(x), and a lane keeps the filters of N(v) and N(t).
+__host__ __device__ __forceinline__ int filter_bit(int y) {
+    const unsigned h = (unsigned)y * 0x9E3779B1u;
+    return (int)(((unsigned long long)h * 96ull) >> 32);
+}
+
+__host__ __device__ __forceinline__ bool filter_has(unsigned f0, unsigned f1, unsigned f2, int b) {
+    const unsigned word = b < 32 ? f0 : (b < 64 ? f1 : f2);
+    return (word >> (b & 31)) & 1u;
+}
 
 struct GraphDev {
     const int4* rec;            // [n] NodeRec viewed as int4
     const int* dsts;            // [m + 8] sorted rows (membership search, fallback)
     // proposal entries, one 32-byte sector per CSR entry e (row v, target x):
     //   fat[2e]     = {x, deg_x, off_x lo, off_x hi}
-    //   fat[2e + 1] = {w_vx bits (1.0 unweighted), wmax_x bits, rev, w_xv bits}
+    //   fat[2e + 1] = weighted:   {w_vx bits, wmax_x bits, rev, w_xv bits}
+    //                 unweighted: {filter of N(x) bits 0-31, bits 32-63, rev, bits 64-95}
     // rev = position of v in N(x) (-1 when absent), w_xv the weight there
     const int4* fat;
     long long n;
@@ -234,9 +250,18 @@ struct __align__(16) WRec {
     int len;
 };
 
+// Unweighted graphs: the neighbour filters of the current and previous node.
+struct __align__(16) FRec {
+    unsigned fv[3];       // filter of N(v) (all ones when unknown: the walk's start)
+    unsigned pad0;
+    unsigned ft[3];       // filter of N(t)
+    unsigned pad1;
+};
+
 // Dynamic shared memory per lane: a 32-byte output staging slot, the 32-byte
-// entry of the proposal under a membership search, the lane's TRec and its WRec.
-constexpr int kLaneSharedBytes = 128;
+// entry of the proposal under a membership search, the lane's TRec, its WRec
+// and its FRec.
+constexpr int kLaneSharedBytes = 160;
 
 // Row writer.  Each lane stages its row's entries in its own 32-byte slot of
 // shared memory; when an entry completes a 32-byte sector that lies inside the
@@ -269,6 +294,11 @@ __device__ __forceinline__ unsigned long long* warp_ticket() {
 __device__ __forceinline__ WRec* wrec() {
     extern __shared__ int4 stage_words[];
     return reinterpret_cast<WRec*>(stage_words + 6 * blockDim.x) + threadIdx.x;
+}
+
+__device__ __forceinline__ FRec* frec() {
+    extern __shared__ int4 stage_words[];
+    return reinterpret_cast<FRec*>(stage_words + 8 * blockDim.x) + threadIdx.x;
 }
 
 __device__ __forceinline__ void put(const Lane& L, int* row, int s, int val, int len) {
@@ -429,6 +459,10 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
         return false;
     }
     put(L, rowp, 0, (int)v0, wc.walk_len);
+    {
+        FRec* fr = frec();                 // the start's filter is not at hand: all ones
+        fr->fv[0] = fr->fv[1] = fr->fv[2] = ~0u;
+    }
     const NodeRec r = load_rec(g, (int)v0);
     L.v = (int)v0;
     L.t = -1;
@@ -775,10 +809,34 @@ struct Engine {
     }
 
     // Move along the proposal whose entry is (a, b), at position idx of N(v).
+    // Unweighted: the filter of N(v) becomes that of N(t), and the entry's
+    // filter (of N(x)) that of N(v).
     __device__ __forceinline__ bool advance_entry(Lane& L, int4 a, int4 b, int idx) {
+        if (!WEIGHTED) shift_filters((unsigned)b.x, (unsigned)b.y, (unsigned)b.w);
         const long long off = (long long)(((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.z);
         return advance(L, a.x, off, a.y, __int_as_float(b.y), b.z, __int_as_float(b.w), idx,
                        __int_as_float(b.x));
+    }
+
+    __device__ __forceinline__ void shift_filters(unsigned f0, unsigned f1, unsigned f2) {
+        FRec* fr = frec();
+        const unsigned v0 = fr->fv[0], v1 = fr->fv[1], v2 = fr->fv[2];
+        fr->ft[0] = v0;
+        fr->ft[1] = v1;
+        fr->ft[2] = v2;
+        fr->fv[0] = f0;
+        fr->fv[1] = f1;
+        fr->fv[2] = f2;
+    }
+
+    // Unweighted: do the filters prove that x is not in N(t)?  The filter of
+    // N(t) tests x; on undirected graphs x in N(t) <=> t in N(x), so the filter
+    // of N(x), which arrived in x's entry (ld2), tests t as well.
+    __device__ __forceinline__ bool filters_exclude(const Lane& L, int x) {
+        const FRec* fr = frec();
+        if (!filter_has(fr->ft[0], fr->ft[1], fr->ft[2], filter_bit(x))) return true;
+        return g.undirected &&
+               !filter_has((unsigned)ld2.x, (unsigned)ld2.y, (unsigned)ld2.w, filter_bit(L.t));
     }
 
     // Steps drawn by the exact fallback while the trial cap is spent.  Returns have.
@@ -882,6 +940,10 @@ struct Engine {
             if (A.acc_a == A.acc_b || !HAS_Q) {
                 if (A.acc_a) take = true;
                 else L.k++;
+            } else if (!WEIGHTED && filters_exclude(L, A.x)) {
+                cnt.add(C_FILTERED);            // x is not in N(t): the out class decides
+                if (A.acc_b) take = true;
+                else L.k++;
             } else {
                 begin_search(L, A);
                 probe = true;
@@ -917,8 +979,14 @@ struct Engine {
                 const TRec tr = *trec();
                 a = make_int4(L.t, tr.deg_t, (int)(unsigned)tr.off_t,
                               (int)(unsigned)((unsigned long long)tr.off_t >> 32));
-                b = make_int4(__float_as_int(L.wr), __float_as_int(tr.wmax_t), tr.jv,
-                              __float_as_int(tr.wj));
+                if (WEIGHTED) {
+                    b = make_int4(__float_as_int(L.wr), __float_as_int(tr.wmax_t), tr.jv,
+                                  __float_as_int(tr.wj));
+                } else {
+                    // back to t: its filter was the previous node's
+                    const FRec* fr = frec();
+                    b = make_int4((int)fr->ft[0], (int)fr->ft[1], tr.jv, (int)fr->ft[2]);
+                }
                 jv = L.rt;
             }
             if (!advance_entry(L, a, b, jv)) return false;
