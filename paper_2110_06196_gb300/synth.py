@@ -264,9 +264,13 @@ WORKLOADS = {
     # R-MAT scale 24, 256M undirected edges, unweighted, hub-heavy.
     "rmat24": dict(kind="rmat", scale=24, m=1 << 28, seed=3, weighted=False,
                    job=WalkJob(80, 10, 1.0, 0.25, 11)),
-    # R-MAT scale 22, 64M undirected edges, unweighted: the scale-24 job's
-    # kernel at a size a full profiler capture can hold (about 4 GB on device).
+    # R-MAT scale 22, 64M undirected edges, unweighted: the scale-24 job on a
+    # graph of a sixteenth of the size (about 6 GB on device with its rows).
     "rmat22": dict(kind="rmat", scale=22, m=1 << 26, seed=3, weighted=False,
+                   job=WalkJob(80, 1, 1.0, 0.25, 11)),
+    # R-MAT scale 21, 32M undirected edges, unweighted: the scale-24 job's
+    # kernel at a size a full profiler capture holds (about 3 GB on device).
+    "rmat21": dict(kind="rmat", scale=21, m=1 << 25, seed=3, weighted=False,
                    job=WalkJob(80, 1, 1.0, 0.25, 11)),
     # R-MAT scale 26, 1B undirected edges, unweighted (serving graph).
     "rmat26": dict(kind="rmat", scale=26, m=1 << 30, seed=5, weighted=False, job=None),
