@@ -14,8 +14,10 @@ gets byte-identical output to a single-threaded call.
 Pins (see ``tests/test_oracle_*.py``): Philox4x32-10 against the published
 known-answer vectors; transition frequencies against the exact law computed from
 graph distances d(t, x) (eq. alphaRW) by chi-square; closed forms on cycles,
-complete graphs and stars; stationarity of p = q = 1 walks; and the trial-cap
-fallback against the same exact law.
+complete graphs and stars; stationarity of p = q = 1 walks; the trial-cap
+fallback against the same exact law; and the context windows against a worked
+example, an independent sliding-window construction, a closed-form count and
+their symmetry.
 """
 from __future__ import annotations
 
@@ -72,6 +74,8 @@ def _bind(lib):
     lib.oracle_walks.argtypes = [vp, vp, vp, vp, i64, vp, i64, i32, dbl, dbl, u64, i64,
                                  i64, i64, vp, vp]
     lib.oracle_walks.restype = ctypes.c_int
+    lib.oracle_contexts.argtypes = [vp, i64, i32, i32, vp]
+    lib.oracle_contexts.restype = None
     return lib
 
 
@@ -198,4 +202,17 @@ def walk_rows(g: Graph, starts, walk_len, walks_per_node, p, q, seed, ids,
         rows, _ = walks(g, starts, walk_len, walks_per_node, p, q, seed, trial_cap,
                         walk_ids=(int(w), int(w) + 1))
         out[j] = rows[0]
+    return out
+
+
+def contexts(rows, window, lib=None):
+    """Context windows of walk rows (``oracle_contexts``): int32
+    [num_rows, walk_len, 2 * window], the ``window`` positions before each
+    centre then the ``window`` after it, -1 outside the row, after a dead end,
+    or around a -1 centre."""
+    lib = lib or load()
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    n, L = rows.shape
+    out = np.empty((n, L, 2 * window), dtype=np.int32)
+    lib.oracle_contexts(_ptr(rows), int(n), int(L), int(window), _ptr(out))
     return out

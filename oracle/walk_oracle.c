@@ -285,3 +285,34 @@ void oracle_next_many(const int64_t* offsets, const int32_t* dsts, const float* 
         out[j] = oracle_next(offsets, dsts, weights, wmax, t, v, p, q, seed,
                              walk_begin + j, step, trial_cap, stats);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Context windows of walk rows (GRAPE, "First and second-order RW-based      */
+/* embedding methods": SkipGram and CBOW learn from windows of a given size   */
+/* sliding over the walks).  For row r and position i, ctx[r][i] lists the    */
+/* window around the centre row[r][i]: the `window` positions before it, in   */
+/* walk order, then the `window` positions after it:                          */
+/*     ctx[r][i][j]          = row[r][i - window + j]     j = 0 .. window-1   */
+/*     ctx[r][i][window + j] = row[r][i + 1 + j]          j = 0 .. window-1   */
+/* An entry is -1 when its position lies outside the row, when it holds -1    */
+/* (after a dead end), or when the centre itself is -1.  SkipGram pairs are   */
+/* (centre, entry) over the entries that are not -1; CBOW uses the entries of */
+/* a centre together.                                                         */
+/* ------------------------------------------------------------------------ */
+void oracle_contexts(const int32_t* rows, int64_t num_rows, int32_t walk_len, int32_t window,
+                     int32_t* ctx)
+{
+    const int64_t width = 2 * (int64_t)window;
+    for (int64_t r = 0; r < num_rows; ++r) {
+        const int32_t* row = rows + r * (int64_t)walk_len;
+        for (int32_t i = 0; i < walk_len; ++i) {
+            int32_t* out = ctx + (r * (int64_t)walk_len + i) * width;
+            for (int32_t j = 0; j < 2 * window; ++j) {
+                int64_t pos = (j < window) ? (int64_t)i - window + j : (int64_t)i + 1 + (j - window);
+                int32_t val = -1;
+                if (row[i] >= 0 && pos >= 0 && pos < walk_len && row[pos] >= 0) val = row[pos];
+                out[j] = val;
+            }
+        }
+    }
+}
