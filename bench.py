@@ -56,6 +56,7 @@ def parse():
                          "graph, for profiling); 0 keeps the workload's own")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-contexts", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-rates", default="50,200,1000")
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -405,11 +406,63 @@ def run_ours(args, dist):
     }
     if want_batched:
         res["batched"] = bench_batched(g, csr, dev)
+    if want_batched and not args.no_contexts:
+        res["contexts"] = bench_contexts(g, job, n, dev, peak)
     if want_cpu:
         rate, cores, sample = oracle_rate(csr_host, job, args.cpu_seconds)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": sample}
     return res
+
+
+def bench_contexts(g, job, n, dev, peak, window=5, chunk=1 << 20):
+    """The whole job's SkipGram/CBOW context windows (window 5 each side),
+    streamed in chunks of walk ids through grape_walk_contexts into one reused
+    device buffer (walk rows only in scratch), and the windows kernel alone
+    (grape_contexts_from_rows) against the copy peak: it reads 4 B and writes
+    8 * window B per walk entry."""
+    from paper_2110_06196_gb300 import contexts, contexts_from_rows, walks
+    total = n * job.walks_per_node
+    L = job.walk_len
+    out = torch.empty((chunk, L, 2 * window), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def run_job():
+        for b in range(0, total, chunk):
+            c = min(chunk, total - b)
+            contexts(g, None, L, job.walks_per_node, job.p, job.q, job.seed, window=window,
+                     walk_begin=b, walk_count=c, out=out[:c])
+
+    run_job()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run_job()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    last = total - (total - 1) // chunk * chunk
+    pairs_last = int((out[:last] >= 0).sum())
+    # the windows kernel alone, on one chunk of materialised rows
+    rows = walks(g, None, L, job.walks_per_node, job.p, job.q, job.seed, out=None)[:chunk].contiguous()
+    contexts_from_rows(rows, window, out=out)
+    torch.cuda.synchronize(dev)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        contexts_from_rows(rows, window, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    kms = e0.elapsed_time(e1) / reps
+    kbytes = rows.numel() * 4 * (1 + 2 * window)
+    del rows, out
+    torch.cuda.empty_cache()
+    entries = total * L * 2 * window
+    return {"window": window, "walks": total, "chunk_walks": chunk, "ms": ms,
+            "context_entries_per_s": entries / (ms / 1e3),
+            "skipgram_pairs_in_last_chunk": pairs_last,
+            "windows_kernel": {"ms": kms, "bytes": kbytes, "achieved_gbs": kbytes / kms / 1e6,
+                               "peak_gbs": peak, "frac": kbytes / kms / 1e6 / peak}}
 
 
 def bench_batched(g, csr, dev):

@@ -203,6 +203,44 @@ grape_status_t grape_walks_host(const grape_graph_t* graph, const int32_t* start
                                 double p, double q, uint64_t seed, int32_t* out,
                                 grape_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* Context windows (SkipGram / CBOW input)                                   */
+/* ------------------------------------------------------------------------ */
+
+#define GRAPE_MAX_CONTEXT_WINDOW 64
+
+/*
+ * Context windows of walk rows, the input the shallow SkipGram and CBOW models
+ * learn from (GRAPE, Methods, "First and second-order RW-based embedding
+ * methods": windows of a given size sliding over the walks).  For row r and
+ * position i:
+ *     contexts[r][i][j]          = rows[r][i - window + j]   j = 0 .. window-1
+ *     contexts[r][i][window + j] = rows[r][i + 1 + j]        j = 0 .. window-1
+ * and -1 where that position lies outside the row, holds -1 (after a dead
+ * end), or the centre rows[r][i] is -1.  SkipGram pairs are (centre, entry)
+ * over the entries that are not -1.
+ *   rows: device int32[num_rows][walk_len]; contexts: device
+ *   int32[num_rows][walk_len][2 * window]; window in [1, GRAPE_MAX_CONTEXT_WINDOW].
+ * Enqueued on `stream`.
+ */
+grape_status_t grape_contexts_from_rows(const int32_t* rows, int64_t num_rows, int32_t walk_len,
+                                        int32_t window, int32_t* contexts, grape_stream_t stream);
+
+/*
+ * Walks [walk_begin, walk_begin + walk_count) of the job that grape_walks(starts,
+ * num_starts, walk_len, walks_per_node, p, q, seed) describes, turned into
+ * their context windows as in grape_contexts_from_rows.  The walk rows go to
+ * `centres` (device int32[walk_count][walk_len]) when it is not NULL; otherwise
+ * they live only in scratch taken from, and given back to, the device's
+ * stream-ordered pool.  Calling this for consecutive ranges streams a job's
+ * windows to a trainer without holding all of its walks.  Enqueued on `stream`.
+ */
+grape_status_t grape_walk_contexts(const grape_graph_t* graph, const int32_t* starts,
+                                   int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                                   double p, double q, uint64_t seed, int32_t window,
+                                   int64_t walk_begin, int64_t walk_count, int32_t* centres,
+                                   int32_t* contexts, grape_stream_t stream);
+
 /* One walk request: rows as in grape_walks. */
 typedef struct grape_walk_request {
     const int32_t* starts;    /* device int32[num_starts] for batched calls; HOST for the server */

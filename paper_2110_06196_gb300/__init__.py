@@ -4,9 +4,10 @@ The compute path is libgrape_walk (CUDA, sm_103a) behind the C ABI declared in
 include/grape_walk.h; ``walk`` is its Python face (argument marshalling over
 ctypes).  ``synth`` builds seeded synthetic inputs.
 """
-from .walk import (BatchPlan, Graph, Server, autotune_batched, philox4x32_10, sector_probe,
-                   walks, walks_batched, walks_host)
+from .walk import (BatchPlan, Graph, Server, autotune_batched, contexts, contexts_from_rows,
+                   philox4x32_10, sector_probe, walks, walks_batched, walks_host)
 from ._lib import GrapeError
 
 __all__ = ["Graph", "walks", "walks_host", "walks_batched", "BatchPlan", "autotune_batched",
-           "Server", "philox4x32_10", "sector_probe", "GrapeError"]
+           "Server", "contexts", "contexts_from_rows", "philox4x32_10", "sector_probe",
+           "GrapeError"]

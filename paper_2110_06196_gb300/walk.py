@@ -148,6 +148,44 @@ def walks_host(graph: Graph, starts=None, walk_len=80, walks_per_node=1, p=1.0, 
     return out
 
 
+def contexts_from_rows(rows: torch.Tensor, window: int, out=None, stream=None) -> torch.Tensor:
+    """grape_contexts_from_rows: int32 [num_rows, walk_len, 2 * window] on the device."""
+    lib = _lib.load()
+    rows = rows.contiguous()
+    n, L = rows.shape
+    if out is None:
+        out = torch.empty((n, L, 2 * window), dtype=torch.int32, device=rows.device)
+    check(lib.grape_contexts_from_rows(_ptr(rows), n, L, int(window), _ptr(out),
+                                       _stream_ptr(stream)), "grape_contexts_from_rows")
+    return out
+
+
+def contexts(graph: Graph, starts=None, walk_len=80, walks_per_node=1, p=1.0, q=1.0, seed=0,
+             window=5, walk_begin=0, walk_count=None, num_starts=None, centres=False, out=None,
+             stream=None):
+    """grape_walk_contexts: (centre rows or None, contexts) on the device for walks
+    [walk_begin, walk_begin + walk_count) of the job."""
+    lib = graph._lib
+    if starts is not None:
+        starts = _dev_tensor(starts, torch.int32, graph.device)
+        ns = starts.numel()
+    else:
+        ns = graph.num_nodes if num_starts is None else int(num_starts)
+    total = ns * walks_per_node
+    count = total - walk_begin if walk_count is None else int(walk_count)
+    cen = None
+    if centres:
+        cen = torch.empty((count, walk_len), dtype=torch.int32, device=graph.device)
+    if out is None:
+        out = torch.empty((count, walk_len, 2 * window), dtype=torch.int32, device=graph.device)
+    code = lib.grape_walk_contexts(graph.handle, _ptr(starts), ns, walk_len, walks_per_node,
+                                   float(p), float(q), int(seed) & (2**64 - 1), int(window),
+                                   int(walk_begin), count, _ptr(cen), _ptr(out),
+                                   _stream_ptr(stream))
+    check(code, "grape_walk_contexts")
+    return cen, out
+
+
 def _requests(reqs, graph):
     """list of dicts {starts (device tensor or None), num_starts, walk_len,
     walks_per_node, p, q, seed, out (device tensor)} -> ctypes array."""

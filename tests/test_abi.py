@@ -101,6 +101,12 @@ def test_argument_errors_return_before_cuda(lib):
     assert lib.grape_walk_server_create(None, None, ctypes.byref(h)) == INVALID
     assert lib.grape_philox4x32_10(None, -1, None, None) == INVALID
     assert lib.grape_sector_probe(None, 0, 0, 0, 0, None, None) == INVALID
+    assert lib.grape_contexts_from_rows(None, 4, 8, 2, None, None) == INVALID
+    for window in (0, 65):
+        assert lib.grape_contexts_from_rows(ctypes.c_void_p(16), 4, 8, window,
+                                            ctypes.c_void_p(16), None) == INVALID
+    assert lib.grape_walk_contexts(None, None, 4, 8, 1, 1.0, 1.0, 0, 2, 0, 4, None, None,
+                                   None) == INVALID
     lib.grape_graph_destroy(None)
     lib.grape_walk_server_destroy(None)
     lib.grape_batch_plan_destroy(None)
