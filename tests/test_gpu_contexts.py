@@ -66,8 +66,7 @@ def test_walk_contexts_equal_oracle_windows_of_oracle_walks(weighted):
 
 def test_shards_and_dead_ends():
     n, e = _law.graph_directed()
-    off, dst = _law.csr_from_edges(n, e, None, False)
-    csr = csr_from_np(off, dst)
+    csr = csr_from_np(*_law.csr_from_edges(n, e, None, False))
     g = Graph.from_csr(csr, undirected=False)
     og = oracle.Graph(*csr.numpy())
     rows_want, _ = oracle.walks(og, None, 12, 40, 0.5, 2.0, seed=4)
