@@ -415,7 +415,7 @@ def run_ours(args, dist):
     return res
 
 
-def bench_contexts(g, job, n, dev, peak, window=5, chunk=1 << 20):
+def bench_contexts(g, job, n, dev, peak, window=5, chunk=1 << 22):
     """The whole job's SkipGram/CBOW context windows (window 5 each side),
     streamed in chunks of walk ids through grape_walk_contexts into one reused
     device buffer (walk rows only in scratch), and the windows kernel alone
