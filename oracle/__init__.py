@@ -66,13 +66,15 @@ def _bind(lib):
     lib.oracle_weighted_accept.restype = ctypes.c_int
     lib.oracle_node_wmax.argtypes = [vp, vp, i64, vp]
     lib.oracle_node_wmax.restype = None
-    lib.oracle_next.argtypes = [vp, vp, vp, vp, i32, i32, dbl, dbl, u64, i64, i32, i64, vp]
+    lib.oracle_next.argtypes = [vp, vp, vp, vp, i32, i32, dbl, dbl, u64, i64, i32, i64, i64, vp]
     lib.oracle_next.restype = i32
     lib.oracle_next_many.argtypes = [vp, vp, vp, vp, i32, i32, dbl, dbl, u64, i64, i64,
-                                     i32, i64, vp, vp]
+                                     i32, i64, i64, vp, vp]
     lib.oracle_next_many.restype = None
     lib.oracle_walks.argtypes = [vp, vp, vp, vp, i64, vp, i64, i32, dbl, dbl, u64, i64,
-                                 i64, i64, vp, vp]
+                                 i64, i64, i64, vp, vp]
+    lib.oracle_suss_positions.argtypes = [i64, i64, u64, i64, i32, vp]
+    lib.oracle_suss_positions.restype = None
     lib.oracle_walks.restype = ctypes.c_int
     lib.oracle_contexts.argtypes = [vp, i64, i32, i32, vp]
     lib.oracle_contexts.restype = None
@@ -144,21 +146,24 @@ def thresholds(p, q, lib=None):
 
 
 def next_many(g: Graph, t, v, p, q, seed, walk_begin, n, step, trial_cap=DEFAULT_TRIAL_CAP,
-              stats=None):
+              stats=None, suss_k=0):
     """n independent draws of the transition out of v with previous node t
-    (t = -1: first step), one per walk id in [walk_begin, walk_begin + n)."""
+    (t = -1: first step), one per walk id in [walk_begin, walk_begin + n).
+    suss_k > 0: approximated walks (SUSS sub-sample of k when deg(v) > k)."""
     out = np.empty(n, dtype=np.int32)
     st = stats if stats is not None else OracleStats()
     g.lib.oracle_next_many(_ptr(g.offsets), _ptr(g.dsts), _ptr(g.weights), _ptr(g.wmax),
                            int(t), int(v), float(p), float(q), int(seed), int(walk_begin),
-                           int(n), int(step), int(trial_cap), _ptr(out), ctypes.byref(st))
+                           int(n), int(step), int(trial_cap), int(suss_k), _ptr(out),
+                           ctypes.byref(st))
     return out
 
 
 def walks(g: Graph, starts, walk_len, walks_per_node, p, q, seed,
-          trial_cap=DEFAULT_TRIAL_CAP, walk_ids=None, stats=None):
+          trial_cap=DEFAULT_TRIAL_CAP, walk_ids=None, stats=None, suss_k=0):
     """Walk rows for all walk ids (default) or for the half-open id range
     ``walk_ids = (begin, end)``.  ``starts`` None means every node in order.
+    suss_k > 0: approximated walks (GRAPE, "Approximated RWs").
     Returns (rows int32[count, walk_len], rc) with rc -1 on a bad start id."""
     num_starts = g.num_nodes if starts is None else len(starts)
     st_arr = None if starts is None else np.ascontiguousarray(starts, dtype=np.int32)
@@ -168,9 +173,19 @@ def walks(g: Graph, starts, walk_len, walks_per_node, p, q, seed,
     st = stats if stats is not None else OracleStats()
     rc = g.lib.oracle_walks(_ptr(g.offsets), _ptr(g.dsts), _ptr(g.weights), _ptr(g.wmax),
                             g.num_nodes, _ptr(st_arr), num_starts, int(walk_len), float(p),
-                            float(q), int(seed), int(trial_cap), int(b), int(e), _ptr(out),
-                            ctypes.byref(st))
+                            float(q), int(seed), int(trial_cap), int(suss_k), int(b), int(e),
+                            _ptr(out), ctypes.byref(st))
     return out, rc
+
+
+def suss_positions(deg, k, seed, walk_id, step, lib=None):
+    """Row positions of the SUSS sub-sample of one step (k of them when deg > k,
+    else all deg positions)."""
+    lib = lib or load()
+    m = k if 0 < k < deg else deg
+    out = np.empty(m, dtype=np.int64)
+    lib.oracle_suss_positions(int(deg), int(k), int(seed), int(walk_id), int(step), _ptr(out))
+    return out
 
 
 def walks_parallel(g: Graph, starts, walk_len, walks_per_node, p, q, seed, walk_ids=None,

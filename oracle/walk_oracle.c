@@ -164,6 +164,46 @@ static int alpha_class(const int64_t* offsets, const int32_t* dsts, int32_t t, i
     return CLS_OUT;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Approximated walks (GRAPE, Methods, "Approximated RWs"): at a node whose   */
+/* degree exceeds k, a step considers only k neighbours, one drawn uniformly  */
+/* from each of k equal buckets of positions (Sorted Unique Sub-Sampling,     */
+/* SUSS), in bucket order.  Bucket b holds positions                          */
+/*     [floor(b * deg / k), floor((b + 1) * deg / k))                         */
+/* and its member is drawn from the Philox block of trial index 2^31 + b of   */
+/* the step, so the sub-sample is fixed for the whole step.                   */
+/* ------------------------------------------------------------------------ */
+#define SUSS_TRIAL_BASE 0x80000000LL
+
+/* Number of candidates of a step: deg, or k under SUSS. */
+static uint64_t cand_count(uint64_t deg, int64_t suss_k)
+{
+    return (suss_k > 0 && deg > (uint64_t)suss_k) ? (uint64_t)suss_k : deg;
+}
+
+/* Position in the row of candidate j (j < cand_count). */
+static uint64_t cand_pos(uint64_t deg, int64_t suss_k, uint64_t seed, int64_t walk_id,
+                         int32_t step, uint64_t j)
+{
+    if (!(suss_k > 0 && deg > (uint64_t)suss_k)) return j;
+    uint64_t k = (uint64_t)suss_k;
+    uint64_t lo = (uint64_t)(((unsigned __int128)j * deg) / k);
+    uint64_t hi = (uint64_t)(((unsigned __int128)(j + 1) * deg) / k);
+    uint32_t r[4];
+    trial_block(seed, walk_id, step, SUSS_TRIAL_BASE + (int64_t)j, r);
+    uint64_t r64 = (uint64_t)r[0] | ((uint64_t)r[1] << 32);
+    return lo + (uint64_t)(((unsigned __int128)r64 * (hi - lo)) >> 64);
+}
+
+/* The SUSS sub-sample of one step, for tests: positions of the k candidates. */
+void oracle_suss_positions(int64_t deg, int64_t suss_k, uint64_t seed, int64_t walk_id,
+                           int32_t step, int64_t* out)
+{
+    uint64_t m = cand_count((uint64_t)deg, suss_k);
+    for (uint64_t j = 0; j < m; ++j)
+        out[j] = (int64_t)cand_pos((uint64_t)deg, suss_k, seed, walk_id, step, j);
+}
+
 typedef struct oracle_stats {
     int64_t steps;       /* transitions taken */
     int64_t trials;      /* Philox blocks drawn for rejection trials */
@@ -172,24 +212,28 @@ typedef struct oracle_stats {
 
 /*
  * One transition out of v (previous node t, or t = -1 on the first step).
- * Returns the chosen neighbour.  deg(v) must be > 0.
+ * Returns the chosen neighbour.  deg(v) must be > 0.  suss_k > 0 samples
+ * among the SUSS sub-sample when deg(v) > suss_k (approximated walks); 0 is
+ * the exact walk.  trial_cap must stay below 2^31 (SUSS trial indices).
  */
 int32_t oracle_next(const int64_t* offsets, const int32_t* dsts, const float* weights,
                     const float* wmax, int32_t t, int32_t v, double p, double q,
                     uint64_t seed, int64_t walk_id, int32_t step, int64_t trial_cap,
-                    oracle_stats* st)
+                    int64_t suss_k, oracle_stats* st)
 {
     uint64_t T[3];
     oracle_thresholds(p, q, T);
     const int64_t off = offsets[v];
     const uint64_t deg = (uint64_t)(offsets[v + 1] - off);
+    const uint64_t m = cand_count(deg, suss_k);
     uint32_t r[4];
 
     for (int64_t k = 0; k < trial_cap; ++k) {
         trial_block(seed, walk_id, step, k, r);
         if (st) st->trials++;
         uint64_t r64 = (uint64_t)r[0] | ((uint64_t)r[1] << 32);
-        uint64_t idx = (uint64_t)(((unsigned __int128)r64 * deg) >> 64);
+        uint64_t j = (uint64_t)(((unsigned __int128)r64 * m) >> 64);
+        uint64_t idx = cand_pos(deg, suss_k, seed, walk_id, step, j);
         int32_t x = dsts[off + (int64_t)idx];
         int cls = alpha_class(offsets, dsts, t, x);
         uint64_t thr = (cls == CLS_FIRST) ? ((uint64_t)1 << 32) : T[cls];
@@ -207,25 +251,27 @@ int32_t oracle_next(const int64_t* offsets, const int32_t* dsts, const float* we
     trial_block(seed, walk_id, step, trial_cap, r);
     double alpha[3] = { 1.0 / p, 1.0, 1.0 / q };
     double total = 0.0;
-    for (uint64_t j = 0; j < deg; ++j) {
-        int32_t x = dsts[off + (int64_t)j];
+    for (uint64_t j = 0; j < m; ++j) {
+        uint64_t pos = cand_pos(deg, suss_k, seed, walk_id, step, j);
+        int32_t x = dsts[off + (int64_t)pos];
         int cls = alpha_class(offsets, dsts, t, x);
         double a = (cls == CLS_FIRST) ? 1.0 : alpha[cls];
-        double w = weights ? (double)weights[off + (int64_t)j] : 1.0;
+        double w = weights ? (double)weights[off + (int64_t)pos] : 1.0;
         total += a * w;
     }
     uint64_t r64 = (uint64_t)r[0] | ((uint64_t)r[1] << 32);
     double u = ((double)(r64 >> 11) * 0x1p-53) * total;
     double run = 0.0;
-    for (uint64_t j = 0; j < deg; ++j) {
-        int32_t x = dsts[off + (int64_t)j];
+    for (uint64_t j = 0; j < m; ++j) {
+        uint64_t pos = cand_pos(deg, suss_k, seed, walk_id, step, j);
+        int32_t x = dsts[off + (int64_t)pos];
         int cls = alpha_class(offsets, dsts, t, x);
         double a = (cls == CLS_FIRST) ? 1.0 : alpha[cls];
-        double w = weights ? (double)weights[off + (int64_t)j] : 1.0;
+        double w = weights ? (double)weights[off + (int64_t)pos] : 1.0;
         run += a * w;
         if (run > u) return x;
     }
-    return dsts[off + (int64_t)deg - 1];
+    return dsts[off + (int64_t)cand_pos(deg, suss_k, seed, walk_id, step, m - 1)];
 }
 
 /*
@@ -241,7 +287,8 @@ int oracle_walks(const int64_t* offsets, const int32_t* dsts, const float* weigh
                  const float* wmax, int64_t num_nodes,
                  const int32_t* starts, int64_t num_starts,
                  int32_t walk_len, double p, double q, uint64_t seed, int64_t trial_cap,
-                 int64_t walk_begin, int64_t walk_end, int32_t* out, oracle_stats* stats)
+                 int64_t suss_k, int64_t walk_begin, int64_t walk_end, int32_t* out,
+                 oracle_stats* stats)
 {
     int rc = 0;
     for (int64_t w = walk_begin; w < walk_end; ++w) {
@@ -259,7 +306,7 @@ int oracle_walks(const int64_t* offsets, const int32_t* dsts, const float* weigh
         for (; s < walk_len; ++s) {
             if (offsets[v + 1] == offsets[v]) break;          /* dead end */
             int32_t x = oracle_next(offsets, dsts, weights, wmax, t, v, p, q, seed,
-                                    w, s, trial_cap, stats);
+                                    w, s, trial_cap, suss_k, stats);
             row[s] = x;
             if (stats) stats->steps++;
             t = v;
@@ -279,11 +326,11 @@ int oracle_walks(const int64_t* offsets, const int32_t* dsts, const float* weigh
 void oracle_next_many(const int64_t* offsets, const int32_t* dsts, const float* weights,
                       const float* wmax, int32_t t, int32_t v, double p, double q,
                       uint64_t seed, int64_t walk_begin, int64_t n, int32_t step,
-                      int64_t trial_cap, int32_t* out, oracle_stats* stats)
+                      int64_t trial_cap, int64_t suss_k, int32_t* out, oracle_stats* stats)
 {
     for (int64_t j = 0; j < n; ++j)
         out[j] = oracle_next(offsets, dsts, weights, wmax, t, v, p, q, seed,
-                             walk_begin + j, step, trial_cap, stats);
+                             walk_begin + j, step, trial_cap, suss_k, stats);
 }
 
 /* ------------------------------------------------------------------------ */

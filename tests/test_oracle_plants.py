@@ -21,7 +21,7 @@ PLANTS = {
     "swap_p_q": ("double a_ret = 1.0 / p, a_in = 1.0, a_out = 1.0 / q;",
                  "double a_ret = 1.0 / q, a_in = 1.0, a_out = 1.0 / p;"),
     "open_neighbourhood": ("    if (x == t) return CLS_RETURN;\n", ""),
-    "range_one_short": ("* deg) >> 64)", "* (deg - 1)) >> 64)"),
+    "range_one_short": ("(((unsigned __int128)r64 * m) >> 64)", "(((unsigned __int128)r64 * (m - 1)) >> 64)"),
     "weight_ignored": ("oracle_weighted_accept(r[2], wmax[v], thr, weights[off + (int64_t)idx])",
                        "oracle_weighted_accept(r[2], wmax[v], thr, wmax[v])"),
     "weighted_tie_accepted": ("return (lhs << d) < rhs;", "return (lhs << d) <= rhs;"),
