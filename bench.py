@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-contexts", action="store_true")
+    ap.add_argument("--suss-k", type=int, default=0,
+                    help="also time the workload's approximated walks (SUSS sub-samples of k "
+                         "neighbours at nodes of degree above k)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-rates", default="50,200,1000")
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -346,6 +349,24 @@ def run_ours(args, dist):
     value = steps_per_launch * args.steps * dist.world / elapsed_max
     launch_ms = sum(ms) / len(ms)
 
+    approx = None
+    if args.suss_k > 0 and dist.world == 1:
+        from paper_2110_06196_gb300 import walks_approx
+        for _ in range(2):
+            walks_approx(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
+                         suss_k=args.suss_k, out=out)
+        torch.cuda.synchronize(dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(3):
+            walks_approx(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
+                         suss_k=args.suss_k, out=out)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ams = a0.elapsed_time(a1) / 3
+        asteps = count_steps(out)
+        approx = {"suss_k": args.suss_k, "ms_per_launch": ams, "steps_per_s": asteps / ams * 1e3,
+                  "exact_ms_per_launch": None}
     del out
     torch.cuda.empty_cache()
     # end to end through the host-buffer entry point: H2D starts, walks, D2H rows
@@ -406,6 +427,9 @@ def run_ours(args, dist):
     }
     if want_batched:
         res["batched"] = bench_batched(g, csr, dev)
+    if approx is not None:
+        approx["exact_ms_per_launch"] = launch_ms
+        res["approx"] = approx
     if want_batched and not args.no_contexts:
         res["contexts"] = bench_contexts(g, job, n, dev, peak)
     if want_cpu:

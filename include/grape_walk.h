@@ -133,7 +133,8 @@ grape_status_t grape_graph_info(const grape_graph_t* graph, grape_graph_info_t* 
  * change how the work is spread over the GPU.
  */
 typedef struct grape_tuning {
-    int64_t trial_cap;        /* rejection trials before the exact fallback (default 4096; 0 = always fall back) */
+    int64_t trial_cap;        /* rejection trials before the exact fallback, in [0, 2^31 - 1]
+                                 (default 4096; 0 = always fall back) */
     int32_t shorter_min;      /* undirected graphs: when deg(t) exceeds this, the record of x is
                                  loaded first and the shorter of N(t), N(x) is searched; otherwise
                                  N(t) is searched at once (INT32_MAX: always N(t)) */
@@ -186,6 +187,22 @@ grape_status_t grape_walks_range(const grape_graph_t* graph, const int32_t* star
                                  int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
                                  double p, double q, uint64_t seed, int64_t walk_begin,
                                  int64_t walk_count, int32_t* out, grape_stream_t stream);
+
+/*
+ * Approximated walks (GRAPE, Methods, "Approximated RWs"): as grape_walks,
+ * except that a step at a node of degree above suss_k considers only suss_k
+ * neighbours, one drawn uniformly from each of suss_k equal buckets of row
+ * positions (Sorted Unique Sub-Sampling), bucket b holding positions
+ * [floor(b deg / suss_k), floor((b + 1) deg / suss_k)), and samples among them
+ * with the same rule (rejection, then after trial_cap rejections the cumulative
+ * sum over the sub-sample in bucket order).  The member of bucket b comes from
+ * the Philox block of trial index 2^31 + b of the step, so the sub-sample is
+ * fixed for the step.  suss_k = 0 gives grape_walks' rows; suss_k >= 1 otherwise.
+ */
+grape_status_t grape_walks_approx(const grape_graph_t* graph, const int32_t* starts,
+                                  int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                                  double p, double q, uint64_t seed, int32_t suss_k, int32_t* out,
+                                  grape_stream_t stream);
 
 /*
  * The same walks as grape_walks, with `starts` and `out` in HOST memory

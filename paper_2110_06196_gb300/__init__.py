@@ -5,9 +5,9 @@ include/grape_walk.h; ``walk`` is its Python face (argument marshalling over
 ctypes).  ``synth`` builds seeded synthetic inputs.
 """
 from .walk import (BatchPlan, Graph, Server, autotune_batched, contexts, contexts_from_rows,
-                   philox4x32_10, sector_probe, walks, walks_batched, walks_host)
+                   philox4x32_10, sector_probe, walks, walks_approx, walks_batched, walks_host)
 from ._lib import GrapeError
 
-__all__ = ["Graph", "walks", "walks_host", "walks_batched", "BatchPlan", "autotune_batched",
+__all__ = ["Graph", "walks", "walks_approx", "walks_host", "walks_batched", "BatchPlan", "autotune_batched",
            "Server", "contexts", "contexts_from_rows", "philox4x32_10", "sector_probe",
            "GrapeError"]

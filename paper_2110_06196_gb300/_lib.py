@@ -107,6 +107,8 @@ SIGNATURES = {
     "grape_philox4x32_10": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
     "grape_sector_probe": (c_i32, [c_vp, c_i64, c_i64, c_u64, c_i32, c_vp, c_vp]),
     "grape_contexts_from_rows": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_vp, c_vp]),
+    "grape_walks_approx": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_i32,
+                                   c_vp, c_vp]),
     "grape_walk_contexts": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_i32,
                                     c_i64, c_i64, c_vp, c_vp, c_vp]),
 }

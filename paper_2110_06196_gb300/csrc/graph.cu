@@ -379,7 +379,7 @@ grape_status_t grape_graph_get_tuning(const grape_graph_t* g, grape_tuning_t* t)
 
 grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t) {
     if (!g || !t) return GRAPE_ERR_INVALID_ARG;
-    if (t->trial_cap < 0 || t->trial_cap > 0xffffffffLL || t->shorter_min < 0 ||
+    if (t->trial_cap < 0 || t->trial_cap > 0x7fffffffLL || t->shorter_min < 0 ||
         t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
         t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->interp_search != 0 && t->interp_search != 1) ||
         (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&

@@ -58,6 +58,7 @@ struct StaticQueueFeed {
     __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wrec()->tm1_in; }
     __device__ __forceinline__ unsigned tm1_out(const Lane&) const { return wrec()->tm1_out; }
     __device__ __forceinline__ int* row(const Lane&) const { return wrec()->row; }
+    __device__ __forceinline__ int suss_k(const Lane&) const { return 0; }   // exact walks
 
     template <class C>
     __device__ __forceinline__ void finish(int, C& cnt) { cnt.add(C_WALKS); }

@@ -93,7 +93,7 @@ struct __align__(16) WalkConst {
     int walk_len;
     double a_ret, a_out;        // 1/p and 1/q for the exact fallback
     int out_vec;                // 1 when out is 32-byte aligned (whole-sector row stores)
-    int pad;
+    int suss_k;                 // approximated walks: SUSS sub-sample size (0: exact walks)
 };
 static_assert(sizeof(WalkConst) % 16 == 0, "WalkConst is loaded as int4 words");
 
@@ -139,6 +139,20 @@ __device__ __forceinline__ int scale_index(unsigned lo, unsigned hi, int n) {
     const unsigned long long a = (unsigned long long)lo * (unsigned)n;
     const unsigned long long b = (unsigned long long)hi * (unsigned)n + (a >> 32);
     return (int)(b >> 32);
+}
+
+// Approximated walks (GRAPE, Methods, "Approximated RWs"): at a node of degree
+// deg > k a step draws among k candidates, one per bucket of row positions
+// [floor(b deg / k), floor((b + 1) deg / k)), the member of bucket b taken
+// from the step's Philox block of trial index 2^31 + b (fixed for the step).
+constexpr unsigned kSussTrialBase = 0x80000000u;
+
+__device__ __forceinline__ int suss_pos(unsigned long long seed, long long w, int s, int b,
+                                        int deg, int k) {
+    const long long lo = (long long)b * deg / k;
+    const long long hi = (long long)(b + 1) * deg / k;
+    const uint4 u = trial_block(seed, w, s, kSussTrialBase | (unsigned)b);
+    return (int)lo + scale_index(u.x, u.y, (int)(hi - lo));
 }
 
 // One 32-byte sector in a single 256-bit read-only load (sm_100 and later):
@@ -400,18 +414,23 @@ __device__ __forceinline__ bool accept_test(unsigned r2, float wmax, unsigned tm
 // Exact fallback after trial_cap rejections: inverse transform over the
 // cumulative sum of pi in row order (GRAPE, "Efficient sampling for Node2Vec
 // RWs"), in fp64 with every product and sum rounded separately.
-// Returns the position of the drawn node in N(v).
+// Returns the position of the drawn node in N(v).  Under SUSS (suss_k > 0
+// and deg_v > suss_k) the cumulative sum runs over the k candidates of the
+// step's sub-sample, in bucket order.
 template <bool WEIGHTED>
-__device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long long seed,
-                              double a_ret, double a_out, unsigned trial_cap) {
+__device__ __forceinline__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long long seed,
+                              double a_ret, double a_out, unsigned trial_cap, int suss_k) {
     const uint4 r = trial_block(seed, L.w, L.s, trial_cap);
     const bool first = (L.t < 0);
     const TRec* tr = trec();
     const int* const nt = first ? g.dsts : g.dsts + tr->off_t;
     const int deg_t = first ? 0 : tr->deg_t;
+    const bool suss = suss_k > 0 && L.deg_v > suss_k;
+    const int m = suss ? suss_k : L.deg_v;
     double total = 0.0;
-    for (int j = 0; j < L.deg_v; ++j) {
-        const long long e = L.off_v + j;
+    for (int j = 0; j < m; ++j) {
+        const int pos = suss ? suss_pos(seed, L.w, L.s, j, L.deg_v, suss_k) : j;
+        const long long e = L.off_v + pos;
         const int x = __ldg(g.dsts + e);
         double a = 1.0;
         if (!first) {
@@ -424,8 +443,9 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
     const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
     const double u = __dmul_rn(__dmul_rn((double)(r64 >> 11), 0x1p-53), total);
     double run = 0.0;
-    for (int j = 0; j < L.deg_v; ++j) {
-        const long long e = L.off_v + j;
+    for (int j = 0; j < m; ++j) {
+        const int pos = suss ? suss_pos(seed, L.w, L.s, j, L.deg_v, suss_k) : j;
+        const long long e = L.off_v + pos;
         const int x = __ldg(g.dsts + e);
         double a = 1.0;
         if (!first) {
@@ -434,9 +454,9 @@ __device__ int exact_fallback(const GraphDev& g, const Lane& L, unsigned long lo
         }
         const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
         run = __dadd_rn(run, __dmul_rn(a, w));
-        if (run > u) return j;
+        if (run > u) return pos;
     }
-    return L.deg_v - 1;
+    return suss ? suss_pos(seed, L.w, L.s, m - 1, L.deg_v, suss_k) : L.deg_v - 1;
 }
 
 // Start the walk of row `row` (walk id walk_base + row) of request wc on this
@@ -512,6 +532,8 @@ __device__ __forceinline__ void set_wrec(const WalkConst& wc, long long row) {
 }
 
 // Per call: lane j of the grid takes walks j, j + stride, j + 2 * stride, ...
+// SUSS: the approximated-walk instantiation (exact walks compile it out).
+template <bool SUSS>
 struct GridFeed {
     const WalkConst* wc;     // kernel-parameter copy
     long long next;
@@ -524,6 +546,7 @@ struct GridFeed {
     __device__ __forceinline__ unsigned tm1_ret(const Lane&) const { return wc->tm1_ret; }
     __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wc->tm1_in; }
     __device__ __forceinline__ unsigned tm1_out(const Lane&) const { return wc->tm1_out; }
+    __device__ __forceinline__ int suss_k(const Lane&) const { return SUSS ? wc->suss_k : 0; }
     // the row of walk id w is row w - walk_base of this call's output
     __device__ __forceinline__ int* row(const Lane& L) const {
         return wc->out + (L.w - wc->walk_base) * (long long)wc->walk_len;
@@ -593,6 +616,7 @@ struct QueueFeed {
     __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wrec()->tm1_in; }
     __device__ __forceinline__ unsigned tm1_out(const Lane&) const { return wrec()->tm1_out; }
     __device__ __forceinline__ int* row(const Lane&) const { return wrec()->row; }
+    __device__ __forceinline__ int suss_k(const Lane&) const { return 0; }   // exact walks
 
     template <class C>
     __device__ __forceinline__ void finish(int req, C& cnt) {
@@ -845,7 +869,8 @@ struct Engine {
             cnt.add(C_FALLBACKS);
             double a_ret, a_out;
             feed.alphas(L.req, a_ret, a_out);
-            const int j = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap);
+            const int j = exact_fallback<WEIGHTED>(g, L, feed.seed(L), a_ret, a_out, trial_cap,
+                                                   feed.suss_k(L));
             int4 a, b;
             ld_sector(g.fat + 2 * (L.off_v + j), a, b);
             if (!advance_entry(L, a, b, j)) return false;
@@ -1024,7 +1049,11 @@ struct Engine {
                     if (!fallback_steps(L)) return false;
                 }
                 const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
-                const int idx = scale_index(r.x, r.y, L.deg_v);
+                const int sk = feed.suss_k(L);
+                const int idx = (sk > 0 && L.deg_v > sk)
+                                    ? suss_pos(feed.seed(L), L.w, L.s, scale_index(r.x, r.y, sk),
+                                               L.deg_v, sk)
+                                    : scale_index(r.x, r.y, L.deg_v);
                 cnt.add(C_TRIALS);
                 if (L.t >= 0) {
                     if (idx == L.rt) {

@@ -28,10 +28,12 @@ constexpr int kMinBlocksQueue = 4;
 // Per-call walk kernel: the eight specialisations of GRAPE ("Implementation of
 // second-order RWs": p == 1, q == 1, weighted or not) as template arguments.
 // COUNT: the instantiation that also keeps the work counters.
-template <bool W, bool P, bool Q, bool COUNT>
+// SUSS: the approximated walks (GRAPE, Methods, "Approximated RWs"), only with
+// the general p, q specialisation.
+template <bool W, bool P, bool Q, bool COUNT, bool SUSS = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
 walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min, int interp_search) {
-    GridFeed f;
+    GridFeed<SUSS> f;
     f.wc = &wc;
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
@@ -123,17 +125,17 @@ int occupancy_blocks(K kernel, int threads) {
     return nb;
 }
 
-template <bool W, bool P, bool Q, bool C>
+template <bool W, bool P, bool Q, bool C, bool S = false>
 cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
                           cudaStream_t stream) {
     const int threads = std::min(t.block_threads, kMaxThreads);
     int per_sm = t.blocks_per_sm;
-    if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q, C>, threads);
+    if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q, C, S>, threads);
     long long blocks = (wc.num_walks + threads - 1) / threads;
     const long long cap = (long long)g->num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    walk_kernel<W, P, Q, C><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
+    walk_kernel<W, P, Q, C, S><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
         g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
     return cudaGetLastError();
 }
@@ -147,6 +149,13 @@ cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const Wal
 
 cudaError_t dispatch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
                           bool has_p, bool has_q, cudaStream_t s) {
+    if (wc.suss_k > 0) {
+        if (g->weighted)
+            return g->counting ? launch_walk_c<true, true, true, true, true>(g, t, wc, s)
+                               : launch_walk_c<true, true, true, false, true>(g, t, wc, s);
+        return g->counting ? launch_walk_c<false, true, true, true, true>(g, t, wc, s)
+                           : launch_walk_c<false, true, true, false, true>(g, t, wc, s);
+    }
     if (g->weighted) {
         if (has_p) return has_q ? launch_walk<true, true, true>(g, t, wc, s)
                                 : launch_walk<true, true, false>(g, t, wc, s);
@@ -372,6 +381,21 @@ grape_status_t grape_walks(const grape_graph_t* g, const int32_t* starts, int64_
     grape_status_t st = make_walk_const(g, starts, num_starts, walk_len, walks_per_node, p, q,
                                         seed, out, &wc);
     if (st != GRAPE_OK) return st;
+    const grape_tuning_t t = tuning_of(g);
+    return grape::cuda_status(dispatch_walk(g, t, wc, p != 1.0, q != 1.0,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
+grape_status_t grape_walks_approx(const grape_graph_t* g, const int32_t* starts,
+                                  int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                                  double p, double q, uint64_t seed, int32_t suss_k, int32_t* out,
+                                  grape_stream_t stream) {
+    if (suss_k < 0) return GRAPE_ERR_INVALID_ARG;
+    WalkConst wc;
+    grape_status_t st = make_walk_const(g, starts, num_starts, walk_len, walks_per_node, p, q,
+                                        seed, out, &wc);
+    if (st != GRAPE_OK) return st;
+    wc.suss_k = suss_k;
     const grape_tuning_t t = tuning_of(g);
     return grape::cuda_status(dispatch_walk(g, t, wc, p != 1.0, q != 1.0,
                                             reinterpret_cast<cudaStream_t>(stream)));

@@ -107,6 +107,8 @@ def test_argument_errors_return_before_cuda(lib):
                                             ctypes.c_void_p(16), None) == INVALID
     assert lib.grape_walk_contexts(None, None, 4, 8, 1, 1.0, 1.0, 0, 2, 0, 4, None, None,
                                    None) == INVALID
+    assert lib.grape_walks_approx(None, None, 4, 8, 1, 1.0, 1.0, 0, -1, None, None) == INVALID
+    assert lib.grape_walks_approx(None, None, 4, 8, 1, 1.0, 1.0, 0, 3, None, None) == INVALID
     lib.grape_graph_destroy(None)
     lib.grape_walk_server_destroy(None)
     lib.grape_batch_plan_destroy(None)
