@@ -10,10 +10,10 @@
 // centre.
 //
 // The kernel is bound by HBM writes: 2 * window int32 out per walk entry in.
-// A block stages a tile of rows and their whole output tile in shared memory,
-// then writes the output tile as one contiguous, coalesced run (consecutive
-// threads, consecutive 16-byte words).  Rows too long for a tile are served by
-// a direct kernel that reads the row through the read-only path.
+// A block stages a tile of rows in shared memory and writes the tile's
+// outputs as one contiguous, coalesced run (consecutive threads, consecutive
+// 16-byte words).  Rows too long for a tile are served by a direct kernel that
+// reads the row through the read-only path.
 #include <algorithm>
 
 #include "internal.h"
@@ -32,45 +32,73 @@ __device__ __forceinline__ int ctx_value(const int* row, int L, int i, int j, in
     return v >= 0 ? v : -1;
 }
 
-// Tiles of R rows: stage the rows, build the R * L * 2W outputs in shared
-// memory, write them out contiguously.
+// n / d for 0 <= n < 2^24 and 1 <= d < 2^24: a float estimate, corrected once
+// (the estimate is off by at most one in this range).
+__device__ __forceinline__ int small_div(int n, int d, float inv_d) {
+    int q = __float2int_rz((float)n * inv_d);
+    if (q * d > n) --q;
+    else if ((q + 1) * d <= n) ++q;
+    return q;
+}
+
+// Tiles of R rows staged in shared memory; the tile's outputs, R * L * 2W
+// contiguous int32, are written by consecutive threads in consecutive 16-byte
+// words, each thread walking its four entries forward from one division.
 __global__ void __launch_bounds__(kCtxThreads)
 contexts_tiled_kernel(const int* __restrict__ rows, long long nrows, int L, int W, int R,
                       int* __restrict__ ctx) {
     extern __shared__ int4 smem4[];
     int* sm_rows = reinterpret_cast<int*>(smem4);
-    const long long width = 2LL * W;
-    const int tile_in = R * L;
-    // the output tile starts on a 16-byte boundary of shared memory
-    int* sm_out = sm_rows + ((tile_in + 3) & ~3);
+    const int width = 2 * W;
+    const float inv_width = 1.0f / (float)width;
+    const float inv_L = 1.0f / (float)L;
     for (long long r0 = (long long)blockIdx.x * R; r0 < nrows; r0 += (long long)gridDim.x * R) {
         const int nr = (int)(nrows - r0 < R ? nrows - r0 : R);
         const int nin = nr * L;
         const int* src = rows + r0 * L;
         for (int e = threadIdx.x; e < nin; e += blockDim.x) sm_rows[e] = __ldg(src + e);
         __syncthreads();
-        for (int c = threadIdx.x; c < nin; c += blockDim.x) {
-            const int r = c / L;
+        const int nout = nin * width;                 // < 2^24 (R is chosen for it)
+        int* dst = ctx + r0 * L * (long long)width;
+        // leading entries up to a 16-byte boundary of dst, then whole words
+        const int head = (int)(((16u - (reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u) >> 2);
+        for (int e = threadIdx.x; e < head && e < nout; e += blockDim.x) {
+            const int c = small_div(e, width, inv_width);
+            const int r = small_div(c, L, inv_L);
             const int i = c - r * L;
             const int* row = sm_rows + r * L;
-            const int centre = row[i];
-            int* o = sm_out + (long long)c * width;
-            for (int j = 0; j < 2 * W; ++j) o[j] = ctx_value(row, L, i, j, W, centre);
+            dst[e] = ctx_value(row, L, i, e - c * width, W, row[i]);
         }
-        __syncthreads();
-        const long long nout = (long long)nin * width;
-        int* dst = ctx + r0 * L * width;
-        // 16-byte stores where dst is 16-byte aligned (the shared tile is)
-        const bool vec = ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0);
-        long long done = 0;
-        if (vec) {
-            const long long n4 = nout >> 2;
-            const int4* s4 = reinterpret_cast<const int4*>(sm_out);
-            int4* d4 = reinterpret_cast<int4*>(dst);
-            for (long long k = threadIdx.x; k < n4; k += blockDim.x) d4[k] = s4[k];
-            done = n4 << 2;
+        const int nwords = (nout - head) >> 2;
+        int4* d4 = reinterpret_cast<int4*>(dst + head);
+        for (int k = threadIdx.x; k < nwords; k += blockDim.x) {
+            const int e = head + 4 * k;
+            int c = small_div(e, width, inv_width);
+            int j = e - c * width;
+            int r = small_div(c, L, inv_L);
+            int i = c - r * L;
+            int v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int* row = sm_rows + r * L;
+                v[u] = ctx_value(row, L, i, j, W, row[i]);
+                if (++j == width) {
+                    j = 0;
+                    if (++i == L) {
+                        i = 0;
+                        ++r;
+                    }
+                }
+            }
+            d4[k] = make_int4(v[0], v[1], v[2], v[3]);
         }
-        for (long long k = done + threadIdx.x; k < nout; k += blockDim.x) dst[k] = sm_out[k];
+        for (int e = head + 4 * nwords + threadIdx.x; e < nout; e += blockDim.x) {
+            const int c = small_div(e, width, inv_width);
+            const int r = small_div(c, L, inv_L);
+            const int i = c - r * L;
+            const int* row = sm_rows + r * L;
+            dst[e] = ctx_value(row, L, i, e - c * width, W, row[i]);
+        }
         __syncthreads();
     }
 }
@@ -117,14 +145,17 @@ grape_status_t grape_contexts_from_rows(const int32_t* rows, int64_t num_rows, i
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
-    // rows per tile: input plus output tile, each padded to 16 bytes
-    const size_t per_row = (size_t)walk_len * (1 + 2 * (size_t)window) * sizeof(int32_t);
-    const int R = (int)std::min<size_t>(64, (kCtxSmemBytes - 32) / per_row);
+    // rows per tile: the staged rows fit the block's shared memory and the
+    // tile's outputs stay below 2^24 entries (small_div's range)
+    const size_t row_bytes = (size_t)walk_len * sizeof(int32_t);
+    const long long out_per_row = (long long)walk_len * 2 * window;
+    const long long r_smem = (long long)(kCtxSmemBytes / row_bytes);
+    const long long r_out = ((1LL << 24) - 1) / out_per_row;
+    const int R = (int)std::min<long long>(64, std::min(r_smem, r_out));
     if (R >= 1) {
-        const size_t smem = (((size_t)R * walk_len + 3) & ~(size_t)3) * sizeof(int32_t) +
-                            (size_t)R * walk_len * 2 * window * sizeof(int32_t);
+        const size_t smem = (size_t)R * row_bytes;
         const long long tiles = (num_rows + R - 1) / R;
-        const int blocks = (int)std::min<long long>(tiles, (long long)sms * 8);
+        const int blocks = (int)std::min<long long>(tiles, (long long)sms * 16);
         contexts_tiled_kernel<<<blocks, kCtxThreads, smem, stream>>>(rows, num_rows, walk_len,
                                                                     window, R, contexts);
     } else {
