@@ -18,6 +18,10 @@ complete graphs and stars; stationarity of p = q = 1 walks; the trial-cap
 fallback against the same exact law; and the context windows against a worked
 example, an independent sliding-window construction, a closed-form count and
 their symmetry.
+
+``elias_fano.py`` is the oracle of the Elias-Fano graph store (plain Python and
+numpy): the edge encoding phi_k, the low/high split, the quantum indexes, and
+rank and select, pinned in ``tests/test_oracle_ef.py``.
 """
 from __future__ import annotations
 
