@@ -48,6 +48,11 @@ grape_status_t make_walk_const(const grape_graph* g, const int32_t* starts, int6
                                int32_t walk_len, int32_t walks_per_node, double p, double q,
                                uint64_t seed, int32_t* out, WalkConst* wc);
 
+// The same for a graph of num_nodes nodes held in another store.
+grape_status_t make_walk_const_n(int64_t num_nodes, const int32_t* starts, int64_t num_starts,
+                                 int32_t walk_len, int32_t walks_per_node, double p, double q,
+                                 uint64_t seed, int32_t* out, WalkConst* wc);
+
 // Restrict wc to the walk ids [walk_begin, walk_begin + walk_count).
 grape_status_t restrict_walks(WalkConst* wc, int64_t walk_begin, int64_t walk_count);
 

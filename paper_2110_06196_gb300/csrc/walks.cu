@@ -203,10 +203,18 @@ namespace grape {
 grape_status_t make_walk_const(const grape_graph* g, const int32_t* starts, int64_t num_starts,
                                int32_t walk_len, int32_t walks_per_node, double p, double q,
                                uint64_t seed, int32_t* out, WalkConst* wc) {
-    if (!g || !out || !wc || num_starts < 1 || walk_len < 1 || walks_per_node < 1 ||
+    if (!g) return GRAPE_ERR_INVALID_ARG;
+    return make_walk_const_n(g->n, starts, num_starts, walk_len, walks_per_node, p, q, seed, out,
+                             wc);
+}
+
+grape_status_t make_walk_const_n(int64_t num_nodes, const int32_t* starts, int64_t num_starts,
+                                 int32_t walk_len, int32_t walks_per_node, double p, double q,
+                                 uint64_t seed, int32_t* out, WalkConst* wc) {
+    if (!out || !wc || num_starts < 1 || walk_len < 1 || walks_per_node < 1 ||
         !valid_pq(p) || !valid_pq(q))
         return GRAPE_ERR_INVALID_ARG;
-    if (!starts && num_starts > g->n) return GRAPE_ERR_INVALID_ARG;
+    if (!starts && num_starts > num_nodes) return GRAPE_ERR_INVALID_ARG;
     if (num_starts > (INT64_MAX / walks_per_node) / walk_len) return GRAPE_ERR_INVALID_ARG;
     std::memset(wc, 0, sizeof(*wc));
     wc->starts = starts;
