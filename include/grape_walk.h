@@ -441,6 +441,129 @@ grape_status_t grape_walk_server_stats(grape_server_t* server, grape_server_stat
 void grape_walk_server_destroy(grape_server_t* server);
 
 /* ------------------------------------------------------------------------ */
+/* Elias-Fano graph store                                                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A graph held as the Elias-Fano representation of its edge codes (GRAPE,
+ * Methods, "Succinct data structures for adjacency matrices"), for graphs whose
+ * CSR and proposal entries would not fit the device: about
+ * 2 + floor(log2(u / m)) bits per CSR entry plus the indexes, against 36 bytes
+ * per entry for grape_graph_t.
+ *   - Edge Encoding: k = ceil(log2 num_nodes); the entry (a, b) is the code
+ *     phi_k(a, b) = a * 2^k + b; u = num_nodes * 2^k.
+ *   - Elias-Fano of the m sorted codes: l = floor(log2(u / m)) low bits per
+ *     code (0 when u <= m), packed least significant bit first, code i at bits
+ *     [i l, (i + 1) l) of the low array; the high parts in the high array as
+ *     the inverted unary codes of their gaps, code i's one at bit
+ *     (code_i >> l) + i, followed by the zeros that close every bucket up to
+ *     (u - 1) >> l (Z = ((u - 1) >> l) + 1 zeros in all, zero j closing bucket j).
+ *     Bit b of an array is bit b mod 64 of its 64-bit word b / 64.
+ *   - Indexes ("Efficient implementation of Elias-Fano"): the positions of one
+ *     number j * quantum (j < ceil(m / quantum)) and of zero number j * quantum
+ *     (j < ceil(Z / quantum)).  The paper uses quantum 1024.
+ *   - rank(c) = number of codes below c; select(i) = the i-th smallest code
+ *     (0-based); deg(a) = rank(phi(a + 1, 0)) - rank(phi(a, 0)) ("Operations on
+ *     Elias-Fano").
+ */
+typedef struct grape_ef_graph grape_ef_graph_t;
+
+#define GRAPE_EF_PAPER_QUANTUM 1024
+
+/*
+ * Build the store from a device CSR laid out as in Conventions (the same
+ * arguments as grape_graph_create), on `stream`, synchronising it.  The CSR is
+ * always checked first (the store's layout is computed from the ids):
+ * GRAPE_ERR_INVALID_GRAPH for bad offsets, ids out of range, rows not strictly
+ * increasing, or weights not finite or <= 0.  The caller keeps its buffers.
+ *   quantum: a power of two in [1, 65536].  num_entries <= 2^40.
+ *   flags: GRAPE_UNDIRECTED and GRAPE_VALIDATE are accepted and change nothing.
+ *   Weighted graphs also hold the weights (fp32 per entry) and each row's
+ *   largest weight (fp32 per node) uncompressed.
+ *   *out receives the store on GRAPE_OK, and NULL otherwise.
+ */
+grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts,
+                                     const float* weights, int64_t num_nodes,
+                                     int64_t num_entries, int32_t quantum, uint32_t flags,
+                                     grape_stream_t stream, grape_ef_graph_t** out);
+
+/* Free the store (synchronises the device first).  NULL is a no-op. */
+void grape_ef_graph_destroy(grape_ef_graph_t* graph);
+
+typedef struct grape_ef_info {
+    int64_t num_nodes;
+    int64_t num_entries;       /* m, the number of codes */
+    int64_t universe;          /* u = num_nodes * 2^k */
+    int64_t num_zeros;         /* Z */
+    int64_t high_bits;         /* m + Z */
+    int64_t low_words;         /* ceil(m l / 64) 64-bit words */
+    int64_t high_words;        /* ceil((m + Z) / 64) 64-bit words */
+    int64_t ones_index_len;    /* ceil(m / quantum) */
+    int64_t zeros_index_len;   /* ceil(Z / quantum) */
+    int64_t structure_bytes;   /* device bytes of the bit arrays (padding included) and indexes */
+    int64_t device_bytes;      /* structure_bytes plus the weights and row maxima */
+    int32_t code_bits;         /* k */
+    int32_t low_bits;          /* l */
+    int32_t quantum;
+    int32_t weighted;
+    int32_t max_degree;
+    int32_t pad;
+} grape_ef_info_t;
+
+grape_status_t grape_ef_graph_info(const grape_ef_graph_t* graph, grape_ef_info_t* info);
+
+/*
+ * Copy the store's arrays into caller-owned device buffers of the lengths in
+ * grape_ef_info_t (low_words, high_words, ones_index_len, zeros_index_len
+ * elements; the padding is not copied).  Any pointer may be NULL to skip that
+ * array.  Enqueued on `stream`.
+ */
+grape_status_t grape_ef_graph_export(const grape_ef_graph_t* graph, uint64_t* low,
+                                     uint64_t* high, int64_t* ones_index, int64_t* zeros_index,
+                                     grape_stream_t stream);
+
+/*
+ * out[j] = select(idx[j]), the idx[j]-th smallest code, for n indexes (device
+ * int64 arrays).  An index outside [0, m) gives -1 and sets the status word.
+ */
+grape_status_t grape_ef_select(const grape_ef_graph_t* graph, const int64_t* idx, int64_t n,
+                               int64_t* out, grape_stream_t stream);
+
+/* out[j] = rank(values[j]), the number of codes below values[j] (0 for values <= 0, m for values >= u). */
+grape_status_t grape_ef_rank(const grape_ef_graph_t* graph, const int64_t* values, int64_t n,
+                             int64_t* out, grape_stream_t stream);
+
+/*
+ * The walks of grape_walks (same arguments, same rule, byte-identical rows for
+ * the same CSR, starts, p, q, seed and trial_cap) read from the Elias-Fano
+ * store: each proposal is a select, each degree two ranks, each membership
+ * test a rank.  trial_cap in [0, 2^31 - 1] (grape_tuning_t's default is 4096).
+ * Starts out of range give -1 rows and set the store's status word.
+ */
+grape_status_t grape_ef_walks(const grape_ef_graph_t* graph, const int32_t* starts,
+                              int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                              double p, double q, uint64_t seed, int64_t trial_cap,
+                              int32_t* out, grape_stream_t stream);
+
+/* Synchronise `stream`, read and clear the store's status word (GRAPE_ERR_DEVICE if set). */
+grape_status_t grape_ef_stream_status(const grape_ef_graph_t* graph, grape_stream_t stream);
+
+/* Work counters of grape_ef_walks (counting launches only; enabling clears them). */
+typedef struct grape_ef_counters {
+    int64_t steps;             /* transitions taken */
+    int64_t trials;            /* proposals drawn (Philox blocks) */
+    int64_t codes_read;        /* proposals whose code was selected */
+    int64_t membership_tests;  /* class-deciding tests x in N(t) */
+    int64_t sectors;           /* distinct 32-byte sectors read by each select, rank and weight load, summed */
+    int64_t fallbacks;         /* steps drawn by the cumulative-sum fallback */
+    int64_t walks;             /* walks started from a valid start */
+} grape_ef_counters_t;
+
+grape_status_t grape_ef_counters_enable(grape_ef_graph_t* graph, int32_t enable);
+/* Synchronises the device, copies the counters out and clears them. */
+grape_status_t grape_ef_counters_read(grape_ef_graph_t* graph, grape_ef_counters_t* out);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics                                                               */
 /* ------------------------------------------------------------------------ */
 
