@@ -104,6 +104,8 @@ class EliasFano:
             pos += 1
             prev = int(high[i])
         self.high_bitarray = H
+        self._H = H.tolist()                    # plain list: the scans index it bit by bit
+        self._low_list = self.low_bitarray.tolist()
         self.low_words = _pack_words(self.low_bitarray)
         self.high_words = _pack_words(self.high_bitarray)
         ones = np.flatnonzero(H == 1)
@@ -122,14 +124,14 @@ class EliasFano:
     def low(self, i: int) -> int:
         v = 0
         for j in range(self.l):
-            v |= int(self.low_bitarray[i * self.l + j]) << j
+            v |= self._low_list[i * self.l + j] << j
         return v
 
     def _scan(self, start: int, bit: int, count: int) -> int:
         """Position of the count-th (0-based) `bit` at or after `start`."""
         p = start
         seen = -1
-        H = self.high_bitarray
+        H = self._H
         while True:
             if H[p] == bit:
                 seen += 1
@@ -169,7 +171,7 @@ class EliasFano:
         # one before that position belongs to a value with high part < h
         p = 0 if h == 0 else self.select0(h - 1) + 1
         i = p - h
-        H = self.high_bitarray
+        H = self._H
         while H[p] == 1 and self.low(i) < lo:   # bucket h ends at its closing zero
             i += 1
             p += 1

@@ -75,6 +75,27 @@ class ServerStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class EFInfo(ctypes.Structure):
+    _fields_ = [("num_nodes", c_i64), ("num_entries", c_i64), ("universe", c_i64),
+                ("num_zeros", c_i64), ("high_bits", c_i64), ("low_words", c_i64),
+                ("high_words", c_i64), ("ones_index_len", c_i64), ("zeros_index_len", c_i64),
+                ("structure_bytes", c_i64), ("device_bytes", c_i64), ("code_bits", c_i32),
+                ("low_bits", c_i32), ("quantum", c_i32), ("weighted", c_i32),
+                ("max_degree", c_i32), ("pad", c_i32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+class EFCounters(ctypes.Structure):
+    _fields_ = [("steps", c_i64), ("trials", c_i64), ("codes_read", c_i64),
+                ("membership_tests", c_i64), ("sectors", c_i64), ("fallbacks", c_i64),
+                ("walks", c_i64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # name -> (restype, argtypes); mirrors include/grape_walk.h
 SIGNATURES = {
     "grape_status_string": (ctypes.c_char_p, [c_i32]),
@@ -111,6 +132,17 @@ SIGNATURES = {
                                    c_vp, c_vp]),
     "grape_walk_contexts": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_i32,
                                     c_i64, c_i64, c_vp, c_vp, c_vp]),
+    "grape_ef_graph_create": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i32, c_u32, c_vp, c_vp]),
+    "grape_ef_graph_destroy": (None, [c_vp]),
+    "grape_ef_graph_info": (c_i32, [c_vp, c_vp]),
+    "grape_ef_graph_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "grape_ef_select": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "grape_ef_rank": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "grape_ef_walks": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_i64, c_vp,
+                               c_vp]),
+    "grape_ef_stream_status": (c_i32, [c_vp, c_vp]),
+    "grape_ef_counters_enable": (c_i32, [c_vp, c_i32]),
+    "grape_ef_counters_read": (c_i32, [c_vp, c_vp]),
 }
 
 _lock = threading.Lock()

@@ -1,0 +1,860 @@
+// ef.cu -- the Elias-Fano graph store and node2vec walks over it.
+//
+// GRAPE, Methods, "Succinct data structures for adjacency matrices":
+//   * Edge Encoding: the edge (a, b) becomes phi_k(a, b) = a * 2^k + b with
+//     k = ceil(log2 |V|), so the codes of N(a) are the sorted run in
+//     [phi_k(a, 0), phi_k(a + 1, 0)); every code is below u = |V| * 2^k.
+//   * Efficient implementation of Elias-Fano: l = floor(log2(u / m)) low bits
+//     of each code in a packed array; the high parts as the inverted unary
+//     codes of their gaps; the positions of every q-th one and every q-th zero
+//     of the high bits as indexes, from which a select scans forward.
+//   * Operations on Elias-Fano: rank(c) = number of codes below c, select(i)
+//     = the i-th smallest code; deg(a) = rank(phi(a + 1, 0)) - rank(phi(a, 0))
+//     and N(a) = select(i) & (2^k - 1) over that range.
+//
+// Layout (64-bit words; bit b of an array is bit b mod 64 of word b / 64):
+//   low[]         code i's l low bits at bits [i l, (i + 1) l), least significant first
+//   high[]        code i's one at bit (code_i >> l) + i; Z = ((u - 1) >> l) + 1 zeros,
+//                 zero j closing bucket j (it follows every code whose high part is <= j)
+//   ones_index[]  position of one number j q,   j < ceil(m / q)
+//   zeros_index[] position of zero number j q,  j < ceil(Z / q)
+// Both bit arrays carry four words of zero padding.
+//
+// Walks over the store follow the same rule as the CSR engine (rejection
+// against max(1/p, 1, 1/q) * wmax_v with Philox blocks keyed by (seed, walk,
+// step, trial), then the cumulative-sum fallback), so their rows are
+// byte-identical to grape_walks' rows for the same graph.  One thread owns one
+// walk; every neighbour, degree and membership test is a select or rank on the
+// compressed store.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace grape;
+
+struct grape_ef_graph {
+    int64_t n = 0, m = 0, u = 0;
+    int32_t k = 0, l = 0, quantum = 0, qlog = 0;
+    int64_t num_zeros = 0, high_bits = 0;
+    int64_t low_words = 0, high_words = 0, ones_len = 0, zeros_len = 0;
+    int32_t max_degree = 0;
+    bool weighted = false;
+    int device = 0, num_sms = 0;
+    unsigned long long* low = nullptr;
+    unsigned long long* high = nullptr;
+    long long* ones_idx = nullptr;
+    long long* zeros_idx = nullptr;
+    float* weights = nullptr;
+    float* wmax = nullptr;
+    int* status = nullptr;                    // [0] device status word, [1] bad flags, [2] max degree
+    unsigned long long* counters = nullptr;   // [C_COUNT]
+    bool counting = false;
+    int64_t device_bytes = 0, structure_bytes = 0;
+};
+
+namespace {
+
+constexpr int kEFThreads = 256;
+constexpr int kPadWords = 4;
+
+struct EFDev {
+    const unsigned long long* low;
+    const unsigned long long* high;
+    const long long* ones_idx;
+    const long long* zeros_idx;
+    const float* weights;
+    const float* wmax;
+    long long m, n, u;
+    long long hwords;           // high-bit words, padding included
+    int k, l, qlog;
+    int* status;                // bit 0: a start id out of range; bit 1: an inconsistent store
+    unsigned long long* counters;
+};
+
+EFDev dev_view(const grape_ef_graph* g) {
+    EFDev d;
+    d.low = g->low;
+    d.high = g->high;
+    d.ones_idx = g->ones_idx;
+    d.zeros_idx = g->zeros_idx;
+    d.weights = g->weights;
+    d.wmax = g->wmax;
+    d.m = g->m;
+    d.n = g->n;
+    d.u = g->u;
+    d.hwords = g->high_words + kPadWords;
+    d.k = g->k;
+    d.l = g->l;
+    d.qlog = g->qlog;
+    d.status = g->status;
+    d.counters = g->counting ? g->counters : nullptr;
+    return d;
+}
+
+int ef_grid(int num_sms, long long items, int per_block) {
+    const long long b = (items + per_block - 1) / per_block;
+    return (int)std::max(1LL, std::min(b, (long long)num_sms * 32));
+}
+
+// ---------------------------------------------------------------------------
+// Building the store from a device CSR
+// ---------------------------------------------------------------------------
+__global__ void ef_check_offsets_kernel(const int64_t* __restrict__ offsets, long long n,
+                                        long long m, int* bad) {
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a <= n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const long long o = offsets[a];
+        bool ok = o >= 0 && o <= m;
+        if (a == 0) ok = ok && o == 0;
+        if (a == n) ok = ok && o == m;
+        if (a < n) ok = ok && offsets[a + 1] >= o;
+        if (!ok) atomicOr(bad, 1);
+    }
+}
+
+// One warp per row: ids in range, rows strictly increasing, weights finite and
+// > 0; the largest degree and each row's largest weight.
+__global__ void ef_check_rows_kernel(const int64_t* __restrict__ offsets,
+                                     const int32_t* __restrict__ dsts,
+                                     const float* __restrict__ weights, long long n,
+                                     float* __restrict__ wmax, int* bad, int* max_deg) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long a = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+        const long long lo = offsets[a], hi = offsets[a + 1];
+        bool ok = true;
+        float wm = 0.0f;
+        for (long long e = lo + lane; e < hi; e += 32) {
+            const int x = dsts[e];
+            ok = ok && x >= 0 && x < n;
+            if (e + 1 < hi) ok = ok && dsts[e + 1] > x;
+            if (weights) {
+                const float w = weights[e];
+                ok = ok && isfinite(w) && w > 0.0f;
+                wm = fmaxf(wm, w);
+            }
+        }
+        if (!__all_sync(FULL, ok) && lane == 0) atomicOr(bad, 1);
+        if (weights) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(FULL, wm, o));
+            if (lane == 0) wmax[a] = wm;
+        }
+        if (lane == 0) {
+            const long long d = hi - lo;
+            atomicMax(max_deg, (int)(d < INT32_MAX ? d : INT32_MAX));
+        }
+    }
+}
+
+// One warp per row: OR each code's low bits and its high-part one into the
+// zeroed arrays.  Codes and positions depend only on the CSR, so the words do
+// not depend on the order of the ORs.
+__global__ void ef_fill_kernel(const int64_t* __restrict__ offsets,
+                               const int32_t* __restrict__ dsts, long long n, int k, int l,
+                               unsigned long long* __restrict__ low,
+                               unsigned long long* __restrict__ high) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long lmask = l ? ((1ull << l) - 1) : 0ull;
+    for (long long a = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+        const long long lo = offsets[a], hi = offsets[a + 1];
+        for (long long e = lo + lane; e < hi; e += 32) {
+            const unsigned long long c = ((unsigned long long)a << k) | (unsigned)dsts[e];
+            const unsigned long long pos = (c >> l) + (unsigned long long)e;
+            atomicOr(high + (pos >> 6), 1ull << (pos & 63));
+            if (l) {
+                const unsigned long long bits = c & lmask;
+                const unsigned long long b = (unsigned long long)e * (unsigned)l;
+                const int s = (int)(b & 63);
+                if (bits) {
+                    atomicOr(low + (b >> 6), bits << s);
+                    if (s + l > 64) atomicOr(low + (b >> 6) + 1, bits >> (64 - s));
+                }
+            }
+        }
+    }
+}
+
+// Number of codes below c, from the CSR (c < u): offsets[a] plus the position
+// of b in the sorted row a.
+__device__ long long csr_rank(const int64_t* __restrict__ offsets, const int32_t* __restrict__ dsts,
+                              long long n, int k, unsigned long long c) {
+    const long long a = (long long)(c >> k);
+    if (a >= n) return offsets[n];
+    const int b = (int)(c & ((1ull << k) - 1));
+    long long lo = offsets[a], hi = offsets[a + 1];
+    while (lo < hi) {                          // first entry >= b
+        const long long mid = lo + ((hi - lo) >> 1);
+        if (dsts[mid] < b) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Index entries.  One number j q (code e = j q of row a) sits at
+// (code >> l) + e.  Zero number z closes bucket z: it follows the codes whose
+// high part is <= z, that is the codes below (z + 1) 2^l, so it sits at
+// z + rank((z + 1) 2^l).
+__global__ void ef_index_kernel(const int64_t* __restrict__ offsets,
+                                const int32_t* __restrict__ dsts, long long n, int k, int l,
+                                int qlog, long long ones_len, long long zeros_len,
+                                unsigned long long u, long long* __restrict__ ones_idx,
+                                long long* __restrict__ zeros_idx) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < ones_len + zeros_len;
+         j += (long long)gridDim.x * blockDim.x) {
+        if (j < ones_len) {
+            const long long e = j << qlog;
+            long long lo = 0, hi = n;                // row of entry e: last a with offsets[a] <= e
+            while (hi - lo > 1) {
+                const long long mid = lo + ((hi - lo) >> 1);
+                if (offsets[mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            const unsigned long long c = ((unsigned long long)lo << k) | (unsigned)dsts[e];
+            ones_idx[j] = (long long)((c >> l) + (unsigned long long)e);
+        } else {
+            const long long z = (j - ones_len) << qlog;
+            const unsigned long long lim = (unsigned long long)(z + 1) << l;
+            const long long r = lim >= u ? offsets[n] : csr_rank(offsets, dsts, n, k, lim);
+            zeros_idx[j - ones_len] = z + r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// select and rank on the device
+// ---------------------------------------------------------------------------
+
+// Distinct 32-byte sectors read by one operation (counting kernels only).
+template <bool ON>
+struct Tally {
+    unsigned long long last = ~0ull;
+    unsigned sectors = 0;
+    __device__ __forceinline__ void begin() { last = ~0ull; }
+    __device__ __forceinline__ void touch(const void* p) {
+        const unsigned long long s = reinterpret_cast<uintptr_t>(p) >> 5;
+        if (s != last) {
+            last = s;
+            ++sectors;
+        }
+    }
+};
+template <>
+struct Tally<false> {
+    __device__ __forceinline__ void begin() {}
+    __device__ __forceinline__ void touch(const void*) {}
+};
+
+// Position of the r-th (0-based) set bit of x; x has more than r set bits.
+__device__ __forceinline__ int nth_set_bit(unsigned long long x, int r) {
+    int pos = 0;
+    unsigned w = (unsigned)x;
+    int c = __popc(w);
+    if (r >= c) {
+        r -= c;
+        w = (unsigned)(x >> 32);
+        pos = 32;
+    }
+    c = __popc(w & 0xffffu);
+    if (r >= c) { r -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xffu);
+    if (r >= c) { r -= c; w >>= 8; pos += 8; }
+    c = __popc(w & 0xfu);
+    if (r >= c) { r -= c; w >>= 4; pos += 4; }
+    c = __popc(w & 0x3u);
+    if (r >= c) { r -= c; w >>= 2; pos += 2; }
+    if (r >= (int)(w & 1u)) pos += 1;
+    return pos;
+}
+
+// Position of the r-th one (ONES) or zero at or after bit p of the high bits.
+// A scan that would leave the array (an inconsistent store) stops, sets
+// status bit 1 and returns the array's end.
+template <bool ONES, bool C>
+__device__ __forceinline__ long long scan_high(const EFDev& g, long long p, long long r,
+                                               Tally<C>& ty) {
+    long long w = p >> 6;
+    if (p < 0 || w >= g.hwords) {
+        atomicOr(g.status, 2);
+        return g.hwords << 6;
+    }
+    ty.touch(g.high + w);
+    unsigned long long x = __ldg(g.high + w);
+    if (!ONES) x = ~x;
+    x &= ~0ull << (p & 63);
+    while (true) {
+        const int c = __popcll(x);
+        if (r < c) return (w << 6) + nth_set_bit(x, (int)r);
+        r -= c;
+        if (++w >= g.hwords) {
+            atomicOr(g.status, 2);
+            return g.hwords << 6;
+        }
+        ty.touch(g.high + w);
+        x = __ldg(g.high + w);
+        if (!ONES) x = ~x;
+    }
+}
+
+template <bool C>
+__device__ __forceinline__ long long select1(const EFDev& g, long long i, Tally<C>& ty) {
+    ty.touch(g.ones_idx + (i >> g.qlog));
+    const long long p = __ldg(g.ones_idx + (i >> g.qlog));
+    return scan_high<true>(g, p, i & ((1LL << g.qlog) - 1), ty);
+}
+
+template <bool C>
+__device__ __forceinline__ long long select0(const EFDev& g, long long z, Tally<C>& ty) {
+    ty.touch(g.zeros_idx + (z >> g.qlog));
+    const long long p = __ldg(g.zeros_idx + (z >> g.qlog));
+    return scan_high<false>(g, p, z & ((1LL << g.qlog) - 1), ty);
+}
+
+template <bool C>
+__device__ __forceinline__ unsigned long long low_of(const EFDev& g, long long i, Tally<C>& ty) {
+    if (g.l == 0) return 0;
+    const unsigned long long b = (unsigned long long)i * (unsigned)g.l;
+    const long long w = (long long)(b >> 6);
+    const int s = (int)(b & 63);
+    ty.touch(g.low + w);
+    unsigned long long v = __ldg(g.low + w) >> s;
+    if (s + g.l > 64) {
+        ty.touch(g.low + w + 1);
+        v |= __ldg(g.low + w + 1) << (64 - s);
+    }
+    return v & ((1ull << g.l) - 1);
+}
+
+// The i-th smallest code.
+template <bool C>
+__device__ __forceinline__ unsigned long long select_code(const EFDev& g, long long i, Tally<C>& ty) {
+    const unsigned long long h = (unsigned long long)(select1(g, i, ty) - i);
+    return (h << g.l) | low_of(g, i, ty);
+}
+
+// Bit position where bucket h's ones begin (just after the zero closing
+// bucket h - 1); the first code of the bucket is number (position - h).
+template <bool C>
+__device__ __forceinline__ long long bucket_begin(const EFDev& g, long long h, Tally<C>& ty) {
+    return h == 0 ? 0 : select0(g, h - 1, ty) + 1;
+}
+
+// Codes below c (0 <= c), and whether c itself is stored.
+template <bool C>
+__device__ long long rank_code(const EFDev& g, unsigned long long c, bool& found, Tally<C>& ty) {
+    found = false;
+    if ((long long)c >= g.u) return g.m;
+    const long long h = (long long)(c >> g.l);
+    const unsigned long long lo = g.l ? (c & ((1ull << g.l) - 1)) : 0ull;
+    const long long p = bucket_begin(g, h, ty);
+    const long long i0 = p - h;
+    // length of bucket h: the run of ones from p (the word at p, then the
+    // zeros index when the run reaches the end of that word)
+    const long long w = p >> 6;
+    if (w >= g.hwords) {                        // an inconsistent store (scan_high flagged it)
+        atomicOr(g.status, 2);
+        return g.m;
+    }
+    ty.touch(g.high + w);
+    const unsigned long long x = __ldg(g.high + w) >> (p & 63);
+    const int room = 64 - (int)(p & 63);
+    int run = (~x == 0ull) ? 64 : __ffsll((long long)~x) - 1;
+    long long len;
+    if (run < room) len = run;
+    else len = select0(g, h, ty) - p;          // the zero closing bucket h
+    if (i0 < 0 || len < 0 || i0 + len > g.m) {
+        atomicOr(g.status, 2);
+        return g.m;
+    }
+    if (len == 0) return i0;
+    if (lo == 0) {
+        found = (low_of(g, i0, ty) == 0);
+        return i0;
+    }
+    // first code of the bucket whose low part is >= lo (lows increase within a bucket)
+    long long a = i0, b = i0 + len;
+    while (a < b) {
+        const long long mid = a + ((b - a) >> 1);
+        if (low_of(g, mid, ty) < lo) a = mid + 1;
+        else b = mid;
+    }
+    found = (a < i0 + len) && low_of(g, a, ty) == lo;
+    return a;
+}
+
+// First code of row a and its degree (a row that does not fit inside the
+// codes, from an inconsistent store, reads as empty and sets status bit 1).
+template <bool C>
+__device__ __forceinline__ void row_of(const EFDev& g, long long a, long long& off, int& deg,
+                                       Tally<C>& ty) {
+    bool f;
+    off = rank_code(g, (unsigned long long)a << g.k, f, ty);
+    const long long end = rank_code(g, (unsigned long long)(a + 1) << g.k, f, ty);
+    deg = (int)(end - off);
+    if (off < 0 || end < off || end > g.m || end - off > 0x7fffffffLL) {
+        atomicOr(g.status, 2);
+        off = 0;
+        deg = 0;
+    }
+}
+
+__global__ void ef_select_kernel(EFDev g, const long long* __restrict__ idx, long long n,
+                                 long long* __restrict__ out) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx[j];
+        Tally<false> ty;
+        if (i < 0 || i >= g.m) {
+            out[j] = -1;
+            atomicOr(g.status, 1);
+        } else {
+            out[j] = (long long)select_code(g, i, ty);
+        }
+    }
+}
+
+__global__ void ef_rank_kernel(EFDev g, const long long* __restrict__ vals, long long n,
+                               long long* __restrict__ out) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long c = vals[j];
+        Tally<false> ty;
+        bool f;
+        out[j] = c <= 0 ? 0 : rank_code(g, (unsigned long long)c, f, ty);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Walks
+// ---------------------------------------------------------------------------
+
+// Is x in N(t)?
+template <bool C>
+__device__ __forceinline__ bool ef_has_edge(const EFDev& g, int t, int x, Tally<C>& ty) {
+    bool found;
+    rank_code(g, ((unsigned long long)t << g.k) | (unsigned)x, found, ty);
+    return found;
+}
+
+__device__ __forceinline__ int ef_target(const EFDev& g, unsigned long long code) {
+    return (int)(code & ((1ull << g.k) - 1));
+}
+
+// The exact fallback after trial_cap rejections: inverse transform over the
+// cumulative sum of pi in row order (GRAPE, "Efficient sampling for Node2Vec
+// RWs"), every fp64 product and sum rounded separately; the uniform comes from
+// the Philox block of trial index trial_cap.  Returns a position in N(v).
+template <bool WEIGHTED, bool C>
+__device__ int ef_fallback(const EFDev& g, long long w, int s, unsigned long long seed, int t,
+                           long long off_v, int deg_v, double a_ret, double a_out,
+                           unsigned trial_cap, Tally<C>& ty) {
+    const uint4 r = trial_block(seed, w, s, trial_cap);
+    double total = 0.0;
+    for (int j = 0; j < deg_v; ++j) {
+        const int x = ef_target(g, select_code(g, off_v + j, ty));
+        double a = 1.0;
+        if (t >= 0) a = (x == t) ? a_ret : (ef_has_edge(g, t, x, ty) ? 1.0 : a_out);
+        const double wv = WEIGHTED ? (double)__ldg(g.weights + off_v + j) : 1.0;
+        total = __dadd_rn(total, __dmul_rn(a, wv));
+    }
+    const unsigned long long r64 = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+    const double u = __dmul_rn(__dmul_rn((double)(r64 >> 11), 0x1p-53), total);
+    double run = 0.0;
+    for (int j = 0; j < deg_v; ++j) {
+        const int x = ef_target(g, select_code(g, off_v + j, ty));
+        double a = 1.0;
+        if (t >= 0) a = (x == t) ? a_ret : (ef_has_edge(g, t, x, ty) ? 1.0 : a_out);
+        const double wv = WEIGHTED ? (double)__ldg(g.weights + off_v + j) : 1.0;
+        run = __dadd_rn(run, __dmul_rn(a, wv));
+        if (run > u) return j;
+    }
+    return deg_v - 1;
+}
+
+// One thread per walk (grid-stride over the launch's rows).  Rows are staged
+// per thread in a 32-byte slot of shared memory and leave as whole sectors
+// (put / fill_dead of the CSR engine).
+template <bool WEIGHTED, bool COUNT>
+__global__ void __launch_bounds__(kEFThreads)
+ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap) {
+    Counts<COUNT> cnt;
+    cnt.clear();
+    Tally<COUNT> ty;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < wc.num_walks;
+         row += stride) {
+        const long long w = wc.walk_base + row;
+        int* const rowp = wc.out + row * (long long)wc.walk_len;
+        const int len = wc.walk_len;
+        Lane L;
+        L.flags = (wc.out_vec ? F_VEC : 0u) |
+                  ((unsigned)((row * (long long)len) & 7) << F_PHASE_SHIFT);
+        const long long i = w % wc.num_starts;
+        const long long v0 = wc.starts ? (long long)__ldg(wc.starts + i) : i;
+        if (v0 < 0 || v0 >= g.n) {
+            atomicOr(g.status, 1);
+            fill_dead(L, rowp, 0, len);
+            continue;
+        }
+        cnt.add(C_WALKS);
+        put(L, rowp, 0, (int)v0, len);
+        int v = (int)v0, t = -1;
+        long long off_v;
+        int deg_v;
+        ty.begin();
+        row_of(g, v, off_v, deg_v, ty);
+        float wmax_v = 0.0f;
+        if (WEIGHTED) {
+            ty.touch(g.wmax + v);
+            wmax_v = __ldg(g.wmax + v);
+        }
+        int s = 1;
+        for (; s < len && deg_v > 0; ++s) {
+            int x = -1;
+            long long e = -1;
+            unsigned k = 0;
+            for (; k < trial_cap; ++k) {
+                const uint4 r = trial_block(wc.seed, w, s, k);
+                cnt.add(C_TRIALS);
+                e = off_v + scale_index(r.x, r.y, deg_v);
+                ty.begin();
+                const int cand = ef_target(g, select_code(g, e, ty));
+                cnt.add(C_GATHERS);
+                float wv = 1.0f;
+                if (WEIGHTED) {
+                    ty.touch(g.weights + e);
+                    wv = __ldg(g.weights + e);
+                }
+                bool acc;
+                if (t < 0) {
+                    acc = accept_test<WEIGHTED>(r.z, wmax_v, 0xffffffffu, wv);
+                } else if (cand == t) {
+                    acc = accept_test<WEIGHTED>(r.z, wmax_v, wc.tm1_ret, wv);
+                } else {
+                    bool acc_in, acc_out;
+                    if (WEIGHTED) {
+                        weighted_accept2(r.z, wmax_v, wc.tm1_in, wc.tm1_out, wv, acc_in, acc_out);
+                    } else {
+                        acc_in = r.z <= wc.tm1_in;
+                        acc_out = r.z <= wc.tm1_out;
+                    }
+                    acc = acc_in;
+                    if (acc_in != acc_out) {      // only then does the class decide
+                        cnt.add(C_SEARCHES);
+                        ty.begin();
+                        acc = ef_has_edge(g, t, cand, ty) ? acc_in : acc_out;
+                    }
+                }
+                if (acc) {
+                    x = cand;
+                    break;
+                }
+            }
+            if (x < 0) {
+                cnt.add(C_FALLBACKS);
+                const int j = ef_fallback<WEIGHTED>(g, w, s, wc.seed, t, off_v, deg_v, wc.a_ret,
+                                                    wc.a_out, trial_cap, ty);
+                ty.begin();
+                x = ef_target(g, select_code(g, off_v + j, ty));
+            }
+            put(L, rowp, s, x, len);
+            cnt.add(C_STEPS);
+            t = v;
+            v = x;
+            ty.begin();
+            row_of(g, v, off_v, deg_v, ty);
+            if (WEIGHTED) {
+                ty.touch(g.wmax + v);
+                wmax_v = __ldg(g.wmax + v);
+            }
+        }
+        if (s < len) fill_dead(L, rowp, s, len);
+    }
+    if constexpr (COUNT) {
+        if (g.counters) {
+            cnt.c[C_PROBES] = ty.sectors;        // sectors read, in the probes slot
+#pragma unroll
+            for (int c = 0; c < C_COUNT; ++c) {
+                unsigned long long v = cnt.c[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if ((threadIdx.x & 31) == 0 && v) atomicAdd(g.counters + c, v);
+            }
+        }
+    }
+}
+
+template <bool W, bool C>
+cudaError_t launch_walks(const grape_ef_graph* g, const WalkConst& wc, unsigned trial_cap,
+                         cudaStream_t stream) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, ef_walk_kernel<W, C>, kEFThreads, 32 * kEFThreads);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    const long long need = (wc.num_walks + kEFThreads - 1) / kEFThreads;
+    const int blocks = (int)std::max(1LL, std::min(need, (long long)g->num_sms * per_sm));
+    ef_walk_kernel<W, C><<<blocks, kEFThreads, 32 * kEFThreads, stream>>>(dev_view(g), wc,
+                                                                           trial_cap);
+    return cudaGetLastError();
+}
+
+void free_ef(grape_ef_graph* g) {
+    if (!g) return;
+    cudaFree(g->low);
+    cudaFree(g->high);
+    cudaFree(g->ones_idx);
+    cudaFree(g->zeros_idx);
+    cudaFree(g->weights);
+    cudaFree(g->wmax);
+    cudaFree(g->status);
+    cudaFree(g->counters);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts,
+                                     const float* weights, int64_t num_nodes, int64_t num_entries,
+                                     int32_t quantum, uint32_t flags, grape_stream_t stream_,
+                                     grape_ef_graph_t** out) {
+    if (!out) return GRAPE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!offsets || num_nodes < 1 || num_nodes > 0x7fffffffLL || num_entries < 0 ||
+        num_entries > (1LL << 40) || (num_entries > 0 && !dsts) ||
+        quantum < 1 || quantum > (1 << 16) || (quantum & (quantum - 1)) ||
+        (flags & ~(GRAPE_UNDIRECTED | GRAPE_VALIDATE)))
+        return GRAPE_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    grape_ef_graph* g = new (std::nothrow) grape_ef_graph();
+    if (!g) return GRAPE_ERR_NOMEM;
+    g->n = num_nodes;
+    g->m = num_entries;
+    g->weighted = weights != nullptr;
+    g->quantum = quantum;
+    while ((1 << g->qlog) < quantum) ++g->qlog;
+    // k = ceil(log2 |V|); u = |V| 2^k; l = floor(log2(u / m)) (0 when u <= m)
+    while ((1LL << g->k) < num_nodes) ++g->k;
+    g->u = num_nodes << g->k;
+    if (num_entries > 0 && g->u > num_entries) {
+        const long long ratio = g->u / num_entries;     // floor(log2(u/m)) = floor(log2(floor(u/m)))
+        while ((2LL << g->l) <= ratio) ++g->l;
+    }
+    g->num_zeros = ((g->u - 1) >> g->l) + 1;
+    g->high_bits = num_entries + g->num_zeros;
+    g->low_words = (num_entries * g->l + 63) / 64;
+    g->high_words = (g->high_bits + 63) / 64;
+    g->ones_len = (num_entries + quantum - 1) / quantum;
+    g->zeros_len = (g->num_zeros + quantum - 1) / quantum;
+
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    const size_t low_bytes = 8 * (size_t)(g->low_words + kPadWords);
+    const size_t high_bytes = 8 * (size_t)(g->high_words + kPadWords);
+    if (e == cudaSuccess) e = cudaMalloc(&g->low, low_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&g->high, high_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&g->ones_idx, 8 * (size_t)std::max<int64_t>(g->ones_len, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->zeros_idx, 8 * (size_t)g->zeros_len);
+    if (e == cudaSuccess && weights) {
+        e = cudaMalloc(&g->weights, sizeof(float) * (size_t)std::max<int64_t>(num_entries, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&g->wmax, sizeof(float) * (size_t)num_nodes);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * C_COUNT);
+    if (e != cudaSuccess) {
+        free_ef(g);
+        return cuda_status(e);
+    }
+    g->structure_bytes = (int64_t)(low_bytes + high_bytes + 8 * (g->ones_len + g->zeros_len));
+    g->device_bytes = g->structure_bytes +
+                      (weights ? (int64_t)(4 * num_entries + 4 * num_nodes) : 0);
+    int host[4] = {0, 0, 0, 0};
+    e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * C_COUNT, stream);
+    // 1. offsets, then the rows: the store's layout is computed from the ids,
+    //    so the CSR is always checked before anything is written from it
+    if (e == cudaSuccess) {
+        ef_check_offsets_kernel<<<ef_grid(g->num_sms, num_nodes + 1, 256), 256, 0, stream>>>(
+            offsets, num_nodes, num_entries, g->status + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, g->status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess || host[1] != 0) {
+        free_ef(g);
+        return e != cudaSuccess ? cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
+    }
+    if (e == cudaSuccess) {
+        ef_check_rows_kernel<<<ef_grid(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+            offsets, dsts, weights, num_nodes, g->wmax, g->status + 1, g->status + 2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, g->status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess || host[1] != 0) {
+        free_ef(g);
+        return e != cudaSuccess ? cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
+    }
+    g->max_degree = host[2];
+    // 2. the bit arrays and their indexes
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->low, 0, low_bytes, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->high, 0, high_bytes, stream);
+    if (e == cudaSuccess && weights && num_entries > 0)
+        e = cudaMemcpyAsync(g->weights, weights, sizeof(float) * (size_t)num_entries,
+                            cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess) {
+        ef_fill_kernel<<<ef_grid(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+            offsets, dsts, num_nodes, g->k, g->l, g->low, g->high);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        ef_index_kernel<<<ef_grid(g->num_sms, g->ones_len + g->zeros_len, 256), 256, 0, stream>>>(
+            offsets, dsts, num_nodes, g->k, g->l, g->qlog, g->ones_len, g->zeros_len,
+            (unsigned long long)g->u, g->ones_idx, g->zeros_idx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        free_ef(g);
+        return cuda_status(e);
+    }
+    *out = g;
+    return GRAPE_OK;
+}
+
+void grape_ef_graph_destroy(grape_ef_graph_t* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    free_ef(g);
+}
+
+grape_status_t grape_ef_graph_info(const grape_ef_graph_t* g, grape_ef_info_t* info) {
+    if (!g || !info) return GRAPE_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->num_nodes = g->n;
+    info->num_entries = g->m;
+    info->universe = g->u;
+    info->num_zeros = g->num_zeros;
+    info->high_bits = g->high_bits;
+    info->low_words = g->low_words;
+    info->high_words = g->high_words;
+    info->ones_index_len = g->ones_len;
+    info->zeros_index_len = g->zeros_len;
+    info->structure_bytes = g->structure_bytes;
+    info->device_bytes = g->device_bytes;
+    info->code_bits = g->k;
+    info->low_bits = g->l;
+    info->quantum = g->quantum;
+    info->weighted = g->weighted ? 1 : 0;
+    info->max_degree = g->max_degree;
+    return GRAPE_OK;
+}
+
+grape_status_t grape_ef_graph_export(const grape_ef_graph_t* g, uint64_t* low, uint64_t* high,
+                                     int64_t* ones_index, int64_t* zeros_index,
+                                     grape_stream_t stream_) {
+    if (!g) return GRAPE_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e = cudaSuccess;
+    if (low && g->low_words)
+        e = cudaMemcpyAsync(low, g->low, 8 * (size_t)g->low_words, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && high && g->high_words)
+        e = cudaMemcpyAsync(high, g->high, 8 * (size_t)g->high_words, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && ones_index && g->ones_len)
+        e = cudaMemcpyAsync(ones_index, g->ones_idx, 8 * (size_t)g->ones_len,
+                            cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess && zeros_index && g->zeros_len)
+        e = cudaMemcpyAsync(zeros_index, g->zeros_idx, 8 * (size_t)g->zeros_len,
+                            cudaMemcpyDeviceToDevice, stream);
+    return cuda_status(e);
+}
+
+grape_status_t grape_ef_select(const grape_ef_graph_t* g, const int64_t* idx, int64_t n,
+                               int64_t* out, grape_stream_t stream_) {
+    if (!g || n < 0 || (n > 0 && (!idx || !out))) return GRAPE_ERR_INVALID_ARG;
+    if (n == 0) return GRAPE_OK;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    ef_select_kernel<<<ef_grid(g->num_sms, n, 256), 256, 0, stream>>>(
+        dev_view(g), reinterpret_cast<const long long*>(idx), n, reinterpret_cast<long long*>(out));
+    return cuda_status(cudaGetLastError());
+}
+
+grape_status_t grape_ef_rank(const grape_ef_graph_t* g, const int64_t* values, int64_t n,
+                             int64_t* out, grape_stream_t stream_) {
+    if (!g || n < 0 || (n > 0 && (!values || !out))) return GRAPE_ERR_INVALID_ARG;
+    if (n == 0) return GRAPE_OK;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    ef_rank_kernel<<<ef_grid(g->num_sms, n, 256), 256, 0, stream>>>(
+        dev_view(g), reinterpret_cast<const long long*>(values), n,
+        reinterpret_cast<long long*>(out));
+    return cuda_status(cudaGetLastError());
+}
+
+grape_status_t grape_ef_walks(const grape_ef_graph_t* g, const int32_t* starts,
+                              int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                              double p, double q, uint64_t seed, int64_t trial_cap,
+                              int32_t* out, grape_stream_t stream_) {
+    if (!g || trial_cap < 0 || trial_cap > 0x7fffffffLL) return GRAPE_ERR_INVALID_ARG;
+    WalkConst wc;
+    grape_status_t st = make_walk_const_n(g->n, starts, num_starts, walk_len, walks_per_node, p,
+                                          q, seed, out, &wc);
+    if (st != GRAPE_OK) return st;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    cudaError_t e;
+    const unsigned cap = (unsigned)trial_cap;
+    if (g->counting) {
+        e = g->weighted ? launch_walks<true, true>(g, wc, cap, stream)
+                        : launch_walks<false, true>(g, wc, cap, stream);
+    } else {
+        e = g->weighted ? launch_walks<true, false>(g, wc, cap, stream)
+                        : launch_walks<false, false>(g, wc, cap, stream);
+    }
+    return cuda_status(e);
+}
+
+grape_status_t grape_ef_stream_status(const grape_ef_graph_t* g, grape_stream_t stream_) {
+    if (!g) return GRAPE_ERR_INVALID_ARG;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, g->status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return word ? GRAPE_ERR_DEVICE : GRAPE_OK;
+}
+
+grape_status_t grape_ef_counters_enable(grape_ef_graph_t* g, int32_t enable) {
+    if (!g) return GRAPE_ERR_INVALID_ARG;
+    g->counting = enable != 0;
+    return cuda_status(cudaMemset(g->counters, 0, sizeof(unsigned long long) * C_COUNT));
+}
+
+grape_status_t grape_ef_counters_read(grape_ef_graph_t* g, grape_ef_counters_t* out) {
+    if (!g || !out) return GRAPE_ERR_INVALID_ARG;
+    unsigned long long c[C_COUNT];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c, g->counters, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(g->counters, 0, sizeof(c));
+    if (e != cudaSuccess) return cuda_status(e);
+    out->steps = (int64_t)c[C_STEPS];
+    out->trials = (int64_t)c[C_TRIALS];
+    out->codes_read = (int64_t)c[C_GATHERS];
+    out->membership_tests = (int64_t)c[C_SEARCHES];
+    out->sectors = (int64_t)c[C_PROBES];
+    out->fallbacks = (int64_t)c[C_FALLBACKS];
+    out->walks = (int64_t)c[C_WALKS];
+    return GRAPE_OK;
+}
+
+}  // extern "C"

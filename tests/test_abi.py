@@ -52,6 +52,8 @@ STRUCTS = {
     "grape_walk_counters_t": _lib.Counters,
     "grape_server_config_t": _lib.ServerConfig,
     "grape_server_stats_t": _lib.ServerStats,
+    "grape_ef_info_t": _lib.EFInfo,
+    "grape_ef_counters_t": _lib.EFCounters,
 }
 
 
@@ -109,6 +111,20 @@ def test_argument_errors_return_before_cuda(lib):
                                    None) == INVALID
     assert lib.grape_walks_approx(None, None, 4, 8, 1, 1.0, 1.0, 0, -1, None, None) == INVALID
     assert lib.grape_walks_approx(None, None, 4, 8, 1, 1.0, 1.0, 0, 3, None, None) == INVALID
+    # Elias-Fano store: bad sizes, quanta that are not powers of two, null store
+    for quantum in (0, 3, 1 << 17):
+        assert lib.grape_ef_graph_create(ctypes.c_void_p(8), ctypes.c_void_p(8), None, 4, 4,
+                                         quantum, 0, None, ctypes.byref(h)) == INVALID
+    assert lib.grape_ef_graph_create(None, None, None, 4, 0, 64, 0, None, ctypes.byref(h)) == INVALID
+    assert lib.grape_ef_graph_create(ctypes.c_void_p(8), None, None, 4, 4, 64, 0, None,
+                                     ctypes.byref(h)) == INVALID
+    assert lib.grape_ef_graph_create(ctypes.c_void_p(8), ctypes.c_void_p(8), None, 4, (1 << 40) + 1,
+                                     64, 0, None, ctypes.byref(h)) == INVALID
+    assert lib.grape_ef_walks(None, None, 4, 8, 1, 1.0, 1.0, 0, 4096, None, None) == INVALID
+    assert lib.grape_ef_select(None, None, 1, None, None) == INVALID
+    assert lib.grape_ef_rank(None, None, 1, None, None) == INVALID
+    assert lib.grape_ef_graph_info(None, None) == INVALID
+    lib.grape_ef_graph_destroy(None)
     lib.grape_graph_destroy(None)
     lib.grape_walk_server_destroy(None)
     lib.grape_batch_plan_destroy(None)
