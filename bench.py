@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-contexts", action="store_true")
+    ap.add_argument("--ef-quanta", default="64,1024",
+                    help="Elias-Fano store leg: index quanta to build and walk ('' to skip)")
     ap.add_argument("--suss-k", type=int, default=0,
                     help="also time the workload's approximated walks (SUSS sub-samples of k "
                          "neighbours at nodes of degree above k)")
@@ -197,10 +199,14 @@ def profiled_traffic(workload):
 
 
 def count_steps(out: torch.Tensor) -> int:
-    """Transitions taken: valid entries minus one start per row with a valid start."""
-    valid = int((out >= 0).sum())
-    starts = int((out[:, 0] >= 0).sum())
-    return valid - starts
+    """Transitions taken: valid entries minus one start per row with a valid start
+    (counted in slices of rows, so no temporary grows with the job)."""
+    total = 0
+    step = max(1, (1 << 28) // max(1, out.shape[1]))
+    for b in range(0, out.shape[0], step):
+        part = out[b:b + step]
+        total += int((part >= 0).sum(dtype=torch.int64)) - int((part[:, 0] >= 0).sum(dtype=torch.int64))
+    return total
 
 
 def algorithmic_bytes(c: dict, rows: int, walk_len: int) -> int:
@@ -297,6 +303,13 @@ def run_ours(args, dist):
     want_cpu = (not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1)
     want_batched = (not args.no_batched and dist.rank == 0 and args.workload == "rmat20w")
     csr_host = csr.numpy() if want_cpu else None
+    ef_stores = {}
+    if args.ef_quanta and dist.world == 1:
+        from paper_2110_06196_gb300 import EFGraph
+        for qs in args.ef_quanta.split(","):
+            t0 = time.perf_counter()
+            ef_stores[int(qs)] = (EFGraph.from_csr(csr, quantum=int(qs), device=dev),
+                                  time.perf_counter() - t0)
     if not want_batched:
         del csr
         csr = None
@@ -349,6 +362,10 @@ def run_ours(args, dist):
     value = steps_per_launch * args.steps * dist.world / elapsed_max
     launch_ms = sum(ms) / len(ms)
 
+    ef_res = [bench_ef(st, build_s, job, n, dev, out, g.info()["device_bytes"])
+              for st, build_s in ef_stores.values()]
+    for st, _ in ef_stores.values():
+        st.close()
     approx = None
     if args.suss_k > 0 and dist.world == 1:
         from paper_2110_06196_gb300 import walks_approx
@@ -425,6 +442,10 @@ def run_ours(args, dist):
                      "fallbacks": cnt["fallbacks"]},
         "clocks": clk,
     }
+    if ef_res:
+        for r in ef_res:
+            r["frac_of_random_sector_peak"] = r["achieved_gbs"] / rs_peak
+        res["elias_fano"] = ef_res
     if want_batched:
         res["batched"] = bench_batched(g, csr, dev)
     if approx is not None:
@@ -437,6 +458,57 @@ def run_ours(args, dist):
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": sample}
     return res
+
+
+def bench_ef(store, build_s, job, n, dev, ref, csr_bytes, reps=3):
+    """The same job walked over the Elias-Fano store (grape_ef_walks): launch
+    time, steps/s, the store's size against the CSR engine's graph, sectors
+    read per step (counting launch) and the rows checked equal to the CSR
+    engine's rows of the timed run (`ref`)."""
+    from paper_2110_06196_gb300 import ef_walks
+    info = store.info()
+    out = torch.empty_like(ref)
+    stream = torch.cuda.current_stream(dev)
+
+    def launch():
+        ef_walks(store, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed, out=out)
+
+    launch()
+    torch.cuda.synchronize(dev)
+    store.stream_status()
+    step = max(1, (1 << 28) // max(1, out.shape[1]))
+    same = all(bool(torch.equal(out[b:b + step], ref[b:b + step]))
+               for b in range(0, out.shape[0], step))
+    steps = count_steps(out)
+    store.counters(True)
+    launch()
+    c = store.counters()
+    store.counters(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        launch()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    m, u = info["num_entries"], info["universe"]
+    ceil_log = 0
+    while m and (m << ceil_log) < u:
+        ceil_log += 1
+    alg = 32 * c["sectors"] + 4 * out.numel()
+    del out
+    torch.cuda.empty_cache()
+    return {"quantum": info["quantum"], "ms_per_launch": ms, "steps_per_s": steps / ms * 1e3,
+            "rows_equal_csr_engine": same, "build_s": build_s,
+            "low_bits": info["low_bits"], "code_bits": info["code_bits"],
+            "structure_bytes": info["structure_bytes"], "device_bytes": info["device_bytes"],
+            "csr_engine_graph_bytes": csr_bytes,
+            "bits_per_entry": 8 * info["structure_bytes"] / max(1, m),
+            "paper_bound_bits_per_entry": 2 + ceil_log,
+            "sectors_per_step": c["sectors"] / max(1, c["steps"]),
+            "membership_tests_per_step": c["membership_tests"] / max(1, c["steps"]),
+            "trials_per_step": c["trials"] / max(1, c["steps"]),
+            "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / ms / 1e6}
 
 
 def bench_contexts(g, job, n, dev, peak, window=5, chunk=1 << 22):
