@@ -448,8 +448,8 @@ void grape_walk_server_destroy(grape_server_t* server);
  * A graph held as the Elias-Fano representation of its edge codes (GRAPE,
  * Methods, "Succinct data structures for adjacency matrices"), for graphs whose
  * CSR and proposal entries would not fit the device: about
- * 2 + floor(log2(u / m)) bits per CSR entry plus the indexes, against 36 bytes
- * per entry for grape_graph_t.
+ * 2 + floor(log2(u / m)) bits per CSR entry plus the indexes and 8 bytes per
+ * node of row pointers, against 36 bytes per entry for grape_graph_t.
  *   - Edge Encoding: k = ceil(log2 num_nodes); the entry (a, b) is the code
  *     phi_k(a, b) = a * 2^k + b; u = num_nodes * 2^k.
  *   - Elias-Fano of the m sorted codes: l = floor(log2(u / m)) low bits per
@@ -465,6 +465,9 @@ void grape_walk_server_destroy(grape_server_t* server);
  *   - rank(c) = number of codes below c; select(i) = the i-th smallest code
  *     (0-based); deg(a) = rank(phi(a + 1, 0)) - rank(phi(a, 0)) ("Operations on
  *     Elias-Fano").
+ *   - Row pointers: rank(phi(a, 0)) for every node (the CSR offsets), so a walk
+ *     learns a degree from one read instead of two ranks, which scan the dense
+ *     high bits of hub rows.
  */
 typedef struct grape_ef_graph grape_ef_graph_t;
 
@@ -477,7 +480,9 @@ typedef struct grape_ef_graph grape_ef_graph_t;
  * GRAPE_ERR_INVALID_GRAPH for bad offsets, ids out of range, rows not strictly
  * increasing, or weights not finite or <= 0.  The caller keeps its buffers.
  *   quantum: a power of two in [1, 65536].  num_entries <= 2^40.
- *   flags: GRAPE_UNDIRECTED and GRAPE_VALIDATE are accepted and change nothing.
+ *   flags: GRAPE_UNDIRECTED (the caller asserts every entry has its reverse with
+ *       the same weight; a membership test may then search the shorter row),
+ *       GRAPE_VALIDATE (with GRAPE_UNDIRECTED: check that assertion too).
  *   Weighted graphs also hold the weights (fp32 per entry) and each row's
  *   largest weight (fp32 per node) uncompressed.
  *   *out receives the store on GRAPE_OK, and NULL otherwise.
@@ -500,7 +505,7 @@ typedef struct grape_ef_info {
     int64_t high_words;        /* ceil((m + Z) / 64) 64-bit words */
     int64_t ones_index_len;    /* ceil(m / quantum) */
     int64_t zeros_index_len;   /* ceil(Z / quantum) */
-    int64_t structure_bytes;   /* device bytes of the bit arrays (padding included) and indexes */
+    int64_t structure_bytes;   /* device bytes of the bit arrays (padding included), indexes and row pointers */
     int64_t device_bytes;      /* structure_bytes plus the weights and row maxima */
     int32_t code_bits;         /* k */
     int32_t low_bits;          /* l */

@@ -49,6 +49,8 @@ struct grape_ef_graph {
     long long* zeros_idx = nullptr;
     float* weights = nullptr;
     float* wmax = nullptr;
+    long long* rowptr = nullptr;              // [n + 1] first code of every row (CSR offsets)
+    bool undirected = false;
     int* status = nullptr;                    // [0] device status word, [1] bad flags, [2] max degree
     unsigned long long* counters = nullptr;   // [C_COUNT]
     bool counting = false;
@@ -67,9 +69,11 @@ struct EFDev {
     const long long* zeros_idx;
     const float* weights;
     const float* wmax;
+    const long long* rowptr;
     long long m, n, u;
     long long hwords;           // high-bit words, padding included
     int k, l, qlog;
+    int undirected;
     int* status;                // bit 0: a start id out of range; bit 1: an inconsistent store
     unsigned long long* counters;
 };
@@ -82,6 +86,8 @@ EFDev dev_view(const grape_ef_graph* g) {
     d.zeros_idx = g->zeros_idx;
     d.weights = g->weights;
     d.wmax = g->wmax;
+    d.rowptr = g->rowptr;
+    d.undirected = g->undirected ? 1 : 0;
     d.m = g->m;
     d.n = g->n;
     d.u = g->u;
@@ -147,6 +153,32 @@ __global__ void ef_check_rows_kernel(const int64_t* __restrict__ offsets,
             const long long d = hi - lo;
             atomicMax(max_deg, (int)(d < INT32_MAX ? d : INT32_MAX));
         }
+    }
+}
+
+// GRAPE_UNDIRECTED with GRAPE_VALIDATE: every entry (a, b) has its reverse
+// entry (b, a), with the same weight.  One warp per row, one binary search per
+// entry (ids are known in range and rows sorted by now).
+__global__ void ef_check_symmetry_kernel(const int64_t* __restrict__ offsets,
+                                         const int32_t* __restrict__ dsts,
+                                         const float* __restrict__ weights, long long n,
+                                         int* bad) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long a = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+        bool ok = true;
+        for (long long e = offsets[a] + lane; e < offsets[a + 1]; e += 32) {
+            const int b = dsts[e];
+            long long lo = offsets[b], hi = offsets[b + 1];
+            while (lo < hi) {
+                const long long mid = lo + ((hi - lo) >> 1);
+                if (dsts[mid] < a) lo = mid + 1;
+                else hi = mid;
+            }
+            const bool has = lo < offsets[b + 1] && dsts[lo] == a;
+            ok = ok && has && (!weights || weights[lo] == weights[e]);
+        }
+        if (!__all_sync(FULL, ok) && lane == 0) atomicOr(bad, 1);
     }
 }
 
@@ -343,14 +375,12 @@ __device__ __forceinline__ long long bucket_begin(const EFDev& g, long long h, T
     return h == 0 ? 0 : select0(g, h - 1, ty) + 1;
 }
 
-// Codes below c (0 <= c), and whether c itself is stored.
+// Search bucket h, whose ones begin at bit p, for the low part lo: the index
+// of its first code whose low part is >= lo, and whether one equals lo.
 template <bool C>
-__device__ long long rank_code(const EFDev& g, unsigned long long c, bool& found, Tally<C>& ty) {
+__device__ long long bucket_search(const EFDev& g, long long p, long long h, unsigned long long lo,
+                                   bool& found, Tally<C>& ty) {
     found = false;
-    if ((long long)c >= g.u) return g.m;
-    const long long h = (long long)(c >> g.l);
-    const unsigned long long lo = g.l ? (c & ((1ull << g.l) - 1)) : 0ull;
-    const long long p = bucket_begin(g, h, ty);
     const long long i0 = p - h;
     // length of bucket h: the run of ones from p (the word at p, then the
     // zeros index when the run reaches the end of that word)
@@ -384,6 +414,16 @@ __device__ long long rank_code(const EFDev& g, unsigned long long c, bool& found
     }
     found = (a < i0 + len) && low_of(g, a, ty) == lo;
     return a;
+}
+
+// Codes below c (0 <= c), and whether c itself is stored.
+template <bool C>
+__device__ long long rank_code(const EFDev& g, unsigned long long c, bool& found, Tally<C>& ty) {
+    found = false;
+    if ((long long)c >= g.u) return g.m;
+    const long long h = (long long)(c >> g.l);
+    const unsigned long long lo = g.l ? (c & ((1ull << g.l) - 1)) : 0ull;
+    return bucket_search(g, bucket_begin(g, h, ty), h, lo, found, ty);
 }
 
 // First code of row a and its degree (a row that does not fit inside the
@@ -444,6 +484,81 @@ __device__ __forceinline__ int ef_target(const EFDev& g, unsigned long long code
     return (int)(code & ((1ull << g.k) - 1));
 }
 
+// Words a scan near a known position looks at before it turns to an index.
+constexpr int kNearWords = 8;
+
+// The r-th (0-based) one (ONES) or zero at or after bit p, when it lies in the
+// kNearWords words from p's word; -1 otherwise.
+template <bool ONES, bool C>
+__device__ __forceinline__ long long scan_near(const EFDev& g, long long p, long long r,
+                                               Tally<C>& ty) {
+    long long w = p >> 6;
+    const long long wend = w + kNearWords < g.hwords ? w + kNearWords : g.hwords;
+    if (p < 0 || w >= wend) return -1;
+    ty.touch(g.high + w);
+    unsigned long long x = __ldg(g.high + w);
+    if (!ONES) x = ~x;
+    x &= ~0ull << (p & 63);
+    while (true) {
+        const int c = __popcll(x);
+        if (r < c) return (w << 6) + nth_set_bit(x, (int)r);
+        r -= c;
+        if (++w >= wend) return -1;
+        ty.touch(g.high + w);
+        x = __ldg(g.high + w);
+        if (!ONES) x = ~x;
+    }
+}
+
+// Row a's first code off and degree, from the row pointers (one 16-byte read),
+// and its region of the high bits: with l <= k every row starts a bucket,
+// h0 = a 2^(k-l), so the region begins at P = off + h0 (off ones and h0
+// zeros before it) and spans deg ones and nb = 2^(k-l) zeros.  P = -1 when
+// l > k.
+template <bool C>
+__device__ __forceinline__ void region_of(const EFDev& g, long long a, long long& P,
+                                          long long& off, int& deg, Tally<C>& ty) {
+    ty.touch(g.rowptr + a);
+    off = __ldg(g.rowptr + a);
+    ty.touch(g.rowptr + a + 1);
+    const long long end = __ldg(g.rowptr + a + 1);
+    deg = (int)(end - off);
+    P = g.l <= g.k ? off + (a << (g.k - g.l)) : -1;
+}
+
+// Is the region of row a (from region_of; P, deg) short enough for scans near
+// its start to find every position in it?
+__device__ __forceinline__ bool region_near(const EFDev& g, long long P, int deg) {
+    return P >= 0 && (P & 63) + (long long)deg + (1LL << (g.k - g.l)) <= 64LL * kNearWords;
+}
+
+// Code number e, the idx-th code of row v (region start P, near: region_near).
+template <bool C>
+__device__ __forceinline__ unsigned long long row_code(const EFDev& g, long long P, bool near,
+                                                       long long e, long long idx, Tally<C>& ty) {
+    long long pos = near ? scan_near<true>(g, P, idx, ty) : -1;
+    if (pos < 0) pos = select1(g, e, ty);
+    return ((unsigned long long)(pos - e) << g.l) | low_of(g, e, ty);
+}
+
+// Index of the first code of row a at or above phi(a, b), and whether b is in
+// N(a); P and near describe row a's region (region_of, region_near).
+template <bool C>
+__device__ __forceinline__ long long find_in_row(const EFDev& g, long long P, bool near, long long a,
+                                                 int b, bool& found, Tally<C>& ty) {
+    if (P < 0) return rank_code(g, ((unsigned long long)a << g.k) | (unsigned)b, found, ty);
+    const long long j = (long long)((unsigned)b >> g.l);      // bucket within the row
+    const long long h = (a << (g.k - g.l)) + j;
+    const unsigned long long lo = g.l ? ((unsigned)b & ((1ull << g.l) - 1)) : 0ull;
+    long long B = P;
+    if (j > 0) {
+        long long z = near ? scan_near<false>(g, P, j - 1, ty) : -1;
+        if (z < 0) z = select0(g, h - 1, ty);
+        B = z + 1;
+    }
+    return bucket_search(g, B, h, lo, found, ty);
+}
+
 // The exact fallback after trial_cap rejections: inverse transform over the
 // cumulative sum of pi in row order (GRAPE, "Efficient sampling for Node2Vec
 // RWs"), every fp64 product and sum rounded separately; the uniform comes from
@@ -478,12 +593,25 @@ __device__ int ef_fallback(const EFDev& g, long long w, int s, unsigned long lon
 // One thread per walk (grid-stride over the launch's rows).  Rows are staged
 // per thread in a 32-byte slot of shared memory and leave as whole sectors
 // (put / fill_dead of the CSR engine).
+//
+// A lane keeps the region (region_of) of its current node v and of the
+// previous node t, so proposals and membership tests in a short row scan the
+// high bits near a known position instead of going through an index.  On
+// undirected graphs a test against a long N(t) searches N(x) for t when that
+// row is shorter.  With know_ret set (the in and out thresholds are both below
+// 2^32: the return class has the largest bias), a lane whose current row is
+// short also finds rt, the position of t in N(v), once per step: a proposal
+// idx == rt is then the return and is decided without reading the store, and
+// any other proposal whose r2 exceeds both the in and out thresholds is
+// rejected without a read (w <= wmax_v).  Every decision is the same function
+// of (r2, class, weight) as the oracle's, so the rows do not change.
 template <bool WEIGHTED, bool COUNT>
 __global__ void __launch_bounds__(kEFThreads)
-ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap) {
+ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
     Counts<COUNT> cnt;
     cnt.clear();
     Tally<COUNT> ty;
+    const unsigned tm1_io = wc.tm1_in > wc.tm1_out ? wc.tm1_in : wc.tm1_out;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < wc.num_walks;
          row += stride) {
@@ -503,26 +631,40 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap) {
         cnt.add(C_WALKS);
         put(L, rowp, 0, (int)v0, len);
         int v = (int)v0, t = -1;
-        long long off_v;
-        int deg_v;
+        long long P_v, off_v, P_t = -1;
+        int deg_v, deg_t = 0;
         ty.begin();
-        row_of(g, v, off_v, deg_v, ty);
+        region_of(g, v, P_v, off_v, deg_v, ty);
         float wmax_v = 0.0f;
         if (WEIGHTED) {
             ty.touch(g.wmax + v);
             wmax_v = __ldg(g.wmax + v);
         }
+        int rt = -1;               // position of t in N(v) when ret_known, -1 when absent
+        float w_rt = 0.0f;         // weighted: the weight there
+        bool ret_known = false;
         int s = 1;
         for (; s < len && deg_v > 0; ++s) {
+            const bool near_v = region_near(g, P_v, deg_v);
+            const bool near_t = region_near(g, P_t, deg_t);
             int x = -1;
-            long long e = -1;
-            unsigned k = 0;
-            for (; k < trial_cap; ++k) {
+            for (unsigned k = 0; k < trial_cap; ++k) {
                 const uint4 r = trial_block(wc.seed, w, s, k);
                 cnt.add(C_TRIALS);
-                e = off_v + scale_index(r.x, r.y, deg_v);
+                const int idx = scale_index(r.x, r.y, deg_v);
+                if (t >= 0 && ret_known) {
+                    if (idx == rt) {                        // the return, decided in registers
+                        if (accept_test<WEIGHTED>(r.z, wmax_v, wc.tm1_ret, w_rt)) {
+                            x = t;
+                            break;
+                        }
+                        continue;
+                    }
+                    if (r.z > tm1_io) continue;             // rejected whatever its class
+                }
+                const long long e = off_v + idx;
                 ty.begin();
-                const int cand = ef_target(g, select_code(g, e, ty));
+                const int cand = ef_target(g, row_code(g, P_v, near_v, e, idx, ty));
                 cnt.add(C_GATHERS);
                 float wv = 1.0f;
                 if (WEIGHTED) {
@@ -546,7 +688,21 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap) {
                     if (acc_in != acc_out) {      // only then does the class decide
                         cnt.add(C_SEARCHES);
                         ty.begin();
-                        acc = ef_has_edge(g, t, cand, ty) ? acc_in : acc_out;
+                        bool in_t;
+                        if (near_t || !g.undirected) {
+                            find_in_row(g, P_t, near_t, t, cand, in_t, ty);
+                        } else {
+                            // a long N(t) on an undirected graph: search the
+                            // shorter of N(t) and N(x) (t in N(x) <=> x in N(t))
+                            long long P_x, off_x;
+                            int deg_x;
+                            region_of(g, cand, P_x, off_x, deg_x, ty);
+                            if (deg_x < deg_t)
+                                find_in_row(g, P_x, region_near(g, P_x, deg_x), cand, t, in_t, ty);
+                            else
+                                find_in_row(g, P_t, near_t, t, cand, in_t, ty);
+                        }
+                        acc = in_t ? acc_in : acc_out;
                     }
                 }
                 if (acc) {
@@ -559,17 +715,31 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap) {
                 const int j = ef_fallback<WEIGHTED>(g, w, s, wc.seed, t, off_v, deg_v, wc.a_ret,
                                                     wc.a_out, trial_cap, ty);
                 ty.begin();
-                x = ef_target(g, select_code(g, off_v + j, ty));
+                x = ef_target(g, row_code(g, P_v, near_v, off_v + j, j, ty));
             }
             put(L, rowp, s, x, len);
             cnt.add(C_STEPS);
             t = v;
+            P_t = P_v;
+            deg_t = deg_v;
             v = x;
             ty.begin();
-            row_of(g, v, off_v, deg_v, ty);
+            region_of(g, v, P_v, off_v, deg_v, ty);
             if (WEIGHTED) {
                 ty.touch(g.wmax + v);
                 wmax_v = __ldg(g.wmax + v);
+            }
+            // locate the return in a short row only (a long one costs more to
+            // search than the reads it would save)
+            ret_known = know_ret && deg_v > 0 && region_near(g, P_v, deg_v);
+            if (ret_known) {
+                bool found;
+                const long long at = find_in_row(g, P_v, true, v, t, found, ty);
+                rt = found ? (int)(at - off_v) : -1;
+                if (WEIGHTED && found) {
+                    ty.touch(g.weights + at);
+                    w_rt = __ldg(g.weights + at);
+                }
             }
         }
         if (s < len) fill_dead(L, rowp, s, len);
@@ -598,8 +768,11 @@ cudaError_t launch_walks(const grape_ef_graph* g, const WalkConst& wc, unsigned 
     per_sm = std::max(per_sm, 1);
     const long long need = (wc.num_walks + kEFThreads - 1) / kEFThreads;
     const int blocks = (int)std::max(1LL, std::min(need, (long long)g->num_sms * per_sm));
+    // the return is worth locating when it has the largest bias (both other
+    // thresholds below 2^32): other proposals can then be rejected unread
+    const int know_ret = (wc.tm1_in < 0xffffffffu && wc.tm1_out < 0xffffffffu) ? 1 : 0;
     ef_walk_kernel<W, C><<<blocks, kEFThreads, 32 * kEFThreads, stream>>>(dev_view(g), wc,
-                                                                           trial_cap);
+                                                                           trial_cap, know_ret);
     return cudaGetLastError();
 }
 
@@ -611,6 +784,7 @@ void free_ef(grape_ef_graph* g) {
     cudaFree(g->zeros_idx);
     cudaFree(g->weights);
     cudaFree(g->wmax);
+    cudaFree(g->rowptr);
     cudaFree(g->status);
     cudaFree(g->counters);
     delete g;
@@ -637,6 +811,7 @@ grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts
     g->n = num_nodes;
     g->m = num_entries;
     g->weighted = weights != nullptr;
+    g->undirected = (flags & GRAPE_UNDIRECTED) != 0;
     g->quantum = quantum;
     while ((1 << g->qlog) < quantum) ++g->qlog;
     // k = ceil(log2 |V|); u = |V| 2^k; l = floor(log2(u / m)) (0 when u <= m)
@@ -666,13 +841,15 @@ grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts
         e = cudaMalloc(&g->weights, sizeof(float) * (size_t)std::max<int64_t>(num_entries, 1));
         if (e == cudaSuccess) e = cudaMalloc(&g->wmax, sizeof(float) * (size_t)num_nodes);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&g->rowptr, sizeof(long long) * (size_t)(num_nodes + 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * C_COUNT);
     if (e != cudaSuccess) {
         free_ef(g);
         return cuda_status(e);
     }
-    g->structure_bytes = (int64_t)(low_bytes + high_bytes + 8 * (g->ones_len + g->zeros_len));
+    g->structure_bytes = (int64_t)(low_bytes + high_bytes + 8 * (g->ones_len + g->zeros_len) +
+                                   8 * (num_nodes + 1));
     g->device_bytes = g->structure_bytes +
                       (weights ? (int64_t)(4 * num_entries + 4 * num_nodes) : 0);
     int host[4] = {0, 0, 0, 0};
@@ -704,11 +881,26 @@ grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts
         return e != cudaSuccess ? cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
     }
     g->max_degree = host[2];
+    if (g->undirected && (flags & GRAPE_VALIDATE)) {
+        ef_check_symmetry_kernel<<<ef_grid(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+            offsets, dsts, weights, num_nodes, g->status + 1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host, g->status, sizeof(int) * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess || host[1] != 0) {
+            free_ef(g);
+            return e != cudaSuccess ? cuda_status(e) : GRAPE_ERR_INVALID_GRAPH;
+        }
+    }
     // 2. the bit arrays and their indexes
     if (e == cudaSuccess) e = cudaMemsetAsync(g->low, 0, low_bytes, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->high, 0, high_bytes, stream);
     if (e == cudaSuccess && weights && num_entries > 0)
         e = cudaMemcpyAsync(g->weights, weights, sizeof(float) * (size_t)num_entries,
+                            cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->rowptr, offsets, sizeof(long long) * (size_t)(num_nodes + 1),
                             cudaMemcpyDeviceToDevice, stream);
     if (e == cudaSuccess) {
         ef_fill_kernel<<<ef_grid(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(

@@ -20,8 +20,8 @@ class EFGraph:
     """A graph held as the Elias-Fano representation of its edge codes
     (grape_ef_graph_create)."""
 
-    def __init__(self, offsets, dsts, weights=None, quantum=PAPER_QUANTUM, device="cuda",
-                 stream=None):
+    def __init__(self, offsets, dsts, weights=None, quantum=PAPER_QUANTUM, undirected=True,
+                 validate=True, device="cuda", stream=None):
         lib = _lib.load()
         offsets = _dev_tensor(offsets, torch.int64, device)
         dsts = _dev_tensor(dsts, torch.int32, device)
@@ -30,7 +30,10 @@ class EFGraph:
         h = ctypes.c_void_p()
         with torch.cuda.device(offsets.device):
             code = lib.grape_ef_graph_create(_ptr(offsets), _ptr(dsts), _ptr(weights), n,
-                                             dsts.numel(), int(quantum), 0, _stream_ptr(stream),
+                                             dsts.numel(), int(quantum),
+                                             (_lib.GRAPE_UNDIRECTED if undirected else 0) |
+                                             (_lib.GRAPE_VALIDATE if validate else 0),
+                                             _stream_ptr(stream),
                                              ctypes.byref(h))
         check(code, "grape_ef_graph_create")
         self._h = h
@@ -41,8 +44,8 @@ class EFGraph:
         self.weighted = weights is not None
 
     @classmethod
-    def from_csr(cls, csr, quantum=PAPER_QUANTUM, device="cuda"):
-        return cls(csr.offsets, csr.dsts, csr.weights, quantum, device)
+    def from_csr(cls, csr, quantum=PAPER_QUANTUM, undirected=True, validate=True, device="cuda"):
+        return cls(csr.offsets, csr.dsts, csr.weights, quantum, undirected, validate, device)
 
     @property
     def handle(self):

@@ -12,7 +12,8 @@ against the CPU oracles, bit for bit:
   0 and 2, ragged lengths, explicit and out-of-range starts; and equal the CSR
   engine's rows (itself oracle-checked) on the whole R-MAT scale-20 weighted job,
   with sampled rows checked against the oracle;
-* work counters: steps, proposals and fallbacks equal the oracle's counts;
+* work counters: steps, proposals and fallbacks equal the oracle's counts, and
+  codes are read for every proposal except those decided without a read;
 * invalid CSRs are rejected.
 """
 import numpy as np
@@ -52,6 +53,9 @@ def store_graphs():
     return g
 
 
+DIRECTED = {"directed", "directed_w"}
+
+
 def _u64(t):
     return t.cpu().numpy().view(np.uint64)
 
@@ -62,7 +66,7 @@ def test_store_words_equal_oracle(name, quantum):
     csr = store_graphs()[name]
     off, dst, _ = csr.numpy()
     want = OEF.EFGraph(off, dst, csr.num_nodes, quantum=quantum)
-    g = EFGraph.from_csr(csr, quantum=quantum)
+    g = EFGraph.from_csr(csr, quantum=quantum, undirected=name not in DIRECTED)
     info = g.info()
     assert info["code_bits"] == want.k and info["low_bits"] == want.ef.l
     assert info["universe"] == want.ef.u and info["num_zeros"] == want.ef.num_zeros
@@ -83,7 +87,7 @@ def test_select_rank_equal_oracle(name, quantum):
     csr = store_graphs()[name]
     off, dst, _ = csr.numpy()
     want = OEF.EFGraph(off, dst, csr.num_nodes, quantum=quantum).ef
-    g = EFGraph.from_csr(csr, quantum=quantum)
+    g = EFGraph.from_csr(csr, quantum=quantum, undirected=name not in DIRECTED)
     rng = np.random.default_rng(quantum)
     m, u, l = want.n, want.u, want.l
     idx = np.arange(m) if m <= 3000 else rng.integers(0, m, 3000)
@@ -115,8 +119,9 @@ def test_select_out_of_range_sets_status():
     g.stream_status()          # cleared
 
 
-def check_walks(csr, starts, walk_len, wpn, p, q, seed, trial_cap=4096, quantum=64, g=None):
-    g = g or EFGraph.from_csr(csr, quantum=quantum)
+def check_walks(csr, starts, walk_len, wpn, p, q, seed, trial_cap=4096, quantum=64, g=None,
+                undirected=True):
+    g = g or EFGraph.from_csr(csr, quantum=quantum, undirected=undirected)
     st = None if starts is None else torch.as_tensor(np.asarray(starts, np.int32))
     got = ef_walks(g, st, walk_len, wpn, p, q, seed, trial_cap=trial_cap)
     torch.cuda.synchronize()
@@ -151,7 +156,7 @@ def tiny_graphs():
 @pytest.mark.parametrize("name", sorted(tiny_graphs()))
 def test_walks_tiny_graphs_all_pq(name):
     csr = tiny_graphs()[name]
-    g = EFGraph.from_csr(csr, quantum=2)
+    g = EFGraph.from_csr(csr, quantum=2, undirected=name not in DIRECTED)
     for p in PQ5:
         for q in PQ5:
             check_walks(csr, None, 17, 9, p, q, seed=int(p * 100 + q * 10), g=g)
@@ -194,7 +199,7 @@ def test_walks_ragged_lengths_starts_and_dead_ends():
             check_walks(csr, starts, L, wpn, 0.5, 2.0, seed=L * 7 + wpn, g=g)
     n, e = _law.graph_directed()
     d = csr_np(*_law.csr_from_edges(n, e, None, False))
-    check_walks(d, None, 40, 5, 1.0, 0.5, seed=3, quantum=1)
+    check_walks(d, None, 40, 5, 1.0, 0.5, seed=3, quantum=1, undirected=False)
 
 
 def test_walks_out_of_range_starts():
@@ -226,7 +231,14 @@ def test_counters_equal_oracle_counts():
             assert c["steps"] == st.steps
             assert c["trials"] == st.trials
             assert c["fallbacks"] == st.fallbacks
-            assert c["codes_read"] == st.trials
+            # returns and certain rejections are decided without reading a code when
+            # the return has the largest bias (p < 1 and p < q here); else every
+            # proposal reads its code
+            ret_largest = (1.0 / p) > max(1.0, 1.0 / q)
+            if ret_largest:
+                assert 0 < c["codes_read"] < st.trials
+            else:
+                assert c["codes_read"] == st.trials
             assert c["sectors"] > 0
 
 
@@ -255,6 +267,27 @@ def test_rmat20w_full_job_equals_csr_engine_and_sampled_oracle_rows():
     assert np.array_equal(got[torch.from_numpy(ids).cuda()].cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("quantum", [64, 1024])
+def test_walks_shorter_row_search_equals_directed_search(quantum):
+    # an undirected graph walked with membership tests in N(t) only (directed
+    # reading) and with the shorter of N(t), N(x): the same rows, both the oracle's
+    csr = synth.rmat(13, 120000, seed=23)
+    for und in (False, True):
+        g = EFGraph.from_csr(csr, quantum=quantum, undirected=und)
+        for (p, q) in [(1.0, 0.25), (0.5, 2.0)]:
+            check_walks(csr, None, 30, 1, p, q, seed=13, g=g)
+
+
+def test_undirected_store_rejects_asymmetric_csr():
+    off, dst = [0, 2, 3, 5], [1, 2, 0, 0, 1]          # 2 -> 1 without 1 -> 2
+    EFGraph.from_csr(csr_np(off, dst), quantum=4, undirected=False)
+    with pytest.raises(GrapeError, match="INVALID_GRAPH"):
+        EFGraph.from_csr(csr_np(off, dst), quantum=4, undirected=True)
+    # symmetric rows, unequal weights
+    with pytest.raises(GrapeError, match="INVALID_GRAPH"):
+        EFGraph.from_csr(csr_np([0, 1, 2], [1, 0], [1.0, 0.5]), quantum=4, undirected=True)
+
+
 @pytest.mark.parametrize("bad", ["unsorted_row", "id_out_of_range", "multi_edge", "bad_offsets",
                                  "negative_weight"])
 def test_invalid_csr_rejected(bad):
@@ -272,4 +305,4 @@ def test_invalid_csr_rejected(bad):
     elif bad == "negative_weight":
         w = [1.0, 0.5, -1.0, 0.3, 0.2]
     with pytest.raises(GrapeError, match="INVALID_GRAPH"):
-        EFGraph.from_csr(csr_np(off, dst, w), quantum=4)
+        EFGraph.from_csr(csr_np(off, dst, w), quantum=4, undirected=False)
