@@ -467,7 +467,10 @@ void grape_walk_server_destroy(grape_server_t* server);
  *     Elias-Fano").
  *   - Row pointers: rank(phi(a, 0)) for every node (the CSR offsets), so a walk
  *     learns a degree from one read instead of two ranks, which scan the dense
- *     high bits of hub rows.
+ *     high bits of hub rows.  Rows much longer than their 2^(k - l) buckets
+ *     (deg + 2^(k-l) > 448 and deg >= 8 * 2^(k-l)) also get a bucket directory:
+ *     the bit offset of each bucket's start, so a membership test in a hub row
+ *     reads two offsets instead of scanning.
  */
 typedef struct grape_ef_graph grape_ef_graph_t;
 
@@ -479,7 +482,7 @@ typedef struct grape_ef_graph grape_ef_graph_t;
  * always checked first (the store's layout is computed from the ids):
  * GRAPE_ERR_INVALID_GRAPH for bad offsets, ids out of range, rows not strictly
  * increasing, or weights not finite or <= 0.  The caller keeps its buffers.
- *   quantum: a power of two in [1, 65536].  num_entries <= 2^40.
+ *   quantum: a power of two in [1, 65536].  num_entries < 2^40.
  *   flags: GRAPE_UNDIRECTED (the caller asserts every entry has its reverse with
  *       the same weight; a membership test may then search the shorter row),
  *       GRAPE_VALIDATE (with GRAPE_UNDIRECTED: check that assertion too).
@@ -505,14 +508,15 @@ typedef struct grape_ef_info {
     int64_t high_words;        /* ceil((m + Z) / 64) 64-bit words */
     int64_t ones_index_len;    /* ceil(m / quantum) */
     int64_t zeros_index_len;   /* ceil(Z / quantum) */
-    int64_t structure_bytes;   /* device bytes of the bit arrays (padding included), indexes and row pointers */
+    int64_t structure_bytes;   /* device bytes of the bit arrays (padding included), indexes, row
+                                  pointers and bucket directories */
     int64_t device_bytes;      /* structure_bytes plus the weights and row maxima */
     int32_t code_bits;         /* k */
     int32_t low_bits;          /* l */
     int32_t quantum;
     int32_t weighted;
     int32_t max_degree;
-    int32_t pad;
+    int32_t directory_rows;    /* rows with a bucket directory */
 } grape_ef_info_t;
 
 grape_status_t grape_ef_graph_info(const grape_ef_graph_t* graph, grape_ef_info_t* info);

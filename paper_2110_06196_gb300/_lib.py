@@ -81,10 +81,10 @@ class EFInfo(ctypes.Structure):
                 ("high_words", c_i64), ("ones_index_len", c_i64), ("zeros_index_len", c_i64),
                 ("structure_bytes", c_i64), ("device_bytes", c_i64), ("code_bits", c_i32),
                 ("low_bits", c_i32), ("quantum", c_i32), ("weighted", c_i32),
-                ("max_degree", c_i32), ("pad", c_i32)]
+                ("max_degree", c_i32), ("directory_rows", c_i32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class EFCounters(ctypes.Structure):

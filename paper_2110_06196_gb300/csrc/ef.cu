@@ -49,7 +49,10 @@ struct grape_ef_graph {
     long long* zeros_idx = nullptr;
     float* weights = nullptr;
     float* wmax = nullptr;
-    long long* rowptr = nullptr;              // [n + 1] first code of every row (CSR offsets)
+    long long* rowptr = nullptr;              // [n + 1] first code of every row (CSR offsets),
+                                              // a bucket directory slot in bits 40-62
+    unsigned* dir = nullptr;                  // bucket directories of long rows
+    int32_t dir_rows = 0;
     bool undirected = false;
     int* status = nullptr;                    // [0] device status word, [1] bad flags, [2] max degree
     unsigned long long* counters = nullptr;   // [C_COUNT]
@@ -61,6 +64,11 @@ namespace {
 
 constexpr int kEFThreads = 256;
 constexpr int kPadWords = 4;
+// Row pointers hold the row's first code index in bits 0-39 and, for a row with
+// a bucket directory, 1 + the directory's index in bits 40-62.
+constexpr int kRowPtrBits = 40;
+constexpr long long kRowPtrMask = (1LL << kRowPtrBits) - 1;
+constexpr int kMaxDirRows = (1 << 23) - 1;
 
 struct EFDev {
     const unsigned long long* low;
@@ -70,6 +78,7 @@ struct EFDev {
     const float* weights;
     const float* wmax;
     const long long* rowptr;
+    const unsigned* dir;
     long long m, n, u;
     long long hwords;           // high-bit words, padding included
     int k, l, qlog;
@@ -87,6 +96,7 @@ EFDev dev_view(const grape_ef_graph* g) {
     d.weights = g->weights;
     d.wmax = g->wmax;
     d.rowptr = g->rowptr;
+    d.dir = g->dir;
     d.undirected = g->undirected ? 1 : 0;
     d.m = g->m;
     d.n = g->n;
@@ -207,6 +217,55 @@ __global__ void ef_fill_kernel(const int64_t* __restrict__ offsets,
                     if (s + l > 64) atomicOr(low + (b >> 6) + 1, bits >> (64 - s));
                 }
             }
+        }
+    }
+}
+
+// Bucket directories.  A long row (deg + nb > 448 and deg >= 8 nb, nb = 2^(k-l)
+// buckets per row) gets nb + 1 entries: entry j is the bit offset, from the
+// row's region start, where bucket j's ones begin (j + the row's codes in
+// buckets below j), entry nb the region's end (deg + nb).  A membership test in
+// such a row then reads two entries instead of scanning the dense high bits.
+__device__ __forceinline__ bool long_row(long long deg, long long nb) {
+    return deg + nb > 448 && deg >= 8 * nb;
+}
+
+__global__ void ef_count_long_rows_kernel(const int64_t* __restrict__ offsets, long long n,
+                                          long long nb, unsigned long long* count) {
+    unsigned long long c = 0;
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x)
+        c += long_row(offsets[a + 1] - offsets[a], nb) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// One warp per long row: take a slot (their order is arbitrary and changes no
+// result), mark it in the row pointer and fill the directory from the CSR.
+__global__ void ef_fill_dirs_kernel(const int64_t* __restrict__ offsets,
+                                    const int32_t* __restrict__ dsts, long long n, long long nb,
+                                    int l, long long* __restrict__ rowptr,
+                                    unsigned* __restrict__ dir, unsigned long long* next) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long a = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; a < n; a += warps) {
+        const long long lo = offsets[a], hi = offsets[a + 1];
+        if (!long_row(hi - lo, nb)) continue;
+        unsigned long long slot = 0;
+        if (lane == 0) slot = atomicAdd(next, 1ull);
+        slot = __shfl_sync(FULL, slot, 0);
+        if (lane == 0) rowptr[a] = lo | (long long)((slot + 1) << kRowPtrBits);
+        unsigned* d = dir + slot * (unsigned long long)(nb + 1);
+        for (long long j = lane; j <= nb; j += 32) {
+            const long long lim = j << l;          // codes of bucket < j: dsts below j 2^l
+            long long a0 = lo, a1 = hi;
+            while (a0 < a1) {
+                const long long mid = a0 + ((a1 - a0) >> 1);
+                if ((long long)dsts[mid] < lim) a0 = mid + 1;
+                else a1 = mid;
+            }
+            d[j] = (unsigned)(j + (a0 - lo));
         }
     }
 }
@@ -375,6 +434,28 @@ __device__ __forceinline__ long long bucket_begin(const EFDev& g, long long h, T
     return h == 0 ? 0 : select0(g, h - 1, ty) + 1;
 }
 
+// The first of the len codes from i0 (one bucket: their low parts increase)
+// whose low part is >= lo, and whether one equals lo.
+template <bool C>
+__device__ __forceinline__ long long lows_search(const EFDev& g, long long i0, long long len,
+                                                 unsigned long long lo, bool& found,
+                                                 Tally<C>& ty) {
+    found = false;
+    if (len <= 0) return i0;
+    if (lo == 0) {
+        found = (low_of(g, i0, ty) == 0);
+        return i0;
+    }
+    long long a = i0, b = i0 + len;
+    while (a < b) {
+        const long long mid = a + ((b - a) >> 1);
+        if (low_of(g, mid, ty) < lo) a = mid + 1;
+        else b = mid;
+    }
+    found = (a < i0 + len) && low_of(g, a, ty) == lo;
+    return a;
+}
+
 // Search bucket h, whose ones begin at bit p, for the low part lo: the index
 // of its first code whose low part is >= lo, and whether one equals lo.
 template <bool C>
@@ -400,20 +481,7 @@ __device__ long long bucket_search(const EFDev& g, long long p, long long h, uns
         atomicOr(g.status, 2);
         return g.m;
     }
-    if (len == 0) return i0;
-    if (lo == 0) {
-        found = (low_of(g, i0, ty) == 0);
-        return i0;
-    }
-    // first code of the bucket whose low part is >= lo (lows increase within a bucket)
-    long long a = i0, b = i0 + len;
-    while (a < b) {
-        const long long mid = a + ((b - a) >> 1);
-        if (low_of(g, mid, ty) < lo) a = mid + 1;
-        else b = mid;
-    }
-    found = (a < i0 + len) && low_of(g, a, ty) == lo;
-    return a;
+    return lows_search(g, i0, len, lo, found, ty);
 }
 
 // Codes below c (0 <= c), and whether c itself is stored.
@@ -510,49 +578,69 @@ __device__ __forceinline__ long long scan_near(const EFDev& g, long long p, long
     }
 }
 
-// Row a's first code off and degree, from the row pointers (one 16-byte read),
-// and its region of the high bits: with l <= k every row starts a bucket,
-// h0 = a 2^(k-l), so the region begins at P = off + h0 (off ones and h0
-// zeros before it) and spans deg ones and nb = 2^(k-l) zeros.  P = -1 when
-// l > k.
+// A row's place in the store: its first code, degree, the bit position P
+// where its region of the high bits begins (-1 when l > k) and its bucket
+// directory slot (0: none).
+struct Row {
+    long long P;
+    long long off;
+    int deg;
+    int slot;
+};
+
+// Row a from the row pointers (one 16-byte read).  With l <= k every row
+// starts a bucket, h0 = a 2^(k-l), so its region begins at P = off + h0 (off
+// ones and h0 zeros before it) and spans deg ones and nb = 2^(k-l) zeros.
 template <bool C>
-__device__ __forceinline__ void region_of(const EFDev& g, long long a, long long& P,
-                                          long long& off, int& deg, Tally<C>& ty) {
+__device__ __forceinline__ Row region_of(const EFDev& g, long long a, Tally<C>& ty) {
     ty.touch(g.rowptr + a);
-    off = __ldg(g.rowptr + a);
+    const long long w0 = __ldg(g.rowptr + a);
     ty.touch(g.rowptr + a + 1);
-    const long long end = __ldg(g.rowptr + a + 1);
-    deg = (int)(end - off);
-    P = g.l <= g.k ? off + (a << (g.k - g.l)) : -1;
+    const long long w1 = __ldg(g.rowptr + a + 1);
+    Row r;
+    r.off = w0 & kRowPtrMask;
+    r.deg = (int)((w1 & kRowPtrMask) - r.off);
+    r.slot = (int)(w0 >> kRowPtrBits);
+    r.P = g.l <= g.k ? r.off + (a << (g.k - g.l)) : -1;
+    return r;
 }
 
-// Is the region of row a (from region_of; P, deg) short enough for scans near
-// its start to find every position in it?
-__device__ __forceinline__ bool region_near(const EFDev& g, long long P, int deg) {
-    return P >= 0 && (P & 63) + (long long)deg + (1LL << (g.k - g.l)) <= 64LL * kNearWords;
+// Is row r short enough for scans near its start to find every position in it?
+__device__ __forceinline__ bool region_near(const EFDev& g, const Row& r) {
+    return r.P >= 0 && (r.P & 63) + (long long)r.deg + (1LL << (g.k - g.l)) <= 64LL * kNearWords;
 }
 
-// Code number e, the idx-th code of row v (region start P, near: region_near).
+// Code number e, the idx-th code of row r (near: region_near(r)).
 template <bool C>
-__device__ __forceinline__ unsigned long long row_code(const EFDev& g, long long P, bool near,
+__device__ __forceinline__ unsigned long long row_code(const EFDev& g, const Row& r, bool near,
                                                        long long e, long long idx, Tally<C>& ty) {
-    long long pos = near ? scan_near<true>(g, P, idx, ty) : -1;
+    long long pos = near ? scan_near<true>(g, r.P, idx, ty) : -1;
     if (pos < 0) pos = select1(g, e, ty);
     return ((unsigned long long)(pos - e) << g.l) | low_of(g, e, ty);
 }
 
-// Index of the first code of row a at or above phi(a, b), and whether b is in
-// N(a); P and near describe row a's region (region_of, region_near).
+// Index of the first code of row a (r) at or above phi(a, b), and whether b is
+// in N(a): the bucket of b from the row's directory, or a scan of the zeros
+// near the row's start, or the zeros index; then its low parts.
 template <bool C>
-__device__ __forceinline__ long long find_in_row(const EFDev& g, long long P, bool near, long long a,
-                                                 int b, bool& found, Tally<C>& ty) {
-    if (P < 0) return rank_code(g, ((unsigned long long)a << g.k) | (unsigned)b, found, ty);
+__device__ __forceinline__ long long find_in_row(const EFDev& g, const Row& r, bool near,
+                                                 long long a, int b, bool& found, Tally<C>& ty) {
+    if (r.P < 0) return rank_code(g, ((unsigned long long)a << g.k) | (unsigned)b, found, ty);
     const long long j = (long long)((unsigned)b >> g.l);      // bucket within the row
     const long long h = (a << (g.k - g.l)) + j;
     const unsigned long long lo = g.l ? ((unsigned)b & ((1ull << g.l) - 1)) : 0ull;
-    long long B = P;
+    if (r.slot > 0) {
+        const long long nb = 1LL << (g.k - g.l);
+        const unsigned* d = g.dir + (long long)(r.slot - 1) * (nb + 1) + j;
+        ty.touch(d);
+        const unsigned s0 = __ldg(d);
+        ty.touch(d + 1);
+        const unsigned s1 = __ldg(d + 1);
+        return lows_search(g, r.P + s0 - h, (long long)s1 - s0 - 1, lo, found, ty);
+    }
+    long long B = r.P;
     if (j > 0) {
-        long long z = near ? scan_near<false>(g, P, j - 1, ty) : -1;
+        long long z = near ? scan_near<false>(g, r.P, j - 1, ty) : -1;
         if (z < 0) z = select0(g, h - 1, ty);
         B = z + 1;
     }
@@ -631,10 +719,13 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
         cnt.add(C_WALKS);
         put(L, rowp, 0, (int)v0, len);
         int v = (int)v0, t = -1;
-        long long P_v, off_v, P_t = -1;
-        int deg_v, deg_t = 0;
         ty.begin();
-        region_of(g, v, P_v, off_v, deg_v, ty);
+        Row rv = region_of(g, v, ty);
+        Row row_t;                // the previous node's row
+        row_t.P = -1;
+        row_t.off = 0;
+        row_t.deg = 0;
+        row_t.slot = 0;
         float wmax_v = 0.0f;
         if (WEIGHTED) {
             ty.touch(g.wmax + v);
@@ -644,14 +735,14 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
         float w_rt = 0.0f;         // weighted: the weight there
         bool ret_known = false;
         int s = 1;
-        for (; s < len && deg_v > 0; ++s) {
-            const bool near_v = region_near(g, P_v, deg_v);
-            const bool near_t = region_near(g, P_t, deg_t);
+        for (; s < len && rv.deg > 0; ++s) {
+            const bool near_v = region_near(g, rv);
+            const bool near_t = region_near(g, row_t);
             int x = -1;
             for (unsigned k = 0; k < trial_cap; ++k) {
                 const uint4 r = trial_block(wc.seed, w, s, k);
                 cnt.add(C_TRIALS);
-                const int idx = scale_index(r.x, r.y, deg_v);
+                const int idx = scale_index(r.x, r.y, rv.deg);
                 if (t >= 0 && ret_known) {
                     if (idx == rt) {                        // the return, decided in registers
                         if (accept_test<WEIGHTED>(r.z, wmax_v, wc.tm1_ret, w_rt)) {
@@ -662,9 +753,9 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
                     }
                     if (r.z > tm1_io) continue;             // rejected whatever its class
                 }
-                const long long e = off_v + idx;
+                const long long e = rv.off + idx;
                 ty.begin();
-                const int cand = ef_target(g, row_code(g, P_v, near_v, e, idx, ty));
+                const int cand = ef_target(g, row_code(g, rv, near_v, e, idx, ty));
                 cnt.add(C_GATHERS);
                 float wv = 1.0f;
                 if (WEIGHTED) {
@@ -689,18 +780,17 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
                         cnt.add(C_SEARCHES);
                         ty.begin();
                         bool in_t;
-                        if (near_t || !g.undirected) {
-                            find_in_row(g, P_t, near_t, t, cand, in_t, ty);
+                        if (near_t || row_t.slot > 0 || !g.undirected) {
+                            find_in_row(g, row_t, near_t, t, cand, in_t, ty);
                         } else {
-                            // a long N(t) on an undirected graph: search the
-                            // shorter of N(t) and N(x) (t in N(x) <=> x in N(t))
-                            long long P_x, off_x;
-                            int deg_x;
-                            region_of(g, cand, P_x, off_x, deg_x, ty);
-                            if (deg_x < deg_t)
-                                find_in_row(g, P_x, region_near(g, P_x, deg_x), cand, t, in_t, ty);
+                            // a long N(t) without a directory on an undirected
+                            // graph: search the shorter of N(t) and N(x)
+                            // (t in N(x) <=> x in N(t))
+                            const Row rx = region_of(g, cand, ty);
+                            if (rx.deg < row_t.deg)
+                                find_in_row(g, rx, region_near(g, rx), cand, t, in_t, ty);
                             else
-                                find_in_row(g, P_t, near_t, t, cand, in_t, ty);
+                                find_in_row(g, row_t, near_t, t, cand, in_t, ty);
                         }
                         acc = in_t ? acc_in : acc_out;
                     }
@@ -712,30 +802,30 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
             }
             if (x < 0) {
                 cnt.add(C_FALLBACKS);
-                const int j = ef_fallback<WEIGHTED>(g, w, s, wc.seed, t, off_v, deg_v, wc.a_ret,
+                const int j = ef_fallback<WEIGHTED>(g, w, s, wc.seed, t, rv.off, rv.deg, wc.a_ret,
                                                     wc.a_out, trial_cap, ty);
                 ty.begin();
-                x = ef_target(g, row_code(g, P_v, near_v, off_v + j, j, ty));
+                x = ef_target(g, row_code(g, rv, near_v, rv.off + j, j, ty));
             }
             put(L, rowp, s, x, len);
             cnt.add(C_STEPS);
             t = v;
-            P_t = P_v;
-            deg_t = deg_v;
+            row_t = rv;
             v = x;
             ty.begin();
-            region_of(g, v, P_v, off_v, deg_v, ty);
+            rv = region_of(g, v, ty);
             if (WEIGHTED) {
                 ty.touch(g.wmax + v);
                 wmax_v = __ldg(g.wmax + v);
             }
-            // locate the return in a short row only (a long one costs more to
-            // search than the reads it would save)
-            ret_known = know_ret && deg_v > 0 && region_near(g, P_v, deg_v);
+            // locate the return in a short row or one with a directory (a long
+            // scan costs more than the reads it would save)
+            const bool near_new = region_near(g, rv);
+            ret_known = know_ret && rv.deg > 0 && (near_new || rv.slot > 0);
             if (ret_known) {
                 bool found;
-                const long long at = find_in_row(g, P_v, true, v, t, found, ty);
-                rt = found ? (int)(at - off_v) : -1;
+                const long long at = find_in_row(g, rv, near_new, v, t, found, ty);
+                rt = found ? (int)(at - rv.off) : -1;
                 if (WEIGHTED && found) {
                     ty.touch(g.weights + at);
                     w_rt = __ldg(g.weights + at);
@@ -785,6 +875,7 @@ void free_ef(grape_ef_graph* g) {
     cudaFree(g->weights);
     cudaFree(g->wmax);
     cudaFree(g->rowptr);
+    cudaFree(g->dir);
     cudaFree(g->status);
     cudaFree(g->counters);
     delete g;
@@ -801,7 +892,7 @@ grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts
     if (!out) return GRAPE_ERR_INVALID_ARG;
     *out = nullptr;
     if (!offsets || num_nodes < 1 || num_nodes > 0x7fffffffLL || num_entries < 0 ||
-        num_entries > (1LL << 40) || (num_entries > 0 && !dsts) ||
+        num_entries >= (1LL << kRowPtrBits) || (num_entries > 0 && !dsts) ||
         quantum < 1 || quantum > (1 << 16) || (quantum & (quantum - 1)) ||
         (flags & ~(GRAPE_UNDIRECTED | GRAPE_VALIDATE)))
         return GRAPE_ERR_INVALID_ARG;
@@ -913,6 +1004,34 @@ grape_status_t grape_ef_graph_create(const int64_t* offsets, const int32_t* dsts
             (unsigned long long)g->u, g->ones_idx, g->zeros_idx);
         e = cudaGetLastError();
     }
+    // 3. bucket directories of long rows (counted first, then filled; the
+    //    counters double as the two scratch counts and are cleared after)
+    if (e == cudaSuccess && g->l <= g->k && num_entries > 0) {
+        const long long nb = 1LL << (g->k - g->l);
+        unsigned long long count = 0;
+        ef_count_long_rows_kernel<<<ef_grid(g->num_sms, num_nodes, 256), 256, 0, stream>>>(
+            offsets, num_nodes, nb, g->counters);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&count, g->counters, sizeof(count), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess && count > 0 && count <= (unsigned long long)kMaxDirRows) {
+            const size_t dir_bytes = sizeof(unsigned) * (size_t)count * (size_t)(nb + 1);
+            e = cudaMalloc(&g->dir, dir_bytes);
+            if (e == cudaSuccess) {
+                ef_fill_dirs_kernel<<<ef_grid(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+                    offsets, dsts, num_nodes, nb, g->l, g->rowptr, g->dir, g->counters + 1);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                g->dir_rows = (int32_t)count;
+                g->structure_bytes += (int64_t)dir_bytes;
+                g->device_bytes += (int64_t)dir_bytes;
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * C_COUNT, stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
@@ -949,6 +1068,7 @@ grape_status_t grape_ef_graph_info(const grape_ef_graph_t* g, grape_ef_info_t* i
     info->quantum = g->quantum;
     info->weighted = g->weighted ? 1 : 0;
     info->max_degree = g->max_degree;
+    info->directory_rows = g->dir_rows;
     return GRAPE_OK;
 }
 

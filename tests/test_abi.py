@@ -118,7 +118,7 @@ def test_argument_errors_return_before_cuda(lib):
     assert lib.grape_ef_graph_create(None, None, None, 4, 0, 64, 0, None, ctypes.byref(h)) == INVALID
     assert lib.grape_ef_graph_create(ctypes.c_void_p(8), None, None, 4, 4, 64, 0, None,
                                      ctypes.byref(h)) == INVALID
-    assert lib.grape_ef_graph_create(ctypes.c_void_p(8), ctypes.c_void_p(8), None, 4, (1 << 40) + 1,
+    assert lib.grape_ef_graph_create(ctypes.c_void_p(8), ctypes.c_void_p(8), None, 4, 1 << 40,
                                      64, 0, None, ctypes.byref(h)) == INVALID
     assert lib.grape_ef_walks(None, None, 4, 8, 1, 1.0, 1.0, 0, 4096, None, None) == INVALID
     assert lib.grape_ef_select(None, None, 1, None, None) == INVALID

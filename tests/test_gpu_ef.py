@@ -4,7 +4,7 @@ against the CPU oracles, bit for bit:
 * the store itself: the low and high words and both indexes equal the Elias-Fano
   oracle's arrays for graphs with and without isolated nodes, directed, with a
   self-loop, |V| = 1, |V| a power of two, fewer entries than nodes (l > k), no
-  entries at all, and quanta 1 to 1024;
+  entries at all, and quanta 1 to 1024; hub rows get bucket directories;
 * select and rank on every index and on random and boundary values (bucket
   edges, row edges, values at and beyond u) equal the oracle's;
 * walks over the store equal the walk oracle's rows on tiny structured graphs
@@ -171,11 +171,25 @@ def rmat12(weighted):
     return _RMAT12[weighted]
 
 
+def expected_directory_rows(csr):
+    """Rows that get a bucket directory: deg + nb > 448 and deg >= 8 nb, with
+    nb = 2^(k - l) buckets per row (computed here from the CSR)."""
+    off, dst, _ = csr.numpy()
+    d = np.diff(off)
+    k = OEF.code_bits(csr.num_nodes)
+    l = OEF.low_bits_count(len(dst), csr.num_nodes << k)
+    if l > k or len(dst) == 0:
+        return 0
+    nb = 1 << (k - l)
+    return int(((d + nb > 448) & (d >= 8 * nb)).sum())
+
+
 @pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
 @pytest.mark.parametrize("quantum", [64, 1024])
 def test_walks_rmat12(weighted, quantum):
     csr = rmat12(weighted)
     g = EFGraph.from_csr(csr, quantum=quantum)
+    assert g.info()["directory_rows"] == expected_directory_rows(csr) > 0
     for (p, q) in [(1.0, 1.0), (2.0, 1.0), (1.0, 0.5), (0.5, 2.0), (4.0, 0.25), (0.25, 4.0)]:
         check_walks(csr, None, 24, 2, p, q, seed=99, g=g)
 
@@ -274,6 +288,7 @@ def test_walks_shorter_row_search_equals_directed_search(quantum):
     csr = synth.rmat(13, 120000, seed=23)
     for und in (False, True):
         g = EFGraph.from_csr(csr, quantum=quantum, undirected=und)
+        assert g.info()["directory_rows"] == expected_directory_rows(csr) > 0
         for (p, q) in [(1.0, 0.25), (0.5, 2.0)]:
             check_walks(csr, None, 30, 1, p, q, seed=13, g=g)
 
