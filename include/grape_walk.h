@@ -563,7 +563,8 @@ typedef struct grape_ef_counters {
     int64_t trials;            /* proposals drawn (Philox blocks) */
     int64_t codes_read;        /* proposals whose code was selected */
     int64_t membership_tests;  /* class-deciding tests x in N(t) */
-    int64_t sectors;           /* distinct 32-byte sectors read by each select, rank and weight load, summed */
+    int64_t sectors;           /* distinct 32-byte sectors each walk step reads (row pointers,
+                                  directories, high and low bits, indexes, weights), summed */
     int64_t fallbacks;         /* steps drawn by the cumulative-sum fallback */
     int64_t walks;             /* walks started from a valid start */
 } grape_ef_counters_t;

@@ -320,18 +320,27 @@ __global__ void ef_index_kernel(const int64_t* __restrict__ offsets,
 // select and rank on the device
 // ---------------------------------------------------------------------------
 
-// Distinct 32-byte sectors read by one operation (counting kernels only).
+// Distinct 32-byte sectors read (counting kernels only): a touch counts unless
+// its sector is among the last kRecent sectors touched since begin(); a walk
+// calls begin() once per step, so a sector read twice within a step (a row
+// pointer, a high-bits word) counts once.
 template <bool ON>
 struct Tally {
-    unsigned long long last = ~0ull;
+    static constexpr int kRecent = 4;
+    unsigned long long recent[kRecent];
+    unsigned next = 0;
     unsigned sectors = 0;
-    __device__ __forceinline__ void begin() { last = ~0ull; }
+    __device__ __forceinline__ void begin() {
+#pragma unroll
+        for (int i = 0; i < kRecent; ++i) recent[i] = ~0ull;
+    }
     __device__ __forceinline__ void touch(const void* p) {
         const unsigned long long s = reinterpret_cast<uintptr_t>(p) >> 5;
-        if (s != last) {
-            last = s;
-            ++sectors;
-        }
+#pragma unroll
+        for (int i = 0; i < kRecent; ++i)
+            if (recent[i] == s) return;
+        recent[next++ % kRecent] = s;
+        ++sectors;
     }
 };
 template <>
@@ -754,7 +763,6 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
                     if (r.z > tm1_io) continue;             // rejected whatever its class
                 }
                 const long long e = rv.off + idx;
-                ty.begin();
                 const int cand = ef_target(g, row_code(g, rv, near_v, e, idx, ty));
                 cnt.add(C_GATHERS);
                 float wv = 1.0f;
@@ -778,7 +786,6 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
                     acc = acc_in;
                     if (acc_in != acc_out) {      // only then does the class decide
                         cnt.add(C_SEARCHES);
-                        ty.begin();
                         bool in_t;
                         if (near_t || row_t.slot > 0 || !g.undirected) {
                             find_in_row(g, row_t, near_t, t, cand, in_t, ty);
@@ -804,7 +811,6 @@ ef_walk_kernel(EFDev g, WalkConst wc, unsigned trial_cap, int know_ret) {
                 cnt.add(C_FALLBACKS);
                 const int j = ef_fallback<WEIGHTED>(g, w, s, wc.seed, t, rv.off, rv.deg, wc.a_ret,
                                                     wc.a_out, trial_cap, ty);
-                ty.begin();
                 x = ef_target(g, row_code(g, rv, near_v, rv.off + j, j, ty));
             }
             put(L, rowp, s, x, len);
