@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-contexts", action="store_true")
+    ap.add_argument("--no-cumsum", action="store_true",
+                    help="skip the cumulative-sum sampler vs rejection comparison")
     ap.add_argument("--ef-quanta", default="64,1024",
                     help="Elias-Fano store leg: index quanta to build and walk ('' to skip)")
     ap.add_argument("--suss-k", type=int, default=0,
@@ -453,6 +455,8 @@ def run_ours(args, dist):
         res["approx"] = approx
     if want_batched and not args.no_contexts:
         res["contexts"] = bench_contexts(g, job, n, dev, peak)
+    if want_batched and not args.no_cumsum:
+        res["cumsum_sampler"] = bench_cumsum(g, job, n, dev)
     if want_cpu:
         rate, cores, sample = oracle_rate(csr_host, job, args.cpu_seconds)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -509,6 +513,44 @@ def bench_ef(store, build_s, job, n, dev, ref, csr_bytes, reps=3):
             "membership_tests_per_step": c["membership_tests"] / max(1, c["steps"]),
             "trials_per_step": c["trials"] / max(1, c["steps"]),
             "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / ms / 1e6}
+
+
+def bench_cumsum(g, job, n, dev, walks_n=1 << 20, reps=3):
+    """The paper's cumulative-sum sampler at every step (grape_walks_cumsum)
+    against rejection (grape_walks) on the first 2^20 starts, one walk each:
+    at the job's (p, q), and at an adversarial p = 1/16, q = 4 where rejection
+    accepts few proposals (outward moves at 1/64 of the bound, times w/wmax).
+    Each entry: launch ms, steps/s, and rejection's proposals per step."""
+    from paper_2110_06196_gb300 import walks, walks_cumsum
+    ns = min(n, walks_n)
+    out = torch.empty((ns, job.walk_len), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = []
+    for (p, q) in [(job.p, job.q), (1.0 / 16, 4.0)]:
+        entry = {"p": p, "q": q, "walks": ns}
+        for name, fn in (("rejection", walks), ("cumsum", walks_cumsum)):
+            fn(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+            torch.cuda.synchronize(dev)
+            if name == "rejection":
+                g.counters(enable=True)
+                fn(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+                torch.cuda.synchronize(dev)
+                c = g.counters()
+                g.counters(enable=False)
+                entry["rejection_trials_per_step"] = c["trials"] / max(1, c["steps"])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            steps = count_steps(out)
+            entry[name] = {"ms_per_launch": ms, "steps_per_s": steps / ms * 1e3}
+        res.append(entry)
+    del out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_contexts(g, job, n, dev, peak, window=5, chunk=1 << 22):

@@ -205,6 +205,23 @@ grape_status_t grape_walks_approx(const grape_graph_t* graph, const int32_t* sta
                                   grape_stream_t stream);
 
 /*
+ * The walks of grape_walks drawn at every step by the paper's own on-the-fly
+ * sampler (GRAPE, Methods, "Efficient sampling for Node2Vec RWs"): the
+ * un-normalised probabilities alpha(t, x) * w_vx of every neighbour, their
+ * cumulative sum in row order, u = ((r1:r0) >> 11) * 2^-53 * total from the
+ * Philox block of trial index 0, and the first neighbour whose cumulative sum
+ * exceeds u, in fp64 with every product and sum rounded once.  Its rows equal
+ * grape_walks' rows with trial_cap = 0.  A step reads all of N(v) and tests each
+ * neighbour against N(t), so its cost does not depend on (p, q) or the weights:
+ * the alternative to rejection where most proposals would be rejected.
+ * Arguments as grape_walks.
+ */
+grape_status_t grape_walks_cumsum(const grape_graph_t* graph, const int32_t* starts,
+                                  int64_t num_starts, int32_t walk_len, int32_t walks_per_node,
+                                  double p, double q, uint64_t seed, int32_t* out,
+                                  grape_stream_t stream);
+
+/*
  * The same walks as grape_walks, with `starts` and `out` in HOST memory
  * (pageable or pinned).  The call copies the starts in, runs the walks and
  * copies the rows out, and returns once `out` holds them (it synchronises

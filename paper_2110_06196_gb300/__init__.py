@@ -6,10 +6,11 @@ ctypes), and ``elias_fano`` that of the Elias-Fano graph store.  ``synth``
 builds seeded synthetic inputs.
 """
 from .walk import (BatchPlan, Graph, Server, autotune_batched, contexts, contexts_from_rows,
-                   philox4x32_10, sector_probe, walks, walks_approx, walks_batched, walks_host)
+                   philox4x32_10, sector_probe, walks, walks_approx, walks_batched, walks_cumsum,
+                   walks_host)
 from .elias_fano import EFGraph, ef_walks
 from ._lib import GrapeError
 
-__all__ = ["Graph", "walks", "walks_approx", "walks_host", "walks_batched", "BatchPlan", "autotune_batched",
+__all__ = ["Graph", "walks", "walks_cumsum", "walks_approx", "walks_host", "walks_batched", "BatchPlan", "autotune_batched",
            "Server", "contexts", "contexts_from_rows", "philox4x32_10", "sector_probe",
            "EFGraph", "ef_walks", "GrapeError"]

@@ -132,6 +132,8 @@ SIGNATURES = {
                                    c_vp, c_vp]),
     "grape_walk_contexts": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_i32,
                                     c_i64, c_i64, c_vp, c_vp, c_vp]),
+    "grape_walks_cumsum": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_vp,
+                                   c_vp]),
     "grape_ef_graph_create": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i64, c_i32, c_u32, c_vp, c_vp]),
     "grape_ef_graph_destroy": (None, [c_vp]),
     "grape_ef_graph_info": (c_i32, [c_vp, c_vp]),

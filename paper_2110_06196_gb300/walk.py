@@ -127,6 +127,25 @@ def walks(graph: Graph, starts=None, walk_len=80, walks_per_node=1, p=1.0, q=1.0
     return out
 
 
+def walks_cumsum(graph: Graph, starts=None, walk_len=80, walks_per_node=1, p=1.0, q=1.0, seed=0,
+                 num_starts=None, out=None, stream=None) -> torch.Tensor:
+    """grape_walks_cumsum: the paper's cumulative-sum sampler at every step (the
+    rows of walks() with trial_cap = 0)."""
+    lib = graph._lib
+    if starts is not None:
+        starts = _dev_tensor(starts, torch.int32, graph.device)
+        ns = starts.numel()
+    else:
+        ns = graph.num_nodes if num_starts is None else int(num_starts)
+    if out is None:
+        out = torch.empty((ns * walks_per_node, walk_len), dtype=torch.int32, device=graph.device)
+    code = lib.grape_walks_cumsum(graph.handle, _ptr(starts), ns, walk_len, walks_per_node,
+                                  float(p), float(q), int(seed) & (2**64 - 1), _ptr(out),
+                                  _stream_ptr(stream))
+    check(code, "grape_walks_cumsum")
+    return out
+
+
 def walks_approx(graph: Graph, starts=None, walk_len=80, walks_per_node=1, p=1.0, q=1.0, seed=0,
                  suss_k=10000, num_starts=None, out=None, stream=None) -> torch.Tensor:
     """grape_walks_approx: approximated walks (SUSS sub-samples of suss_k

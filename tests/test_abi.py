@@ -124,6 +124,7 @@ def test_argument_errors_return_before_cuda(lib):
     assert lib.grape_ef_select(None, None, 1, None, None) == INVALID
     assert lib.grape_ef_rank(None, None, 1, None, None) == INVALID
     assert lib.grape_ef_graph_info(None, None) == INVALID
+    assert lib.grape_walks_cumsum(None, None, 4, 8, 1, 1.0, 1.0, 0, None, None) == INVALID
     lib.grape_ef_graph_destroy(None)
     lib.grape_graph_destroy(None)
     lib.grape_walk_server_destroy(None)
