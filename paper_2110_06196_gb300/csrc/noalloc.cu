@@ -53,6 +53,9 @@ struct StaticQueueFeed {
     bool drained;
 
     __device__ __forceinline__ unsigned long long seed(const Lane&) const { return wrec()->seed; }
+    __device__ __forceinline__ uint4 trial(const Lane& L, unsigned k) const {
+        return trial_block(wrec()->seed, L.w, L.s, k);
+    }
     __device__ __forceinline__ int len(const Lane&) const { return wrec()->len; }
     __device__ __forceinline__ unsigned tm1_ret(const Lane&) const { return wrec()->tm1_ret; }
     __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wrec()->tm1_in; }

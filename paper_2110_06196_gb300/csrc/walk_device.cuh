@@ -126,6 +126,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// The round keys of one seed: round i uses (seed lo + i 0x9E3779B9,
+// seed hi + i 0xBB67AE85).  A per-call launch passes them as a kernel parameter,
+// so the rounds read them from the constant bank instead of adding them up.
+struct RoundKeys {
+    unsigned k[20];
+};
+
+__host__ __device__ inline RoundKeys round_keys(unsigned long long seed) {
+    RoundKeys rk;
+    unsigned a = (unsigned)seed, b = (unsigned)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        rk.k[2 * i] = a;
+        rk.k[2 * i + 1] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+// philox4x32_10 with the round keys given.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ rk.k[2 * i], (unsigned)p1,
+                       (unsigned)(p0 >> 32) ^ c.w ^ rk.k[2 * i + 1], (unsigned)p0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 trial_block(unsigned long long seed, long long w, int s,
                                              unsigned k) {
     const unsigned long long uw = (unsigned long long)w;
@@ -536,8 +567,16 @@ __device__ __forceinline__ void set_wrec(const WalkConst& wc, long long row) {
 template <bool SUSS>
 struct GridFeed {
     const WalkConst* wc;     // kernel-parameter copy
+    const RoundKeys* rk;     // kernel-parameter copy: the Philox round keys of wc->seed
     long long next;
     long long stride;
+
+    // The Philox block of trial k of the lane's current step.
+    __device__ __forceinline__ uint4 trial(const Lane& L, unsigned k) const {
+        const unsigned long long uw = (unsigned long long)L.w;
+        return philox4x32_10_rk(make_uint4((unsigned)uw, (unsigned)(uw >> 32), (unsigned)L.s, k),
+                                *rk);
+    }
 
     // Per-call constants are uniform: read them from the kernel parameters
     // (constant bank) instead of holding them in every lane's registers.
@@ -611,6 +650,9 @@ struct QueueFeed {
 
     // Per-request constants differ between lanes: held in the lane.
     __device__ __forceinline__ unsigned long long seed(const Lane&) const { return wrec()->seed; }
+    __device__ __forceinline__ uint4 trial(const Lane& L, unsigned k) const {
+        return trial_block(wrec()->seed, L.w, L.s, k);
+    }
     __device__ __forceinline__ int len(const Lane&) const { return wrec()->len; }
     __device__ __forceinline__ unsigned tm1_ret(const Lane&) const { return wrec()->tm1_ret; }
     __device__ __forceinline__ unsigned tm1_in(const Lane&) const { return wrec()->tm1_in; }
@@ -1048,7 +1090,7 @@ struct Engine {
                 if (L.k >= trial_cap) {
                     if (!fallback_steps(L)) return false;
                 }
-                const uint4 r = trial_block(feed.seed(L), L.w, L.s, L.k);
+                const uint4 r = feed.trial(L, L.k);
                 const int sk = feed.suss_k(L);
                 const int idx = (sk > 0 && L.deg_v > sk)
                                     ? suss_pos(feed.seed(L), L.w, L.s, scale_index(r.x, r.y, sk),

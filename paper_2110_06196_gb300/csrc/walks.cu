@@ -32,9 +32,11 @@ constexpr int kMinBlocksQueue = 4;
 // the general p, q specialisation.
 template <bool W, bool P, bool Q, bool COUNT, bool SUSS = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
-walk_kernel(GraphDev g, WalkConst wc, unsigned trial_cap, int shorter_min, int interp_search) {
+walk_kernel(GraphDev g, WalkConst wc, RoundKeys rk, unsigned trial_cap, int shorter_min,
+            int interp_search) {
     GridFeed<SUSS> f;
     f.wc = &wc;
+    f.rk = &rk;
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
     walk_loop<W, P, Q, COUNT>(g, f, trial_cap, shorter_min, interp_search);
@@ -136,7 +138,8 @@ cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const W
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     walk_kernel<W, P, Q, C, S><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
-        g->dev(), wc, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
+        g->dev(), wc, round_keys(wc.seed), (unsigned)t.trial_cap, t.shorter_min,
+        t.interp_search);
     return cudaGetLastError();
 }
 
