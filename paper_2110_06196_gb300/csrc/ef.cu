@@ -18,14 +18,18 @@
 //                 zero j closing bucket j (it follows every code whose high part is <= j)
 //   ones_index[]  position of one number j q,   j < ceil(m / q)
 //   zeros_index[] position of zero number j q,  j < ceil(Z / q)
-// Both bit arrays carry four words of zero padding.
+// Both bit arrays carry four words of zero padding.  Beside the paper's layout
+// the store keeps the row pointers (rank(phi(a, 0)) of every node, with a
+// directory slot in the high bits) and bucket directories for hub rows, so a
+// walk reads a degree in one access and never scans the dense high bits of a
+// hub's row.
 //
 // Walks over the store follow the same rule as the CSR engine (rejection
 // against max(1/p, 1, 1/q) * wmax_v with Philox blocks keyed by (seed, walk,
 // step, trial), then the cumulative-sum fallback), so their rows are
 // byte-identical to grape_walks' rows for the same graph.  One thread owns one
-// walk; every neighbour, degree and membership test is a select or rank on the
-// compressed store.
+// walk; every neighbour is a select and every membership test a bucket search
+// on the compressed store.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -501,22 +505,6 @@ __device__ long long rank_code(const EFDev& g, unsigned long long c, bool& found
     const long long h = (long long)(c >> g.l);
     const unsigned long long lo = g.l ? (c & ((1ull << g.l) - 1)) : 0ull;
     return bucket_search(g, bucket_begin(g, h, ty), h, lo, found, ty);
-}
-
-// First code of row a and its degree (a row that does not fit inside the
-// codes, from an inconsistent store, reads as empty and sets status bit 1).
-template <bool C>
-__device__ __forceinline__ void row_of(const EFDev& g, long long a, long long& off, int& deg,
-                                       Tally<C>& ty) {
-    bool f;
-    off = rank_code(g, (unsigned long long)a << g.k, f, ty);
-    const long long end = rank_code(g, (unsigned long long)(a + 1) << g.k, f, ty);
-    deg = (int)(end - off);
-    if (off < 0 || end < off || end > g.m || end - off > 0x7fffffffLL) {
-        atomicOr(g.status, 2);
-        off = 0;
-        deg = 0;
-    }
 }
 
 __global__ void ef_select_kernel(EFDev g, const long long* __restrict__ idx, long long n,
