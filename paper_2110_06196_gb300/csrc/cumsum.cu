@@ -10,13 +10,15 @@
 //   4. the first neighbour whose cumulative sum exceeds u.
 // Products and sums are fp64, each rounded once, in row order: the arithmetic
 // of the rejection path's exact fallback, so these rows are grape_walks' rows
-// with trial_cap = 0.  The step costs O(deg(v) log deg(t)) reads whatever the
+// with trial_cap = 0.  The step costs O(deg(v)) reads and searches whatever the
 // acceptance rate, which is what makes it the alternative to rejection for
 // (p, q, weight) settings that reject most proposals.
 //
 // One warp owns one walk.  The lanes read 32 consecutive entries of N(v) at a
-// time (coalesced) and each tests its own x in N(t) by binary search, so the
-// in-out bias, which the paper names as the bottleneck, runs 32 wide.  Step 4
+// time (coalesced) and each tests its own x in N(t) by binary search, so
+// the in-out bias, which the paper names as the bottleneck, runs 32 wide; the
+// second pass takes the products of the first 256 entries from shared memory
+// and the membership of the first 1024 from per-lane bit masks.  Step 4
 // compares 32 cumulative sums at once (the warp's form of the paper's linear
 // scan).  The cumulative sums must round as the sequential sum does: when every
 // product of the row is a multiple of 2^lo and the row's total stays below
@@ -35,6 +37,7 @@ namespace {
 constexpr int kCsThreads = 256;
 constexpr int kCsWarps = kCsThreads / 32;
 constexpr int kCsCache = 256;   // products a warp keeps from the first pass for the second
+constexpr int kCsMaskRows = 1024;   // entries whose membership bits a lane keeps (32 chunks)
 
 // p > 0 finite: p = m 2^b with m a 53-bit integer; lo = exponent of p's lowest
 // set bit, hi = floor(log2 p).
@@ -48,7 +51,11 @@ __device__ __forceinline__ void product_bits(double p, int& lo, int& hi) {
     hi = b + 63 - __clzll((long long)m);
 }
 
-// Is key in the sorted list a[0, n)?
+// Is key in the sorted list a[0, n)?  Binary search: the 32 lanes of a warp
+// search the same N(t) for 32 increasing keys, so their first probes share
+// sectors, which stay cached while hub rows are searched again and again (an
+// interpolation search, which spreads the lanes' probes at once, measured 3.3x
+// slower here).
 __device__ __forceinline__ bool in_sorted(const int* __restrict__ a, long long n, int key) {
     long long lo = 0, hi = n;
     while (lo < hi) {
@@ -59,6 +66,19 @@ __device__ __forceinline__ bool in_sorted(const int* __restrict__ a, long long n
     return lo < n && __ldg(a + lo) == key;
 }
 
+// alpha(t, x) of entry j of row v: a_ret, 1 or a_out (1 on the first step).
+__device__ __forceinline__ double alpha_of(const GraphDev& g, int x, int t, long long off_t,
+                                           long long deg_t, double a_ret, double a_out) {
+    if (t < 0) return 1.0;
+    if (x == t) return a_ret;
+    return in_sorted(g.dsts + off_t, deg_t, x) ? 1.0 : a_out;
+}
+
+template <bool WEIGHTED>
+__device__ __forceinline__ double weight_of(const GraphDev& g, long long e) {
+    return WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
+}
+
 // pi of entry j of row v: alpha(t, x) * w, rounded once.
 template <bool WEIGHTED>
 __device__ __forceinline__ double product(const GraphDev& g, long long off_v, long long j, int t,
@@ -66,10 +86,7 @@ __device__ __forceinline__ double product(const GraphDev& g, long long off_v, lo
                                           double a_out) {
     const long long e = off_v + j;
     const int x = __ldg(g.dsts + e);
-    double a = 1.0;
-    if (t >= 0) a = (x == t) ? a_ret : (in_sorted(g.dsts + off_t, deg_t, x) ? 1.0 : a_out);
-    const double w = WEIGHTED ? (double)__int_as_float(__ldg(&g.fat[2 * e + 1].x)) : 1.0;
-    return __dmul_rn(a, w);
+    return __dmul_rn(alpha_of(g, x, t, off_t, deg_t, a_ret, a_out), weight_of<WEIGHTED>(g, e));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -108,11 +125,36 @@ cumsum_walk_kernel(GraphDev g, WalkConst wc) {
             // 1-2: the products, the grid they sit on, and the lanes' partial sums
             int lo_min = INT_MAX, hi_max = INT_MIN;
             double part = 0.0;
+            unsigned inmask = 0;       // bit c / 32: this lane's entry of chunk c is in N(t)
+            // the product of entry j (j = c + lane) again: from the cache, from
+            // the membership bits, or computed afresh
+            auto again = [&](long long j) -> double {
+                if (j < kCsCache) return pc[j];
+                if (j >= kCsMaskRows)
+                    return product<WEIGHTED>(g, rv.off, j, t, off_t, deg_t, wc.a_ret, wc.a_out);
+                const long long e = rv.off + j;
+                const int x = __ldg(g.dsts + e);
+                const double a = t < 0 ? 1.0
+                                       : (x == t ? wc.a_ret
+                                                 : (((inmask >> (j >> 5)) & 1u) ? 1.0 : wc.a_out));
+                return __dmul_rn(a, weight_of<WEIGHTED>(g, e));
+            };
             for (long long c = 0; c < d; c += 32) {
                 const long long j = c + lane;
                 if (j < d) {
-                    const double p = product<WEIGHTED>(g, rv.off, j, t, off_t, deg_t, wc.a_ret,
-                                                       wc.a_out);
+                    const long long e = rv.off + j;
+                    const int x = __ldg(g.dsts + e);
+                    double a = 1.0;
+                    if (t >= 0) {
+                        if (x == t) {
+                            a = wc.a_ret;
+                        } else {
+                            const bool in = in_sorted(g.dsts + off_t, deg_t, x);
+                            if (in && j < kCsMaskRows) inmask |= 1u << (j >> 5);
+                            a = in ? 1.0 : wc.a_out;
+                        }
+                    }
+                    const double p = __dmul_rn(a, weight_of<WEIGHTED>(g, e));
                     int lo, hi;
                     product_bits(p, lo, hi);
                     lo_min = min(lo_min, lo);
@@ -133,11 +175,7 @@ cumsum_walk_kernel(GraphDev g, WalkConst wc) {
                 total = 0.0;
                 for (long long c = 0; c < d; c += 32) {
                     const long long j = c + lane;
-                    double p = 0.0;
-                    if (j < d)
-                        p = j < kCsCache ? pc[j]
-                                         : product<WEIGHTED>(g, rv.off, j, t, off_t, deg_t,
-                                                             wc.a_ret, wc.a_out);
+                    const double p = j < d ? again(j) : 0.0;
                     const int n = (int)min(32LL, d - c);
                     for (int k = 0; k < n; ++k) total = __dadd_rn(total, __shfl_sync(FULL, p, k));
                 }
@@ -151,11 +189,7 @@ cumsum_walk_kernel(GraphDev g, WalkConst wc) {
             double carry = 0.0;
             for (long long c = 0; c < d; c += 32) {
                 const long long j = c + lane;
-                double p = 0.0;
-                if (j < d)
-                    p = j < kCsCache ? pc[j]
-                                     : product<WEIGHTED>(g, rv.off, j, t, off_t, deg_t, wc.a_ret,
-                                                         wc.a_out);
+                const double p = j < d ? again(j) : 0.0;
                 double S;
                 if (exact) {
                     S = p;
