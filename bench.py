@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-contexts", action="store_true")
     ap.add_argument("--no-cumsum", action="store_true",
                     help="skip the cumulative-sum sampler vs rejection comparison")
+    ap.add_argument("--cumsum-walks", type=int, default=1 << 20,
+                    help="starts (one walk each) of the cumulative-sum comparison")
     ap.add_argument("--ef-quanta", default="64,1024",
                     help="Elias-Fano store leg: index quanta to build and walk ('' to skip)")
     ap.add_argument("--suss-k", type=int, default=0,
@@ -456,7 +458,7 @@ def run_ours(args, dist):
     if want_batched and not args.no_contexts:
         res["contexts"] = bench_contexts(g, job, n, dev, peak)
     if want_batched and not args.no_cumsum:
-        res["cumsum_sampler"] = bench_cumsum(g, job, n, dev)
+        res["cumsum_sampler"] = bench_cumsum(g, job, n, dev, walks_n=args.cumsum_walks)
     if want_cpu:
         rate, cores, sample = oracle_rate(csr_host, job, args.cpu_seconds)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -517,7 +519,7 @@ def bench_ef(store, build_s, job, n, dev, ref, csr_bytes, reps=3):
 
 def bench_cumsum(g, job, n, dev, walks_n=1 << 20, reps=3):
     """The paper's cumulative-sum sampler at every step (grape_walks_cumsum)
-    against rejection (grape_walks) on the first 2^20 starts, one walk each:
+    against rejection (grape_walks) on the first walks_n starts, one walk each:
     at the job's (p, q), and at an adversarial p = 1/16, q = 4 where rejection
     accepts few proposals (outward moves at 1/64 of the bound, times w/wmax).
     Each entry: launch ms, steps/s, and rejection's proposals per step."""
