@@ -216,6 +216,17 @@ def test_walks_ragged_lengths_starts_and_dead_ends():
     check_walks(d, None, 40, 5, 1.0, 0.5, seed=3, quantum=1, undirected=False)
 
 
+def test_walks_with_more_low_bits_than_code_bits():
+    # 400 entries over 1000 nodes: l > k, rows do not start buckets, and the
+    # walks fall back to rank and select on the whole store
+    csr = store_graphs()["sparse_l_gt_k"]
+    g = EFGraph.from_csr(csr, quantum=8)
+    info = g.info()
+    assert info["low_bits"] > info["code_bits"] and info["directory_rows"] == 0
+    for (p, q) in [(1.0, 1.0), (0.5, 2.0), (4.0, 0.25)]:
+        check_walks(csr, None, 12, 2, p, q, seed=21, g=g)
+
+
 def test_walks_out_of_range_starts():
     csr = rmat12(False)
     g = EFGraph.from_csr(csr)
