@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-contexts", action="store_true")
     ap.add_argument("--no-cumsum", action="store_true",
                     help="skip the cumulative-sum sampler vs rejection comparison")
+    ap.add_argument("--no-specialisations", action="store_true",
+                    help="skip the timing of the eight p == 1 / q == 1 / weighted variants")
     ap.add_argument("--cumsum-walks", type=int, default=1 << 20,
                     help="starts (one walk each) of the cumulative-sum comparison")
     ap.add_argument("--ef-quanta", default="64,1024",
@@ -457,6 +459,8 @@ def run_ours(args, dist):
         res["approx"] = approx
     if want_batched and not args.no_contexts:
         res["contexts"] = bench_contexts(g, job, n, dev, peak)
+    if want_batched and not args.no_specialisations:
+        res["specialisations"] = bench_specialisations(g, csr, job, n, dev)
     if want_batched and not args.no_cumsum:
         res["cumsum_sampler"] = bench_cumsum(g, job, n, dev, walks_n=args.cumsum_walks)
     if want_cpu:
@@ -515,6 +519,37 @@ def bench_ef(store, build_s, job, n, dev, ref, csr_bytes, reps=3):
             "membership_tests_per_step": c["membership_tests"] / max(1, c["steps"]),
             "trials_per_step": c["trials"] / max(1, c["steps"]),
             "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / ms / 1e6}
+
+
+def bench_specialisations(g, csr, job, n, dev, walks_n=1 << 20, reps=3):
+    """GRAPE's eight node2vec specialisations (p == 1 or not, q == 1 or not,
+    weighted or not) on the first walks_n starts of this graph, one walk each of
+    the job's length: the weighted graph as built, and the same rows without
+    weights.  p = 0.5 and q = 2 stand for p != 1 and q != 1."""
+    from paper_2110_06196_gb300 import Graph, walks
+    ns = min(n, walks_n)
+    gu = Graph(csr.offsets, csr.dsts, None, validate=False, device=dev)
+    out = torch.empty((ns, job.walk_len), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = []
+    for weighted, gg in ((False, gu), (True, g)):
+        for (p, q) in [(1.0, 1.0), (0.5, 1.0), (1.0, 2.0), (0.5, 2.0)]:
+            walks(gg, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                walks(gg, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            res.append({"weighted": weighted, "p": p, "q": q, "ms_per_launch": ms,
+                        "steps_per_s": count_steps(out) / ms * 1e3})
+    gu.close()
+    del out
+    torch.cuda.empty_cache()
+    rates = [r["steps_per_s"] for r in res]
+    return {"walks": ns, "variants": res, "fastest_over_slowest": max(rates) / min(rates)}
 
 
 def bench_cumsum(g, job, n, dev, walks_n=1 << 20, reps=3):
