@@ -7,9 +7,10 @@ mixed by degree; the exact fallback
 (trial caps 0 and 2); tiny and structured graphs (house with a self-loop,
 directed with a dead end, star, path, K_n); ragged walk counts and lengths,
 unaligned output, explicit start lists, out-of-range starts, shards of a job,
-host-buffer calls; the 1,000-node ER workload in full; and the R-MAT scale-20
-weighted and scale-24 hub-heavy workloads at full size, checked on sampled walk
-ids and on every walk that starts at a top hub.
+host-buffer calls; the 1,000-node ER workload in full; the R-MAT scale-20
+weighted workload at full size in full (10.5 M walks); and the scale-24
+hub-heavy workload at full size on 2^20 walk ids in blocks plus every walk that
+starts at one of the top 100 hubs (and both on sampled ids with top-64 hubs).
 """
 import numpy as np
 import pytest
@@ -329,3 +330,62 @@ def test_rmat20_weighted_workload_sampled_parity():
 @pytest.mark.slow
 def test_rmat24_workload_sampled_parity():
     assert _sampled_parity("rmat24", 20000) > 20000
+
+
+@pytest.mark.slow
+def test_rmat20w_workload_full_parity():
+    # the whole job (10,485,760 walks x 100 entries, 1.05 G steps) against the
+    # oracle, its walk ids split over the host cores in blocks of 2^20
+    spec = synth.WORKLOADS["rmat20w"]
+    job = spec["job"]
+    csr = synth.workload_graph("rmat20w", device="cuda")
+    g = Graph.from_csr(csr, validate=False)
+    out = walks(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed)
+    torch.cuda.synchronize()
+    g.stream_status()
+    total = out.shape[0]
+    og = oracle.Graph(*csr.to("cpu").numpy())
+    block = 1 << 20
+    for lo in range(0, total, block):
+        hi = min(total, lo + block)
+        want = oracle.walks_parallel(og, None, job.walk_len, job.walks_per_node, job.p, job.q,
+                                     job.seed, walk_ids=(lo, hi))
+        got = out[lo:hi].cpu().numpy()
+        bad = np.argwhere((got != want).any(axis=1))[:, 0]
+        assert len(bad) == 0, f"walk {lo + bad[0]} differs ({len(bad)} rows in [{lo}, {hi}))"
+
+
+@pytest.mark.slow
+def test_rmat24_workload_million_walks_and_hub_starts():
+    # 2^20 walk ids in 8 blocks at seeded offsets, plus every walk from the top
+    # 100 hubs, of the full 167.8 M-walk job
+    spec = synth.WORKLOADS["rmat24"]
+    job = spec["job"]
+    csr = synth.workload_graph("rmat24", device="cuda")
+    g = Graph.from_csr(csr, validate=False)
+    out = walks(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed)
+    torch.cuda.synchronize()
+    g.stream_status()
+    n = csr.num_nodes
+    total = out.shape[0]
+    top = torch.topk(csr.degrees(), 100).indices.cpu().numpy()
+    og = oracle.Graph(*csr.to("cpu").numpy())
+    del csr
+    block = 1 << 17
+    rng = np.random.default_rng(24)
+    starts = np.sort(rng.choice(total // block, size=8, replace=False)) * block
+    checked = 0
+    for lo in starts:
+        hi = lo + block
+        want = oracle.walks_parallel(og, None, job.walk_len, job.walks_per_node, job.p, job.q,
+                                     job.seed, walk_ids=(int(lo), int(hi)))
+        got = out[int(lo):int(hi)].cpu().numpy()
+        bad = np.argwhere((got != want).any(axis=1))[:, 0]
+        assert len(bad) == 0, f"walk {lo + bad[0]} differs"
+        checked += block
+    hub_ids = (top[None, :] + n * np.arange(job.walks_per_node)[:, None]).ravel()
+    want = oracle.walk_rows(og, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
+                            hub_ids)
+    got = out[torch.from_numpy(hub_ids).cuda()].cpu().numpy()
+    assert np.array_equal(got, want)
+    assert checked + len(hub_ids) >= (1 << 20)
