@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="rmat20w", choices=["er1k", "rmat20w", "rmat21", "rmat22", "rmat24"])
+    ap.add_argument("--workload", default="rmat20w", choices=["er1k", "rmat20w", "rmat21", "rmat22", "rmat24", "rmat26"])
     ap.add_argument("--mode", choices=["walks", "serve"], default="walks")
     ap.add_argument("--walks-per-node", type=int, default=0,
                     help="override the workload's walks per node (a smaller case of the same "

@@ -272,8 +272,10 @@ WORKLOADS = {
     # kernel at a size a full profiler capture holds (about 3 GB on device).
     "rmat21": dict(kind="rmat", scale=21, m=1 << 25, seed=3, weighted=False,
                    job=WalkJob(80, 1, 1.0, 0.25, 11)),
-    # R-MAT scale 26, 1B undirected edges, unweighted (serving graph).
-    "rmat26": dict(kind="rmat", scale=26, m=1 << 30, seed=5, weighted=False, job=None),
+    # R-MAT scale 26, 1B undirected edges, unweighted: the serving graph, and a
+    # walk job of the scale-24 kind with one walk per node.
+    "rmat26": dict(kind="rmat", scale=26, m=1 << 30, seed=5, weighted=False,
+                   job=WalkJob(80, 1, 1.0, 0.25, 13)),
 }
 
 
