@@ -1,15 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark: node2vec second-order walk throughput on GB300.
 
-Default workload: R-MAT scale 20 (2^20 nodes, 16,777,216 undirected edges, fp32
-weights U[0.1, 1]), p = 0.5, q = 2, walk length 100, 10 walks per node
-(10,485,760 walks), seed 7.  One step = one grape_walks launch over the whole
-job (every row of the output).  The graph is 418 MB and the output 4.2 GB, both
-larger than the 129 MB L2, so no flush is needed between steps.
+Headline workload: R-MAT scale 24 (2^24 nodes, 268,435,456 undirected edges,
+unweighted, max degree ~1e5), p = 1, q = 0.25, walk length 80, 10 walks per
+node (167,772,160 walks, 7.06 G steps), seed 11.  One step = one grape_walks
+launch over the whole job (every row of the output).  The graph (19.6 GB) and
+the output (53.7 GB) are both far larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Beside the headline, rank 0 of a one-GPU run also reports: the random-sector
+ceiling (a sweep of the gather probe), the CPU oracle on the host cores (all
+cores and one thread), the weighted R-MAT scale-20 job (per call, batched 512
+requests, context windows, the eight specialisations, the paper's cumulative
+-sum sampler, the Elias-Fano store), and continuous-batching serving on the
+R-MAT scale-26 graph (2^30 undirected edges) under Poisson arrivals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
-  python bench.py --mode serve ...       # continuous-batching server latency run
 
 With N > 1 (torchrun, one rank per GPU) every rank builds the same graph and
 runs its own shard of a job N times as large (walk ids [r*W, (r+1)*W)).
@@ -37,6 +44,14 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
+T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 METRIC = ("walk steps/sec + HBM sector GB/s vs ~8 TB/s; batched/served vs per-request; "
           "p50/p99")
 UNIT = "walk steps/s"
@@ -49,13 +64,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="rmat20w", choices=["er1k", "rmat20w", "rmat21", "rmat22", "rmat24", "rmat26"])
-    ap.add_argument("--mode", choices=["walks", "serve"], default="walks")
+    ap.add_argument("--workload", default="rmat24", choices=["er1k", "rmat20w", "rmat21", "rmat22", "rmat24", "rmat26"])
+    ap.add_argument("--extras-workload", default="rmat20w",
+                    help="graph of the batched / contexts / specialisations / cumulative-sum / "
+                         "Elias-Fano legs ('' to skip them)")
     ap.add_argument("--walks-per-node", type=int, default=0,
                     help="override the workload's walks per node (a smaller case of the same "
                          "graph, for profiling); 0 keeps the workload's own")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-hub-ab", action="store_true",
+                    help="skip the membership-search schedule comparison")
+    ap.add_argument("--no-probe-sweep", action="store_true",
+                    help="time only the probe's default shape instead of sweeping it")
     ap.add_argument("--no-contexts", action="store_true")
     ap.add_argument("--no-cumsum", action="store_true",
                     help="skip the cumulative-sum sampler vs rejection comparison")
@@ -69,8 +91,13 @@ def parse():
                     help="also time the workload's approximated walks (SUSS sub-samples of k "
                          "neighbours at nodes of degree above k)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-single-seconds", type=float, default=8.0)
     ap.add_argument("--serve-rates", default="50,200,1000")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-max-s", type=float, default=120.0,
+                    help="a rate's arrivals stop after this many seconds")
+    ap.add_argument("--serve-saturation", type=int, default=400,
+                    help="requests submitted at once for the served-vs-per-request ratio")
     ap.add_argument("--serve-graph", default="rmat26")
     return ap.parse_args()
 
@@ -215,34 +242,72 @@ def count_steps(out: torch.Tensor) -> int:
     return total
 
 
-def algorithmic_bytes(c: dict, rows: int, walk_len: int) -> int:
-    """Sector-granular lower bound on the DRAM bytes of one launch: one 32-byte
-    sector per proposal whose entry has to be read (the entry holds the
-    candidate, its weight and the candidate's row offset and degree, so an
-    accepted step needs nothing more; returns and certain rejections are decided
-    without one), one per acceptance-deciding membership test (the least any
-    search structure can read), one per walk start (the start's record), plus
-    the 4-byte output entries."""
+def sector_minimal_bytes(c: dict, rows: int, walk_len: int) -> int:
+    """Sector-granular lower bound on the DRAM bytes of one launch of this
+    engine: one 32-byte sector per proposal whose entry has to be read (the
+    entry holds the candidate, its weight and the candidate's row offset and
+    degree, so an accepted step needs nothing more; returns and certain
+    rejections are decided without one), one per acceptance-deciding membership
+    test (the least any search structure can read), one per walk start (the
+    start's record), plus the 4-byte output entries."""
     return SECTOR * (c["gathers"] + c["searches"] + c["walks"]) + 4 * rows * walk_len
 
 
-def random_sector_peak(dev, gib=16, reads=1 << 31):
-    """Calibrated random-sector roofline: useful GB/s of independent random
-    32-byte sector reads over a buffer much larger than L2 (grape_sector_probe)."""
+def model_bytes(c: dict, weighted: bool) -> int:
+    """The per-step byte model of the method: every transition reads the
+    32-byte sector of the next node's offsets and writes its 4-byte output
+    entry (36 B); every proposal reads its 32-byte candidate sector, plus a
+    32-byte weight sector on a weighted graph; every membership-search probe
+    reads one 32-byte sector.  36 + E (32 + 32 [weighted]) + 32 S per step,
+    with E proposals and S probes per step taken from the counting launch."""
+    return 36 * c["steps"] + SECTOR * (2 if weighted else 1) * c["trials"] + SECTOR * c["probes"]
+
+
+def random_sectors(c: dict) -> int:
+    """Independent random 32-byte sectors one launch reads: the proposal
+    entries read, the membership probes and the walk starts' records."""
+    return c["gathers"] + c["probes"] + c["walks"]
+
+
+PROBE_SHAPES = [(w, l) for w, ls in ((4, (8, 16, 32, 64)), (16, (8, 16, 32)), (32, (4, 8, 16)))
+                for l in ls]
+
+
+def random_sector_peak(dev, gib=16, reads=1 << 29, sweep=True):
+    """The random-sector ceiling: independent random 32-byte sector reads over
+    a buffer far larger than L2 (grape_sector_probe), timed with CUDA events
+    over a sweep of load width, loads in flight per thread, resident blocks
+    per SM and cache path.  Returns (best sectors/s, best shape, the sweep)."""
     from paper_2110_06196_gb300 import walk as W
     buf = torch.empty(gib << 28, dtype=torch.int32, device=dev)   # gib GiB
     buf.fill_(1)
-    W.sector_probe(buf, reads // 8, seed=1)                     # warm-up
-    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    shapes = []
+    if sweep:
+        for mode in (0, 1, 2):
+            for (w, l) in PROBE_SHAPES:
+                for bps in (2, 4, 8):
+                    shapes.append((mode, w, l, bps))
+    else:
+        shapes = [(0, 32, 8, 0)]
+    W.sector_probe(buf, reads // 4, seed=1)                         # warm-up
+    rows = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    n = W.sector_probe(buf, reads, seed=2)
-    e1.record()
-    torch.cuda.synchronize(dev)
-    s = e0.elapsed_time(e1) / 1e3
+    for (mode, w, l, bps) in shapes:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        n, res = W.sector_probe(buf, reads, seed=2, mode=mode, load_bytes=w, loads_in_flight=l,
+                                blocks_per_sm=bps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        rows.append({"mode": ["nc", "cg", "cs"][mode], "load_bytes": w, "loads_in_flight": l,
+                     "blocks_per_sm": res, "threads_per_sm": 256 * res,
+                     "sectors_per_s": n / ms * 1e3, "gbs": n * SECTOR / ms / 1e6})
     del buf
     torch.cuda.empty_cache()
-    return n * SECTOR / s / 1e9
+    best = max(rows, key=lambda r: r["sectors_per_s"])
+    return best["sectors_per_s"], best, rows
 
 
 def workload_desc(name, job):
@@ -260,15 +325,18 @@ def workload_desc(name, job):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (reported baseline; test infrastructure)
 # ---------------------------------------------------------------------------
-def oracle_rate(csr_np, job, seconds, starts=None):
+def oracle_rate(csr_np, job, seconds, starts=None, threads=None):
+    """The oracle as it stands (walks_parallel, one contiguous walk-id range per
+    thread; threads=1 is the plain single-threaded walker) on a random sample of
+    the job's walk ids sized to about `seconds` of work."""
     import oracle
     og = oracle.Graph(*csr_np)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     n = og.num_nodes if starts is None else len(starts)
     total = n * job.walks_per_node
     rng = np.random.default_rng(123)
     # calibrate on a small sample, then size the main sample to ~`seconds`
-    probe = 64 * threads
+    probe = 64 * threads if threads > 1 else 256
     b = int(rng.integers(0, max(1, total - probe)))
     t0 = time.perf_counter()
     rows = oracle.walks_parallel(og, starts, job.walk_len, job.walks_per_node, job.p, job.q,
@@ -288,43 +356,22 @@ def oracle_rate(csr_np, job, seconds, starts=None):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args, dist):
-    from paper_2110_06196_gb300 import BatchPlan, Graph, synth, walks, walks_host
-    from paper_2110_06196_gb300 import walk as W
-    from paper_2110_06196_gb300 import _lib
+def job_steps(degrees: torch.Tensor, job) -> int:
+    """Transitions of a whole-graph job on an undirected graph: a walk leaves
+    its start unless the start is isolated, and then never meets a dead end
+    (every node it reaches has the edge it came by), so each walk from a
+    non-isolated start takes walk_len - 1 transitions."""
+    return int((degrees > 0).sum()) * job.walks_per_node * (job.walk_len - 1)
 
-    torch.cuda.set_device(dist.local)
-    dev = torch.device("cuda", dist.local)
-    spec = synth.WORKLOADS[args.workload]
-    job = spec["job"]
-    if args.walks_per_node > 0:
-        job = dataclasses.replace(job, walks_per_node=args.walks_per_node)
-    csr = synth.workload_graph(args.workload, device=dev)
-    g = Graph.from_csr(csr, validate=False, device=dev)
+
+def time_launches(g, job, n, b, rows, wpn_total, dev, steps, warmup, dist=None, clocks=None):
+    """grape_walks_range over walk ids [b, b + rows) of the job: `warmup`
+    untimed launches, one counting launch (work counters), then `steps` timed
+    launches with a CUDA event after each on the launching stream, bracketed by
+    a barrier and a device synchronisation.  Returns the per-launch times, the
+    steps of one launch, the counters and the clock record."""
+    from paper_2110_06196_gb300 import _lib
     lib = g._lib
-    n = csr.num_nodes
-    num_entries = csr.num_entries
-    # the library holds its own copy of the graph: release the generator's
-    # tensors (kept on the host only where the CPU baseline needs them)
-    want_cpu = (not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1)
-    want_batched = (not args.no_batched and dist.rank == 0 and args.workload == "rmat20w")
-    csr_host = csr.numpy() if want_cpu else None
-    ef_stores = {}
-    if args.ef_quanta and dist.world == 1:
-        from paper_2110_06196_gb300 import EFGraph
-        for qs in args.ef_quanta.split(","):
-            t0 = time.perf_counter()
-            ef_stores[int(qs)] = (EFGraph.from_csr(csr, quantum=int(qs), validate=False, device=dev),
-                                  time.perf_counter() - t0)
-    if not want_batched:
-        del csr
-        csr = None
-    torch.cuda.empty_cache()
-    per_rank = n * job.walks_per_node                    # weak scaling: fixed work per GPU
-    total = per_rank * dist.world
-    wpn_total = job.walks_per_node * dist.world
-    b, e = shard(total, dist.world, dist.rank)
-    rows = e - b
     out = torch.empty((rows, job.walk_len), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = ctypes.c_void_p(stream.cuda_stream)
@@ -335,139 +382,353 @@ def run_ours(args, dist):
                                      job.seed, b, rows, outp, sp)
         _lib.check(code, "grape_walks_range")
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(warmup):
         launch()
     torch.cuda.synchronize(dev)
     g.stream_status()
     steps_per_launch = count_steps(out)
-    # work counters for the byte accounting (one extra, untimed launch)
     g.counters(enable=True)
     launch()
     torch.cuda.synchronize(dev)
     cnt = g.counters()
     g.counters(enable=False)
-
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    ids = [x.strip() for x in vis.split(",") if x.strip()]
-    clocks = Clocks(ids[dist.local] if dist.local < len(ids) else str(dist.local))
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    dist.barrier()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize(dev)
-    clocks.start()
-    time.sleep(0.3)                          # let the sampler start
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)                      # let the sampler start
     evs[0].record(stream)
-    for k in range(args.steps):
+    for k in range(steps):
         launch()
         evs[k + 1].record(stream)
     torch.cuda.synchronize(dev)
-    dist.barrier()
-    clk = clocks.stop()
-    ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    elapsed = sum(ms) / 1e3
-    elapsed_max = dist.max(elapsed)
-    value = steps_per_launch * args.steps * dist.world / elapsed_max
-    launch_ms = sum(ms) / len(ms)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return ms, steps_per_launch, cnt, clk, out
 
-    ref_sig = row_signature(out) if ef_stores else None
-    approx = None
-    if args.suss_k > 0 and dist.world == 1:
-        from paper_2110_06196_gb300 import walks_approx
-        for _ in range(2):
-            walks_approx(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
-                         suss_k=args.suss_k, out=out)
-        torch.cuda.synchronize(dev)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(3):
-            walks_approx(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
-                         suss_k=args.suss_k, out=out)
-        a1.record(stream)
-        torch.cuda.synchronize(dev)
-        ams = a0.elapsed_time(a1) / 3
-        asteps = count_steps(out)
-        approx = {"suss_k": args.suss_k, "ms_per_launch": ams, "steps_per_s": asteps / ams * 1e3,
-                  "exact_ms_per_launch": None}
-    del out
-    torch.cuda.empty_cache()
-    # end to end through the host-buffer entry point: H2D starts, walks, D2H rows
-    starts_h = torch.arange(n, dtype=torch.int32).pin_memory()
-    shard_starts = None
-    e2e_rows = n * job.walks_per_node
-    out_h = torch.empty((e2e_rows, job.walk_len), dtype=torch.int32).pin_memory()
+
+def e2e_rate(g, job, n, steps_per_job, dist, k):
+    """The same job end to end through grape_walks_host, the call a user with
+    host buffers makes: the starts go in from pinned host memory and the rows
+    come back into pinned host memory inside every timed call.  One untimed
+    call, then k timed ones.  Returns (steps/s, H2D bytes, D2H bytes per call)."""
+    from paper_2110_06196_gb300 import _lib
+    lib = g._lib
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    rows = n * job.walks_per_node
+    starts_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    starts_h.copy_(torch.arange(n, dtype=torch.int32))
+    out_h = torch.empty((rows, job.walk_len), dtype=torch.int32, pin_memory=True)
     st_ptr = ctypes.c_void_p(starts_h.data_ptr())
     oh_ptr = ctypes.c_void_p(out_h.data_ptr())
 
-    def e2e_step():
+    def call():
         code = lib.grape_walks_host(g.handle, st_ptr, n, job.walk_len, job.walks_per_node, job.p,
                                     job.q, job.seed + dist.rank, oh_ptr, sp)
         _lib.check(code, "grape_walks_host")
 
-    e2e_step()
-    e2e_steps = count_steps(torch.from_numpy(out_h.numpy()))
+    call()
     dist.barrier()
     t0 = time.perf_counter()
-    k_e2e = max(1, min(args.steps, 5))
-    for _ in range(k_e2e):
-        e2e_step()
-    e2e_dt = dist.max(time.perf_counter() - t0)
-    e2e_value = e2e_steps * k_e2e * dist.world / e2e_dt
-    del shard_starts, out_h, starts_h
-    ef_res = [bench_ef(st, build_s, job, n, dev, ref_sig, rows, g.info()["device_bytes"])
-              for st, build_s in ef_stores.values()]
-    for st, _ in ef_stores.values():
-        st.close()
+    for _ in range(k):
+        call()
+    dt = dist.max(time.perf_counter() - t0)
+    h2d, d2h = 4 * n, 4 * rows * job.walk_len
+    del starts_h, out_h
+    from paper_2110_06196_gb300 import walk as W
+    W.trim_scratch(0)                        # the call's pooled device scratch goes back
+    return steps_per_job * k * dist.world / dt, h2d, d2h
 
+
+def roofline(cnt, rows, walk_len, weighted, launch_ms, peak, peak_kind, traffic, rs):
+    """The dominant kernel against the measured copy peak, under the method's
+    per-step byte model and under this engine's sector-granular minimum, and
+    its random sectors against the measured random-sector ceiling `rs`
+    (sectors/s, or None)."""
+    s = launch_ms / 1e3
+    mb = model_bytes(cnt, weighted)
+    sm = sector_minimal_bytes(cnt, rows, walk_len)
+    rsec = random_sectors(cnt)
+    steps = max(1, cnt["steps"])
+    r = {"bound": "hbm", "achieved": mb / s / 1e9, "peak": peak, "unit": "GB/s",
+         "frac": mb / s / 1e9 / peak, "traffic": traffic,
+         "peak_kind": f"{peak_kind} copy bandwidth",
+         "bytes_model": "per step 36 B (offsets sector + output entry) + per proposal 32 B "
+                        "(+32 B weights) + 32 B per search probe",
+         "algorithmic_bytes_per_launch": mb, "bytes_per_step": mb / steps,
+         "sector_minimal": {"bytes_per_launch": sm, "bytes_per_step": sm / steps,
+                            "achieved": sm / s / 1e9, "frac": sm / s / 1e9 / peak},
+         "random_sectors_per_launch": rsec, "random_sectors_per_step": rsec / steps,
+         "random_sectors_per_s": rsec / s}
+    if rs:
+        r["random_sector_peak_sectors_per_s"] = rs
+        r["random_sector_peak_gbs"] = rs * SECTOR / 1e9
+        r["frac_of_random_sector_peak"] = rsec / s / rs
+    if traffic:
+        r["traffic_over_model_bytes"] = traffic / mb
+    return r
+
+
+def counters_view(cnt):
+    st = max(1, cnt["steps"])
+    return {"trials_per_step": cnt["trials"] / st, "gathers_per_step": cnt["gathers"] / st,
+            "filtered_per_step": cnt["filtered"] / st,
+            "searches_per_step": cnt["searches"] / st,
+            "probes_per_search": cnt["probes"] / max(1, cnt["searches"]),
+            "probes_per_step": cnt["probes"] / st, "fallbacks": cnt["fallbacks"]}
+
+
+def run_ours(args, dist):
+    from paper_2110_06196_gb300 import Graph, synth
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    solo = dist.rank == 0 and dist.world == 1
+    spec = synth.WORKLOADS[args.workload]
+    job = spec["job"]
+    if args.walks_per_node > 0:
+        job = dataclasses.replace(job, walks_per_node=args.walks_per_node)
+    log(f"building {args.workload}")
+    csr = synth.workload_graph(args.workload, device=dev)
+    g = Graph.from_csr(csr, validate=False, device=dev)
+    n = csr.num_nodes
+    num_entries = csr.num_entries
+    degrees = csr.degrees()
+    log("graph resident; timing walks")
+    want_cpu = not args.no_cpu_baseline and solo
+    csr_host = csr.numpy() if want_cpu else None
+    # the library holds its own copy of the graph
+    del csr
+    torch.cuda.empty_cache()
+    per_rank = n * job.walks_per_node                    # weak scaling: fixed work per GPU
+    total = per_rank * dist.world
+    wpn_total = job.walks_per_node * dist.world
+    b, e = shard(total, dist.world, dist.rank)
+    rows = e - b
+    warm = max(args.warmup, 3)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x.strip() for x in vis.split(",") if x.strip()]
+    clocks = Clocks(ids[dist.local] if dist.local < len(ids) else str(dist.local))
+    ms, steps_per_launch, cnt, clk, out = time_launches(g, job, n, b, rows, wpn_total, dev,
+                                                        args.steps, warm, dist, clocks)
+    elapsed_max = dist.max(sum(ms) / 1e3)
+    value = steps_per_launch * args.steps * dist.world / elapsed_max
+    launch_ms = sum(ms) / len(ms)
+    ref_sig = row_signature(out) if (args.ef_quanta and solo) else None
+    hub = None
+    if solo and not args.no_hub_ab:
+        log("membership-search schedules")
+        hub = bench_hub_schedules(g, job, n, rows, out, dev, launch_ms)
+    approx = None
+    if args.suss_k > 0 and solo:
+        approx = bench_approx(g, job, out, dev, args.suss_k, launch_ms)
+    del out
+    torch.cuda.empty_cache()
+    if spec["kind"] != "er" and dist.world == 1:
+        assert steps_per_launch == job_steps(degrees, job), "rows do not have the job's steps"
+    log(f"walks {launch_ms:.1f} ms per launch; end to end")
+    e2e_value, h2d, d2h = e2e_rate(g, job, n, steps_per_launch, dist, max(1, min(args.steps, 5)))
+    log(f"end to end {e2e_value / 1e9:.2f} G steps/s; random-sector probe")
     peak, peak_kind = measured_peaks()
-    alg = algorithmic_bytes(cnt, rows, job.walk_len)
-    achieved = alg / (launch_ms / 1e3) / 1e9
-    traffic = profiled_traffic(args.workload)
-    rs_peak = random_sector_peak(dev)
+    rs, rs_best, rs_sweep = (None, None, None)
+    if dist.rank == 0:
+        rs, rs_best, rs_sweep = random_sector_peak(dev, sweep=not args.no_probe_sweep)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": launch_ms,
+        "steps": args.steps, "warmup": warm, "ms_per_step": launch_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded R-MAT / Erdos-Renyi stand-ins for the paper's graphs)",
-        "config": {"workload": workload_desc(args.workload, job), "walks_per_gpu": rows,
-                   "walk_len": job.walk_len, "steps_per_launch": steps_per_launch,
-                   "graph_entries": num_entries,
-                   "l2": "inputs larger than L2 (graph arrays and output rows > 129 MB)",
-                   "parallelism": f"shards{dist.world}"},
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * e2e_rows * job.walk_len},
+        "config": config_of(args.workload, job, rows, steps_per_launch, num_entries, dist.world),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "call": "grape_walks_host (pinned host starts and rows)",
+                "frac_of_device_value": e2e_value / value},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": f"{peak_kind} copy bandwidth",
-                     "algorithmic_bytes_per_launch": alg,
-                     "random_sector_peak": rs_peak,
-                     "frac_of_random_sector_peak": achieved / rs_peak},
-        "counters": {"trials_per_step": cnt["trials"] / max(1, cnt["steps"]),
-                     "gathers_per_step": cnt["gathers"] / max(1, cnt["steps"]),
-                     "filtered_per_step": cnt["filtered"] / max(1, cnt["steps"]),
-                     "searches_per_step": cnt["searches"] / max(1, cnt["steps"]),
-                     "probes_per_search": cnt["probes"] / max(1, cnt["searches"]),
-                     "fallbacks": cnt["fallbacks"]},
+        "roofline": roofline(cnt, rows, job.walk_len, spec.get("weighted", False), launch_ms,
+                             peak, peak_kind, profiled_traffic(args.workload), rs),
+        "counters": counters_view(cnt),
         "clocks": clk,
     }
-    if ef_res:
-        for r in ef_res:
-            r["frac_of_random_sector_peak"] = r["achieved_gbs"] / rs_peak
-        res["elias_fano"] = ef_res
-    if want_batched:
-        res["batched"] = bench_batched(g, csr, dev)
+    if rs_sweep:
+        res["random_sector_probe"] = {"best": rs_best, "sweep": rs_sweep,
+                                      "buffer": "16 GiB, 2^29 reads per shape"}
     if approx is not None:
-        approx["exact_ms_per_launch"] = launch_ms
         res["approx"] = approx
-    if want_batched and not args.no_contexts:
-        res["contexts"] = bench_contexts(g, job, n, dev, peak)
-    if want_batched and not args.no_specialisations:
-        res["specialisations"] = bench_specialisations(g, csr, job, n, dev)
-    if want_batched and not args.no_cumsum:
-        res["cumsum_sampler"] = bench_cumsum(g, job, n, dev, walks_n=args.cumsum_walks)
+    if hub is not None:
+        res["hub_schedule"] = hub
+    if ref_sig is not None and args.ef_quanta:
+        log("Elias-Fano stores")
+        res["elias_fano"] = bench_ef_stores(args, g, job, n, dev, ref_sig, rows, rs)
     if want_cpu:
+        log("CPU oracle")
         rate, cores, sample = oracle_rate(csr_host, job, args.cpu_seconds)
+        rate1, _, sample1 = oracle_rate(csr_host, job, args.cpu_single_seconds, threads=1)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample,
+                               "single_thread": {"value": rate1, "cores": 1, "sample": sample1}}
+        del csr_host
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    if solo and args.extras_workload:
+        log(f"{args.extras_workload} legs")
+        res[args.extras_workload] = extras(args, dev, peak, peak_kind, rs)
+    if solo and not args.no_serve:
+        log("serving")
+        res["served"] = bench_serve(args, dev)
+    log("done")
+    return res
+
+
+def config_of(workload, job, rows, steps_per_launch, num_entries, world):
+    return {"workload": workload_desc(workload, job), "walks_per_gpu": rows,
+            "walk_len": job.walk_len, "steps_per_launch": steps_per_launch,
+            "graph_entries": num_entries,
+            "l2": "inputs larger than L2 (graph arrays and output rows > 129 MB)",
+            "parallelism": f"shards{world}"}
+
+
+def bench_hub_schedules(g, job, n, rows, out, dev, plain_ms, reps=3):
+    """The headline job under each membership-search schedule (the graph's
+    tuning knobs): sector pivots from a list length on, the same with an L2
+    persisting window over the pivots, and warp-cooperative narrowing of long
+    lists.  Launch time (CUDA events), probes per step (counting launch), and
+    the rows' signature against the plain schedule's."""
+    INT = 0x7fffffff
+    base = g.get_tuning().as_dict()
+    stream = torch.cuda.current_stream(dev)
+    ref = row_signature(out)
+    res = [{"schedule": "per-lane interpolation (default)", "ms_per_launch": plain_ms}]
+    variants = [("sector pivots, lists >= 512", dict(pivot_min=512)),
+                ("sector pivots, lists >= 128", dict(pivot_min=128)),
+                ("sector pivots >= 128 + 96 MB L2 persisting window on them",
+                 dict(pivot_min=128, l2_persist_mb=96)),
+                ("warp-cooperative narrowing, lists > 8192", dict(warp_search_min=8192)),
+                ("warp-cooperative narrowing, lists > 1024", dict(warp_search_min=1024))]
+    for name, kw in variants:
+        t = dict(base)
+        t.update(kw)
+        g.set_tuning(**t)
+        walks_into(g, job, n, rows, out)
+        torch.cuda.synchronize(dev)
+        same = row_signature(out) == ref
+        g.counters(enable=True)
+        walks_into(g, job, n, rows, out)
+        torch.cuda.synchronize(dev)
+        c = g.counters()
+        g.counters(enable=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            walks_into(g, job, n, rows, out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st = max(1, c["steps"])
+        res.append({"schedule": name, "tuning": kw, "ms_per_launch": e0.elapsed_time(e1) / reps,
+                    "rows_equal_default": same, "probes_per_step": c["probes"] / st,
+                    "pivot_probes_per_step": c["pivot_probes"] / st})
+    base.update(l2_persist_mb=0)
+    g.set_tuning(**base)
+    return res
+
+
+def walks_into(g, job, n, rows, out):
+    from paper_2110_06196_gb300 import _lib
+    code = g._lib.grape_walks_range(g.handle, None, n, job.walk_len, job.walks_per_node, job.p,
+                                    job.q, job.seed, 0, rows, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _lib.check(code, "grape_walks_range")
+
+
+def bench_approx(g, job, out, dev, suss_k, exact_ms):
+    """The workload's approximated walks (SUSS sub-samples of k neighbours)."""
+    from paper_2110_06196_gb300 import walks_approx
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        walks_approx(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
+                     suss_k=suss_k, out=out)
+    torch.cuda.synchronize(dev)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(3):
+        walks_approx(g, None, job.walk_len, job.walks_per_node, job.p, job.q, job.seed,
+                     suss_k=suss_k, out=out)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    ams = a0.elapsed_time(a1) / 3
+    return {"suss_k": suss_k, "ms_per_launch": ams, "steps_per_s": count_steps(out) / ams * 1e3,
+            "exact_ms_per_launch": exact_ms}
+
+
+def bench_ef_stores(args, g, job, n, dev, ref_sig, rows, rs):
+    """The headline job over the Elias-Fano store at each index quantum."""
+    from paper_2110_06196_gb300 import EFGraph, synth
+    csr = synth.workload_graph(args.workload, device=dev)
+    res = []
+    for qs in args.ef_quanta.split(","):
+        t0 = time.perf_counter()
+        st = EFGraph.from_csr(csr, quantum=int(qs), validate=False, device=dev)
+        build_s = time.perf_counter() - t0
+        r = bench_ef(st, build_s, job, n, dev, ref_sig, rows, g.info()["device_bytes"])
+        if rs:
+            r["frac_of_random_sector_peak"] = r["sectors_per_s"] / rs
+        st.close()
+        res.append(r)
+    del csr
+    torch.cuda.empty_cache()
+    return res
+
+
+def extras(args, dev, peak, peak_kind, rs):
+    """The weighted R-MAT scale-20 job (per call and end to end) and the legs
+    that run on its graph: batched requests, context windows, the eight
+    specialisations, the paper's cumulative-sum sampler."""
+    from paper_2110_06196_gb300 import Graph, synth
+
+    class _Solo:
+        world, rank = 1, 0
+
+        def barrier(self):
+            pass
+
+        def max(self, x):
+            return x
+
+    wl = args.extras_workload
+    spec = synth.WORKLOADS[wl]
+    job = spec["job"]
+    csr = synth.workload_graph(wl, device=dev)
+    g = Graph.from_csr(csr, validate=False, device=dev)
+    n = csr.num_nodes
+    rows = n * job.walks_per_node
+    ms, steps, cnt, _, out = time_launches(g, job, n, 0, rows, job.walks_per_node, dev, 10, 3)
+    launch_ms = sum(ms) / len(ms)
+    del out
+    torch.cuda.empty_cache()
+    e2e_value, _, _ = e2e_rate(g, job, n, steps, _Solo(), 3)
+    res = {"workload": workload_desc(wl, job), "value": steps / (launch_ms / 1e3),
+           "ms_per_launch": launch_ms, "steps_per_launch": steps,
+           "e2e": {"value": e2e_value, "unit": UNIT},
+           "roofline": roofline(cnt, rows, job.walk_len, spec.get("weighted", False), launch_ms,
+                                peak, peak_kind, profiled_traffic(wl), rs),
+           "counters": counters_view(cnt)}
+    log("batched")
+    if not args.no_batched:
+        res["batched"] = bench_batched(g, csr, dev)
+    log("contexts, specialisations, cumulative sums")
+    if not args.no_contexts:
+        res["contexts"] = bench_contexts(g, job, n, dev, peak)
+    if not args.no_specialisations:
+        res["specialisations"] = bench_specialisations(g, csr, job, n, dev)
+    if not args.no_cumsum:
+        res["cumsum_sampler"] = bench_cumsum(g, job, n, dev, walks_n=args.cumsum_walks)
+    g.close()
+    del g, csr
+    torch.cuda.empty_cache()
     return res
 
 
@@ -532,7 +793,8 @@ def bench_ef(store, build_s, job, n, dev, ref_sig, rows, csr_bytes, reps=3):
             "sectors_per_step": c["sectors"] / max(1, c["steps"]),
             "membership_tests_per_step": c["membership_tests"] / max(1, c["steps"]),
             "trials_per_step": c["trials"] / max(1, c["steps"]),
-            "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / ms / 1e6}
+            "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / ms / 1e6,
+            "sectors_per_s": c["sectors"] / ms * 1e3}
 
 
 def bench_specialisations(g, csr, job, n, dev, walks_n=1 << 20, reps=3):
@@ -699,63 +961,109 @@ def bench_batched(g, csr, dev):
 
 
 # ---------------------------------------------------------------------------
-# serving run
+# serving
 # ---------------------------------------------------------------------------
-def run_serve(args, dist):
-    from paper_2110_06196_gb300 import Graph, Server, synth
-    torch.cuda.set_device(dist.local)
-    dev = torch.device("cuda", dist.local)
+class PinnedPool:
+    """Reusable pinned host buffers for served rows: a request takes the
+    smallest free buffer that holds its rows and gives it back once its rows
+    are counted, so a long arrival stream holds only what is in flight."""
+
+    def __init__(self):
+        self.free = []
+
+    def take(self, elems):
+        fit = [j for j, b in enumerate(self.free) if b.numel() >= elems]
+        if fit:
+            j = min(fit, key=lambda k: self.free[k].numel())
+            return self.free.pop(j)
+        size = 1 << max(20, (elems - 1).bit_length())
+        return torch.empty(size, dtype=torch.int32, pin_memory=True)
+
+    def give(self, b):
+        self.free.append(b)
+
+
+def bench_serve(args, dev):
+    """Continuous batching on the resident R-MAT scale-26 graph: Poisson
+    arrivals at each rate (args.serve_requests requests, or args.serve_max_s
+    seconds of arrivals), latency from submit to rows in host memory, and the
+    server's device-counted transitions per second of wall time.  Then a
+    saturation run: args.serve_saturation requests submitted at once against
+    the same requests as one grape_walks_host launch each, rows compared."""
+    import threading
+    from paper_2110_06196_gb300 import Graph, Server, synth, walks_host
     csr = synth.workload_graph(args.serve_graph, device=dev)
     g = Graph.from_csr(csr, validate=False, device=dev)
+    n = g.num_nodes
+    deg = csr.degrees().cpu().numpy()
     del csr
     torch.cuda.empty_cache()
-    n = g.num_nodes
+    pool = PinnedPool()
     results = []
     for ri, rate in enumerate(float(x) for x in args.serve_rates.split(",")):
-        mix = synth.request_mix(n, args.serve_requests, gen_seed=77 + ri, max_starts=1_000_000,
-                                len_lo=20, len_hi=120, first_seed=10_000 * ri)
+        count = int(min(args.serve_requests, max(1, rate * args.serve_max_s)))
+        mix = synth.request_mix(n, count, gen_seed=77 + ri, max_starts=1_000_000, len_lo=20,
+                                len_hi=120, first_seed=10_000 * ri)
         arrivals = synth.poisson_arrivals(rate, len(mix), seed=5 + ri)
+        log(f"serving {len(mix)} requests at {rate:g}/s")
         srv = Server(g, output_cap_bytes=40 << 30, max_inflight=4096, chunk_walks=0,
                      max_chunks=1 << 24, idle_exit_us=2000)
-        outs = [torch.empty((len(r.starts), r.walk_len), dtype=torch.int32).pin_memory()
-                for r in mix]
+        bufs = {}
         lat = []
-        done_steps = 0
-        import threading
-        stop = threading.Event()
+        mu = threading.Lock()
+        checked = [0, 0]                        # requests checked, of which wrong
 
         def collect():
-            nonlocal done_steps
             while len(lat) < len(mix):
                 t, l, rows = srv.wait_any(timeout_ms=600_000)
+                with mu:
+                    j, buf = bufs.pop(t)
                 lat.append(l)
-                r = rows
-                done_steps += int((r >= 0).sum()) - int((r[:, 0] >= 0).sum())
+                if j % 50 == 0:                 # rows follow the job's step count
+                    r = mix[j]
+                    want = int((deg[r.starts] > 0).sum()) * (r.walk_len - 1)
+                    got = int((rows >= 0).sum()) - int((rows[:, 0] >= 0).sum())
+                    checked[0] += 1
+                    checked[1] += int(got != want)
+                pool.give(buf)
 
         th = threading.Thread(target=collect)
         th.start()
+        st0 = 0
         t0 = time.perf_counter()
         for j, r in enumerate(mix):
             delay = arrivals[j] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            srv.submit(r.starts, r.walk_len, r.p, r.q, r.seed, out=outs[j])
+            elems = len(r.starts) * r.walk_len
+            with mu:
+                buf = pool.take(elems)
+            out = buf[:elems].view(len(r.starts), r.walk_len)
+            t = srv.submit(r.starts, r.walk_len, r.p, r.q, r.seed, out=out)
+            with mu:
+                bufs[t] = (j, buf)
         th.join()
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
         lat_ms = np.array(lat) * 1e3
-        results.append({"rate_req_s": rate, "requests": len(mix), "steps_per_s": done_steps / wall,
+        offered = sum(int((deg[r.starts] > 0).sum()) * (r.walk_len - 1) for r in mix)
+        results.append({"rate_req_s": rate, "requests": len(mix), "wall_s": wall,
+                        "steps_per_s": (st["steps"] - st0) / wall,
+                        "offered_steps_per_s": offered / arrivals[-1],
                         "p50_ms": float(np.percentile(lat_ms, 50)),
                         "p99_ms": float(np.percentile(lat_ms, 99)),
-                        "max_ms": float(lat_ms.max()), "wall_s": wall,
-                        "kernel_launches": st["kernel_launches"]})
-    # Saturation: every request of one mix at once, through the server, then
-    # the same requests as one grape_walks_host launch each, one after another.
-    from paper_2110_06196_gb300 import walks_host
-    mix = synth.request_mix(n, args.serve_requests, gen_seed=99, max_starts=1_000_000,
+                        "max_ms": float(lat_ms.max()),
+                        "kernel_launches": st["kernel_launches"],
+                        "kernel_timeouts": st["kernel_timeouts"],
+                        "requests_step_checked": checked[0],
+                        "requests_step_mismatch": checked[1]})
+    # Saturation: every request of one mix at once through the server, then the
+    # same requests as one grape_walks_host launch each, one after another.
+    mix = synth.request_mix(n, args.serve_saturation, gen_seed=99, max_starts=1_000_000,
                             len_lo=20, len_hi=120, first_seed=90_000)
-    outs = [torch.empty((len(r.starts), r.walk_len), dtype=torch.int32).pin_memory() for r in mix]
+    outs = [torch.empty((len(r.starts), r.walk_len), dtype=torch.int32, pin_memory=True)
+            for r in mix]
     srv = Server(g, output_cap_bytes=40 << 30, max_inflight=4096, chunk_walks=0,
                  max_chunks=1 << 24, idle_exit_us=2000)
     t0 = time.perf_counter()
@@ -765,9 +1073,9 @@ def run_serve(args, dist):
         _, l, _ = srv.wait_any(timeout_ms=600_000)
         lat.append(l)
     t_srv = time.perf_counter() - t0
+    steps = srv.stats()["steps"]
     srv.close()
-    steps = sum(int((o >= 0).sum()) - int((o[:, 0] >= 0).sum()) for o in outs)
-    seq_outs = [torch.empty_like(o).pin_memory() for o in outs]
+    seq_outs = [torch.empty_like(o, pin_memory=True) for o in outs]
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for r, o in zip(mix, seq_outs):
@@ -775,45 +1083,71 @@ def run_serve(args, dist):
     t_seq = time.perf_counter() - t0
     same = all(torch.equal(a, b) for a, b in zip(outs, seq_outs))
     lat_ms = np.array(lat) * 1e3
-    saturation = {"requests": len(mix), "steps": steps, "served_steps_per_s": steps / t_srv,
-                  "sequential_steps_per_s": steps / t_seq,
-                  "served_vs_one_launch_per_request": t_seq / t_srv,
-                  "p50_ms": float(np.percentile(lat_ms, 50)),
-                  "p99_ms": float(np.percentile(lat_ms, 99)),
-                  "rows_identical_to_one_launch_per_request": bool(same)}
-    best = max(max(r["steps_per_s"] for r in results), saturation["served_steps_per_s"])
-    return {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": 1, "steps": len(results),
-            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"serving on {args.serve_graph}: Poisson arrivals, starts "
-                                   "log-uniform [1,1e6], len U[20,120], p,q in {0.25..4}, "
-                                   "admission under a 40 GB output cap"},
-            "serving": results, "saturation": saturation}
+    g.close()
+    del g, outs, seq_outs, pool
+    torch.cuda.empty_cache()
+    return {"graph": f"{args.serve_graph}: " + workload_graph_desc(args.serve_graph),
+            "mix": "starts log-uniform [1, 1e6] (uniform ids), len U[20, 120], p, q in "
+                   "{0.25, 0.5, 1, 2, 4}; 40 GB output cap; latency = submit to rows in host memory",
+            "rates": results,
+            "saturation": {"requests": len(mix), "steps": steps,
+                           "served_steps_per_s": steps / t_srv,
+                           "sequential_steps_per_s": steps / t_seq,
+                           "served_vs_one_launch_per_request": t_seq / t_srv,
+                           "p50_ms": float(np.percentile(lat_ms, 50)),
+                           "p99_ms": float(np.percentile(lat_ms, 99)),
+                           "rows_identical_to_one_launch_per_request": bool(same)}}
+
+
+def workload_graph_desc(name):
+    from paper_2110_06196_gb300 import synth
+    s = synth.WORKLOADS[name]
+    return (f"R-MAT(a=.57,b=.19,c=.19) scale {s['scale']}, {s['m']} undirected edges"
+            f"{', fp32 weights U[0.1,1]' if s['weighted'] else ', unweighted'} (seed {s['seed']})")
 
 
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
 def run_reference(args, dist):
+    """The oracle as it stands on the host cores, on the headline job: each
+    step times a bounded random sample of the job's walk ids.  Its `config` is
+    the GPU arm's (same workload, rows, steps per launch, graph), so the two
+    lines describe the same job; the sample is stated in `sample`."""
     if dist.rank != 0:
         return None
     from paper_2110_06196_gb300 import synth
     job = synth.WORKLOADS[args.workload]["job"]
-    csr = synth.workload_graph(args.workload, device="cpu")
+    if args.walks_per_node > 0:
+        job = dataclasses.replace(job, walks_per_node=args.walks_per_node)
+    # input synthesis only (no walk arithmetic): on the GPU when there is one,
+    # bit-identical to the CPU construction
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    csr = synth.workload_graph(args.workload, device=gen_dev)
+    degrees = csr.degrees()
     csr_np = csr.numpy()
+    n = csr.num_nodes
+    num_entries = csr.num_entries
+    del csr
+    if gen_dev == "cuda":
+        torch.cuda.empty_cache()
+    rows = n * job.walks_per_node
     seconds = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    rates, sample = [], None
+    rates, sample, cores = [], None, os.cpu_count()
     for k in range(args.warmup + args.steps):
         rate, cores, sample = oracle_rate(csr_np, job, seconds)
         if k >= args.warmup:
             rates.append(rate)
     value = statistics.median(rates)
-    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload, job)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": sample},
+    steps = job_steps(degrees, job)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded R-MAT / Erdos-Renyi stand-ins for the paper's graphs)",
+            "config": config_of(args.workload, job, rows, steps, num_entries, dist.world),
+            "sample": f"each step: {sample} on {cores} host threads",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -824,8 +1158,6 @@ def main():
     try:
         if args.impl == "reference":
             res = run_reference(args, dist)
-        elif args.mode == "serve":
-            res = run_serve(args, dist) if dist.rank == 0 else None
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:

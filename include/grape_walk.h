@@ -94,7 +94,8 @@ typedef struct grape_graph grape_graph_t;
  *       caller keeps ownership; they may be freed once `stream` has reached
  *       this call's work (the copies are enqueued on it).
  *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62].  The graph holds
- *   16 * num_nodes + 36 * num_entries bytes: node records, sorted rows, and
+ *   16 * num_nodes + 36.5 * num_entries bytes: node records, sorted rows, their
+ *   sector pivots (the first id of every aligned 32-byte sector), and
  *   per CSR entry one 32-byte proposal entry that carries the target's degree,
  *   row offset and largest row weight, the weight, and the position of the
  *   row's node in the target's row (unweighted graphs: a 96-bit filter of the
@@ -148,6 +149,17 @@ typedef struct grape_tuning {
     int32_t l2_fetch_bytes;   /* 0: leave the L2 fetch granularity as it is; 32, 64 or 128: set
                                  it (cudaLimitMaxL2FetchGranularity, a per-context limit) when
                                  this tuning is applied */
+    int32_t pivot_min;        /* membership searches over lists of at least this many entries
+                                 first search the list's sector pivots (the first id of every
+                                 aligned 32-byte sector of the sorted rows, held beside them),
+                                 which leaves one sector of the list to read; INT32_MAX: never */
+    int32_t warp_search_min;  /* membership searches over lists of more than this many entries
+                                 are first narrowed by the whole warp, 32 probes at once, one
+                                 lane's search at a time; INT32_MAX (default): never */
+    int32_t l2_persist_mb;    /* 0: none; else ask the L2 to keep up to this many MB of the
+                                 sector pivots resident (a persisting access-policy window on
+                                 each walk launch; cudaLimitPersistingL2CacheSize, a per-context
+                                 limit, is raised to it when this tuning is applied) */
     int32_t pad;
 } grape_tuning_t;
 
@@ -237,6 +249,13 @@ grape_status_t grape_walks_host(const grape_graph_t* graph, const int32_t* start
                                 double p, double q, uint64_t seed, int32_t* out,
                                 grape_stream_t stream);
 
+/*
+ * Give back device scratch that grape_walks_host and grape_walk_contexts keep
+ * for reuse in the current device's default stream-ordered memory pool, down
+ * to keep_bytes (>= 0).  Synchronises the device first.
+ */
+grape_status_t grape_trim_scratch(int64_t keep_bytes);
+
 /* ------------------------------------------------------------------------ */
 /* Context windows (SkipGram / CBOW input)                                   */
 /* ------------------------------------------------------------------------ */
@@ -320,25 +339,31 @@ grape_status_t grape_walks_batched(const grape_graph_t* graph,
  * grape_walks_batched: each request's rows are byte-identical.
  *   num_requests must be in [1, 4096]; larger batches return
  *   GRAPE_ERR_INVALID_ARG before anything is enqueued.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The first call on a device, with that device current, looks up the
+ *   array's device address (cudaGetSymbolAddress) and the kernel's occupancy;
+ *   make that first call before any stream capture.
  *   Every call, on every stream, shares the one array per device.  The queue
  *   head is cleared on each call; the rest keeps the last call's contents.
  *   Calls whose work overlaps on the GPU (two streams, or a second call
  *   before the first finished on another stream) race on it: order them on
  *   one stream or synchronise between them.
- *   No cudaMalloc, cudaFree or other allocating routine is called; the table
- *   is uploaded from the host stack in batches of 32 requests.
+ *   No cudaMalloc, cudaFree or other allocating routine is called.  The table
+ *   is written by small launches that each carry 32 requests as kernel
+ *   parameters, so no host buffer has to outlive the call.  The graph's
+ *   tuning (chunk_walks, block_threads, blocks_per_sm, trial_cap, search
+ *   policy) and its work counters apply as for grape_walks_batched.
  */
 grape_status_t grape_walks_batched_static(const grape_graph_t* graph,
                                           const grape_walk_request_t* requests,
                                           int32_t num_requests, grape_stream_t stream);
 
 /*
- * Autotune the batched path for this graph: times a grid of (chunk_walks,
- * shorter_min, interp_search) on the given requests with CUDA events, and stores the
- * fastest pair in the graph's tuning (also returned in *best when not NULL).
- * Writes into the requests' out buffers.  Synchronises `stream`.
+ * Autotune the batched path for this graph with CUDA events on the given
+ * requests, in two stages: first (chunk_walks, shorter_min, interp_search) over
+ * a grid, then, from the best of those, the hub thresholds (pivot_min,
+ * warp_search_min).  Stores the fastest in the graph's tuning (also returned in
+ * *best when not NULL).  Writes into the requests' out buffers.  Synchronises
+ * `stream`.
  */
 grape_status_t grape_autotune_batched(grape_graph_t* graph,
                                       const grape_walk_request_t* requests,
@@ -367,6 +392,7 @@ typedef struct grape_walk_counters {
     int64_t walks;        /* rows written */
     int64_t filtered;     /* membership tests settled by the neighbour filters of an
                              unweighted graph, without reading a row */
+    int64_t pivot_probes; /* of the probes, 32-byte sectors of the sector pivots */
 } grape_walk_counters_t;
 
 grape_status_t grape_counters_enable(grape_graph_t* graph, int32_t enable);
@@ -389,7 +415,9 @@ typedef struct grape_server_config {
     int64_t idle_exit_us;       /* the resident kernel is stopped once the server has had nothing
                                    in flight for this long (relaunched with the next request) */
     int32_t admit_timeout_ms;   /* submit waits this long for memory/slots, then GRAPE_ERR_BUSY */
-    int32_t pad;
+    int32_t kernel_wait_ms;     /* bound on the resident kernel's wait for work while no host
+                                   heartbeat arrives (the host beats several times within it);
+                                   0 = 2000 */
 } grape_server_config_t;
 
 typedef struct grape_server_stats {
@@ -397,7 +425,9 @@ typedef struct grape_server_stats {
     int64_t inflight;            /* admitted, not yet complete */
     int64_t bytes_reserved;      /* output arena bytes in use */
     int64_t kernel_launches;     /* resident-kernel launches so far */
-    int64_t steps;               /* transitions of completed requests (from row contents) */
+    int64_t steps;               /* transitions of completed requests (counted on the device) */
+    int64_t kernel_timeouts;     /* resident-kernel launches that ended because their bounded
+                                    wait ran out without a host heartbeat */
 } grape_server_stats_t;
 
 /*
@@ -410,8 +440,12 @@ typedef struct grape_server_stats {
  * picked up by the running kernel.  Finished rows are copied to the host on the
  * copy stream while the kernel keeps running.  The server stops the resident
  * kernel after idle_exit_us without work in flight (all its warps leave
- * together) and relaunches it with the next request; the kernel's own waits
- * are bounded (about two seconds of polling) should the host never stop it.
+ * together) and relaunches it with the next request.  The kernel's own waits
+ * are bounded should the host stop: a warp that has waited kernel_wait_ms
+ * without a host heartbeat raises bit 2 of the graph's status word (read by
+ * grape_stream_status as GRAPE_ERR_DEVICE) and leaves.  A kernel that ends that
+ * way is counted in stats.kernel_timeouts, requests it left unfinished fail
+ * with GRAPE_ERR_TIMEOUT, and the next request relaunches it.
  */
 grape_status_t grape_walk_server_create(const grape_graph_t* graph,
                                         const grape_server_config_t* config,
@@ -453,6 +487,15 @@ grape_status_t grape_walk_server_wait_any(grape_server_t* server, int64_t timeou
 grape_status_t grape_walk_server_cancel(grape_server_t* server, uint64_t ticket);
 
 grape_status_t grape_walk_server_stats(grape_server_t* server, grape_server_stats_t* stats);
+
+/*
+ * Host-side fault injection, for testing the bounded waits.
+ * GRAPE_FAULT_NO_HEARTBEAT stops the heartbeat that renews the resident
+ * kernel's wait, as a host that has stopped responding would; 0 restores it.
+ * Other bits return GRAPE_ERR_INVALID_ARG.
+ */
+#define GRAPE_FAULT_NO_HEARTBEAT 1u
+grape_status_t grape_walk_server_inject_fault(grape_server_t* server, uint32_t faults);
 
 /* Stop admitting, let admitted work finish (bounded), cancel the rest, free everything. */
 void grape_walk_server_destroy(grape_server_t* server);
@@ -603,16 +646,28 @@ grape_status_t grape_philox4x32_10(const uint32_t* ctr_key, int64_t n, uint32_t*
                                    grape_stream_t stream);
 
 /*
- * Random 32-byte-sector gather probe (HBM random-access calibration): each of
- * `n_reads` reads (rounded up to whole rounds of the grid) fetches one aligned
- * 32-byte sector of `buf` (device, `buf_bytes` long, 32-byte aligned) at a
- * position drawn by Philox from `seed`.  mode picks the load's cache path:
- * 0 read-only through L1 (ld.global.nc), 1 L2 only (ld.global.cg),
- * 2 streaming (ld.global.cs).  The XOR of what was read lands in *sink
- * (device uint32) so nothing is optimised away.
+ * Random 32-byte-sector gather probe: the ceiling of independent random
+ * sector reads on this device, the denominator the walk kernels' gathers are
+ * compared with.  Each read fetches one aligned 32-byte sector of `buf`
+ * (device, `buf_bytes` long, 32-byte aligned) at a position drawn by a hash of
+ * (seed, thread, read).  The launch shape is swept by the caller:
+ *   mode: the load's cache path: 0 read-only through L1 (ld.global.nc),
+ *       1 L2 only (ld.global.cg), 2 streaming (ld.global.cs);
+ *   load_bytes: 4, 16 or 32 (a 32-, 128- or 256-bit load at the sector start);
+ *   loads_in_flight: independent reads each thread issues before it waits:
+ *       8/16/32/64 for 4-byte loads, 8/16/32 for 16-byte loads, 4/8/16 for
+ *       32-byte loads; other pairs return GRAPE_ERR_INVALID_ARG;
+ *   blocks_per_sm: resident 256-thread blocks per SM, capped at what the
+ *       kernel's registers allow (0: that maximum).
+ * n_reads is rounded up to whole rounds of the grid.  The XOR of what was read
+ * lands in *sink (device uint32) so nothing is optimised away.
+ * *resident_blocks_per_sm and *reads_done (host, either may be NULL) receive
+ * the blocks per SM launched and the number of reads enqueued.
  */
 grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_reads,
-                                  uint64_t seed, int32_t mode, uint32_t* sink,
+                                  uint64_t seed, int32_t mode, int32_t load_bytes,
+                                  int32_t loads_in_flight, int32_t blocks_per_sm, uint32_t* sink,
+                                  int32_t* resident_blocks_per_sm, int64_t* reads_done,
                                   grape_stream_t stream);
 
 #ifdef __cplusplus

@@ -16,6 +16,7 @@ c_i32, c_i64, c_u32, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_int64, ctype
 
 GRAPE_UNDIRECTED = 1
 GRAPE_VALIDATE = 2
+GRAPE_FAULT_NO_HEARTBEAT = 1
 
 STATUS = {0: "GRAPE_OK", 1: "GRAPE_ERR_INVALID_ARG", 2: "GRAPE_ERR_INVALID_GRAPH",
           3: "GRAPE_ERR_NOMEM", 4: "GRAPE_ERR_CUDA", 5: "GRAPE_ERR_TIMEOUT", 6: "GRAPE_ERR_BUSY",
@@ -39,7 +40,8 @@ class GraphInfo(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("trial_cap", c_i64), ("shorter_min", c_i32), ("block_threads", c_i32),
                 ("blocks_per_sm", c_i32), ("chunk_walks", c_i32), ("interp_search", c_i32),
-                ("l2_fetch_bytes", c_i32), ("pad", c_i32)]
+                ("l2_fetch_bytes", c_i32), ("pivot_min", c_i32), ("warp_search_min", c_i32),
+                ("l2_persist_mb", c_i32), ("pad", c_i32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
@@ -54,7 +56,7 @@ class WalkRequest(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("steps", c_i64), ("trials", c_i64), ("gathers", c_i64), ("searches", c_i64),
                 ("probes", c_i64), ("fallbacks", c_i64), ("walks", c_i64),
-                ("filtered", c_i64)]
+                ("filtered", c_i64), ("pivot_probes", c_i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -63,13 +65,14 @@ class Counters(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("output_cap_bytes", c_i64), ("max_inflight", c_i32), ("chunk_walks", c_i32),
                 ("max_chunks", c_i64), ("idle_exit_us", c_i64), ("admit_timeout_ms", c_i32),
-                ("pad", c_i32)]
+                ("kernel_wait_ms", c_i32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", c_i64), ("admitted", c_i64), ("completed", c_i64),
                 ("cancelled", c_i64), ("rejected", c_i64), ("inflight", c_i64),
-                ("bytes_reserved", c_i64), ("kernel_launches", c_i64), ("steps", c_i64)]
+                ("bytes_reserved", c_i64), ("kernel_launches", c_i64), ("steps", c_i64),
+                ("kernel_timeouts", c_i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -109,6 +112,7 @@ SIGNATURES = {
                                   c_i64, c_vp, c_vp]),
     "grape_walks_host": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_vp,
                                  c_vp]),
+    "grape_trim_scratch": (c_i32, [c_i64]),
     "grape_batch_plan_create": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     "grape_batch_plan_launch": (c_i32, [c_vp, c_vp]),
     "grape_batch_plan_destroy": (None, [c_vp]),
@@ -124,9 +128,11 @@ SIGNATURES = {
     "grape_walk_server_wait_any": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "grape_walk_server_cancel": (c_i32, [c_vp, c_u64]),
     "grape_walk_server_stats": (c_i32, [c_vp, c_vp]),
+    "grape_walk_server_inject_fault": (c_i32, [c_vp, c_u32]),
     "grape_walk_server_destroy": (None, [c_vp]),
     "grape_philox4x32_10": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
-    "grape_sector_probe": (c_i32, [c_vp, c_i64, c_i64, c_u64, c_i32, c_vp, c_vp]),
+    "grape_sector_probe": (c_i32, [c_vp, c_i64, c_i64, c_u64, c_i32, c_i32, c_i32, c_i32, c_vp,
+                                   c_vp, c_vp, c_vp]),
     "grape_contexts_from_rows": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_vp, c_vp]),
     "grape_walks_approx": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_dbl, c_dbl, c_u64, c_i32,
                                    c_vp, c_vp]),

@@ -15,6 +15,7 @@
 //            sector, so an accepted step needs no further gather (edge-inlined
 //            records); rev tells the walk where its previous node sits in the
 //            next row, so proposals of the return class need no gather at all.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -183,10 +184,20 @@ __global__ void check_symmetry_kernel(const int4* __restrict__ rec, const int32_
     }
 }
 
+// piv[j] = dsts[8 j] for every aligned 32-byte sector j of the rows; the 8
+// entries of padding after the last hold INT_MAX.
+__global__ void build_pivots_kernel(const int32_t* __restrict__ dsts, long long sectors,
+                                    int32_t* __restrict__ piv) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < sectors + 8;
+         j += (long long)gridDim.x * blockDim.x)
+        piv[j] = j < sectors ? dsts[8 * j] : 0x7fffffff;
+}
+
 void free_graph(grape_graph* g) {
     if (!g) return;
     cudaFree(g->rec);
     cudaFree(g->dsts);
+    cudaFree(g->piv);
     cudaFree(g->fat);
     cudaFree(g->status);
     cudaFree(g->counters);
@@ -242,6 +253,8 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g->max_window, cudaDevAttrMaxAccessPolicyWindowSize, g->device);
     // dsts is padded by four entries so that a search probe, which reads the
     // aligned 16-byte block around a list position, never leaves the allocation.
     const size_t m_alloc = (size_t)num_entries + 8;
@@ -251,6 +264,8 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     if (e == cudaSuccess) e = cudaMalloc(&g->rec, sizeof(int4) * (size_t)num_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&g->dsts, sizeof(int32_t) * m_alloc);
     if (e == cudaSuccess) e = cudaMalloc(&g->fat, sizeof(int4) * fat_words);
+    const long long sectors = (num_entries + 7) / 8;
+    if (e == cudaSuccess) e = cudaMalloc(&g->piv, sizeof(int32_t) * (size_t)(sectors + 8));
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->counters, sizeof(unsigned long long) * grape::C_COUNT);
     if (e != cudaSuccess) {
@@ -258,7 +273,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
         return grape::cuda_status(e);
     }
     g->device_bytes = (int64_t)(sizeof(int4) * num_nodes + sizeof(int32_t) * m_alloc +
-                                sizeof(int4) * fat_words);
+                                sizeof(int4) * fat_words + sizeof(int32_t) * (sectors + 8));
     int* scratch = g->status;   // [0] status word, [1] bad flags, [2] max degree
     int host[4] = {0, 0, 0, 0};
     e = cudaMemsetAsync(g->status, 0, sizeof(int) * 4, stream);
@@ -283,6 +298,11 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
                             cudaMemcpyDeviceToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(g->dsts + num_entries, 0, sizeof(int32_t) * 8, stream);   // padding
+    if (e == cudaSuccess) {
+        build_pivots_kernel<<<grid_for(g->num_sms, sectors + 8, 256), 256, 0, stream>>>(
+            g->dsts, sectors, g->piv);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         build_rows_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
             offsets, dsts, weights, num_nodes, (flags & GRAPE_VALIDATE) ? 1 : 0, g->rec,
@@ -348,6 +368,9 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.chunk_walks = 64;
     g->tuning.interp_search = 1;
     g->tuning.l2_fetch_bytes = 0;
+    g->tuning.pivot_min = 0x7fffffff;
+    g->tuning.warp_search_min = 0x7fffffff;
+    g->tuning.l2_persist_mb = 0;
     *out = g;
     return GRAPE_OK;
 }
@@ -383,8 +406,20 @@ grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t)
         t->block_threads < 32 || t->block_threads > 256 || (t->block_threads % 32) ||
         t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->interp_search != 0 && t->interp_search != 1) ||
         (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&
-         t->l2_fetch_bytes != 128))
+         t->l2_fetch_bytes != 128) ||
+        t->pivot_min < 1 || t->warp_search_min < 0 || t->l2_persist_mb < 0)
         return GRAPE_ERR_INVALID_ARG;
+    if (t->l2_persist_mb > 0) {
+        // A per-context limit (released with the context): the L2 set-aside
+        // for persisting accesses, capped at what the device allows.
+        int dev = 0, cap = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&cap, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess)
+            return GRAPE_ERR_CUDA;
+        const size_t want = std::min((size_t)t->l2_persist_mb << 20, (size_t)cap);
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess)
+            return GRAPE_ERR_CUDA;
+    }
     if (t->l2_fetch_bytes != 0) {
         // A per-context limit (released with the context): how far the L2
         // widens a miss when it fetches from DRAM.
@@ -430,6 +465,7 @@ grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out)
     out->fallbacks = (int64_t)c[grape::C_FALLBACKS];
     out->walks = (int64_t)c[grape::C_WALKS];
     out->filtered = (int64_t)c[grape::C_FILTERED];
+    out->pivot_probes = (int64_t)c[grape::C_PIVOT_PROBES];
     return GRAPE_OK;
 }
 

@@ -17,11 +17,13 @@ struct grape_graph {
     bool undirected = false;
     int device = 0;
     int num_sms = 0;
+    int max_window = 0;           // cudaDevAttrMaxAccessPolicyWindowSize
     int4* rec = nullptr;          // NodeRec[n]
-    int32_t* dsts = nullptr;      // [m]
+    int32_t* dsts = nullptr;      // [m + 8]
+    int32_t* piv = nullptr;       // [ceil(m / 8) + 8] sector pivots: piv[j] = dsts[8 j]
     int4* fat = nullptr;          // [m] proposal entries (edge-inlined records)
     int* status = nullptr;        // device status word
-    unsigned long long* counters = nullptr;  // [6]
+    unsigned long long* counters = nullptr;  // [grape::C_COUNT]
     bool counting = false;
     int64_t device_bytes = 0;
     grape_tuning_t tuning{};
@@ -32,6 +34,7 @@ struct grape_graph {
         g.rec = rec;
         g.dsts = dsts;
         g.fat = fat;
+        g.piv = piv;
         g.n = n;
         g.status = status;
         g.counters = counting ? counters : nullptr;
@@ -65,14 +68,43 @@ struct LaunchShape {
 LaunchShape queue_launch_shape(const grape_graph* g, const grape_tuning_t& t, int weighted);
 
 // Launch the queue (batched / served) kernel.
-// ctl[0] is the queue head and ctl[1] the published tail; done / done_flags are
-// the per-request completion counters and host-mapped flags of a served queue
-// (nullptr for batched launches).
+// ctl[0] is the queue head and ctl[1] the published tail; done (two counters per
+// request: finished walks, transitions taken) and done_flags (host-mapped) are
+// the per-request completion state of a served queue (nullptr for batched
+// launches).
 cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
                                 const WalkConst* reqs, const Chunk* chunks,
                                 unsigned long long* ctl, unsigned long long ring,
                                 long long idle_spins, int* exit_flag, unsigned long long* done,
                                 unsigned* done_flags, int blocks, cudaStream_t stream);
+
+inline Policy policy_of(const grape_tuning_t& t) {
+    Policy p;
+    p.trial_cap = (unsigned)t.trial_cap;
+    p.shorter_min = t.shorter_min;
+    p.interp_search = t.interp_search;
+    p.pivot_min = t.pivot_min;
+    p.warp_search_min = t.warp_search_min;
+    return p;
+}
+
+// The launch attribute of a walk launch: with l2_persist_mb > 0, a persisting
+// access-policy window over the graph's sector pivots (hit ratio: the share of
+// the window the set-aside can hold).  Returns the number of attributes (0 or 1).
+inline int walk_launch_attrs(const grape_graph* g, const grape_tuning_t& t,
+                             cudaLaunchAttribute* attr) {
+    if (t.l2_persist_mb <= 0 || !g->piv || g->max_window <= 0) return 0;
+    const size_t bytes = sizeof(int32_t) * (size_t)((g->m + 7) / 8 + 8);
+    const size_t win = bytes < (size_t)g->max_window ? bytes : (size_t)g->max_window;
+    const double ratio = (double)((size_t)t.l2_persist_mb << 20) / (double)win;
+    attr->id = cudaLaunchAttributeAccessPolicyWindow;
+    attr->val.accessPolicyWindow.base_ptr = g->piv;
+    attr->val.accessPolicyWindow.num_bytes = win;
+    attr->val.accessPolicyWindow.hitRatio = (float)(ratio < 1.0 ? ratio : 1.0);
+    attr->val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr->val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    return 1;
+}
 
 inline grape_status_t cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return GRAPE_OK;

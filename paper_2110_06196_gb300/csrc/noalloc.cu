@@ -34,10 +34,24 @@ constexpr size_t kStaticScratchBytes = (sizeof(StaticScratch) + 255) & ~size_t(2
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_batch_scratch[kStaticScratchBytes];
 
-// Per-device address of g_batch_scratch, filled by the first call on a device.
+// Per-device set-up, done by the first call on a device: the device address of
+// g_batch_scratch and the walk kernel's resident blocks per SM.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct DeviceSetup {
+    void* addr = nullptr;
+    int per_sm[2][2] = {{0, 0}, {0, 0}};    // [weighted][counting]
+};
+DeviceSetup g_setup[kMaxDevices];
+
+// Requests uploaded per table-fill launch.  The batch travels as a kernel
+// parameter, which the launch copies, so nothing on the host has to outlive
+// the call.
+constexpr int kBatch = 32;
+struct TableBatch {
+    WalkConst reqs[kBatch];
+    long long chunk_end[kBatch];
+};
 
 // Queue entries without a stored entry list: entry h is entry
 // h - chunk_end[r - 1] of the request r whose prefix range holds h.
@@ -64,7 +78,8 @@ struct StaticQueueFeed {
     __device__ __forceinline__ int suss_k(const Lane&) const { return 0; }   // exact walks
 
     template <class C>
-    __device__ __forceinline__ void finish(int, C& cnt) { cnt.add(C_WALKS); }
+    __device__ __forceinline__ void finish(const Lane&, C& cnt, int) { cnt.add(C_WALKS); }
+    __device__ __forceinline__ void drain() {}
     __device__ __forceinline__ void alphas(int req, double& a_ret, double& a_out) const {
         a_ret = sc->reqs[req].a_ret;
         a_out = sc->reqs[req].a_out;
@@ -116,7 +131,7 @@ struct StaticQueueFeed {
             if (!have && rank < give) {
                 have = begin_walk(g, sc->reqs[cur_req], cur_req, cur_lo + rank, L);
                 if (have) set_wrec(sc->reqs[cur_req], cur_lo + rank);
-                else finish(cur_req, cnt);
+                else finish(L, cnt, 0);
             }
             cur_lo += give;
             cur_left -= give;
@@ -125,10 +140,18 @@ struct StaticQueueFeed {
     }
 };
 
-template <bool W>
+__global__ void table_fill_kernel(StaticScratch* sc, TableBatch b, int first, int count) {
+    const int j = threadIdx.x;
+    if (j < count) {
+        sc->reqs[first + j] = b.reqs[j];
+        sc->chunk_end[first + j] = b.chunk_end[j];
+    }
+}
+
+template <bool W, bool COUNT>
 __global__ void __launch_bounds__(256, 4)
 static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks, int num_reqs,
-                    int chunk_walks, unsigned trial_cap, int shorter_min, int interp_search) {
+                    int chunk_walks, Policy pol) {
     StaticQueueFeed f;
     f.sc = sc;
     f.head = const_cast<unsigned long long*>(&sc->head);
@@ -139,21 +162,37 @@ static_queue_kernel(GraphDev g, const StaticScratch* sc, long long total_chunks,
     f.cur_left = 0;
     f.cur_req = 0;
     f.drained = false;
-    walk_loop<W, true, true, false>(g, f, trial_cap, shorter_min, interp_search);
+    walk_loop<W, true, true, COUNT>(g, f, pol);
 }
 
-// Device address of g_batch_scratch on the current device (set-up on first use).
-grape_status_t scratch_address(StaticScratch** out) {
+template <bool W, bool C>
+cudaError_t occupancy(int threads, int* out) {
+    int nb = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, static_queue_kernel<W, C>, threads, (size_t)threads * kLaneSharedBytes);
+    *out = nb < 1 ? 1 : nb;
+    return e;
+}
+
+// The current device's set-up (done on first use, with that device current).
+grape_status_t device_setup(int threads, StaticScratch** addr, const DeviceSetup** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GRAPE_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    DeviceSetup& d = g_setup[dev];
+    if (!d.addr) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_batch_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_batch_scratch);
         if (e != cudaSuccess || !p) return GRAPE_ERR_CUDA;
-        g_scratch_addr[dev] = p;
+        if (e == cudaSuccess) e = occupancy<false, false>(threads, &d.per_sm[0][0]);
+        if (e == cudaSuccess) e = occupancy<false, true>(threads, &d.per_sm[0][1]);
+        if (e == cudaSuccess) e = occupancy<true, false>(threads, &d.per_sm[1][0]);
+        if (e == cudaSuccess) e = occupancy<true, true>(threads, &d.per_sm[1][1]);
+        if (e != cudaSuccess) return cuda_status(e);
+        d.addr = p;
     }
-    *out = static_cast<StaticScratch*>(g_scratch_addr[dev]);
+    *addr = static_cast<StaticScratch*>(d.addr);
+    *out = &d;
     return GRAPE_OK;
 }
 
@@ -180,51 +219,53 @@ grape_status_t grape_walks_batched_static(const grape_graph_t* g,
         if (st != GRAPE_OK) return st;
         total += (wc.num_walks + cw - 1) / cw;
     }
+    // Blocks of the graph's tuned size (at most 256, the kernel's launch bounds).
+    constexpr int kDefaultThreads = 256;
+    const int threads = t.block_threads < kDefaultThreads ? t.block_threads : kDefaultThreads;
     StaticScratch* sc = nullptr;
-    grape_status_t st = scratch_address(&sc);
+    const DeviceSetup* dev = nullptr;
+    grape_status_t st = device_setup(kDefaultThreads, &sc, &dev);
     if (st != GRAPE_OK) return st;
-    // Upload in small batches from the stack (no heap allocation): the copy
-    // from pageable memory has consumed the buffer when the call returns.
-    constexpr int kBatch = 32;
-    WalkConst wcs[kBatch];
-    long long ends[kBatch];
     long long run = 0;
     for (int i0 = 0; i0 < n; i0 += kBatch) {
         const int m = (n - i0) < kBatch ? (n - i0) : kBatch;
+        TableBatch b;
+        std::memset(&b, 0, sizeof(b));
         for (int j = 0; j < m; ++j) {
             const grape_walk_request_t& r = reqs[i0 + j];
             make_walk_const(g, r.starts, r.num_starts, r.walk_len, r.walks_per_node, r.p, r.q,
-                            r.seed, r.out, &wcs[j]);
-            run += (wcs[j].num_walks + cw - 1) / cw;
-            ends[j] = run;
+                            r.seed, r.out, &b.reqs[j]);
+            run += (b.reqs[j].num_walks + cw - 1) / cw;
+            b.chunk_end[j] = run;
         }
-        cudaError_t e = cudaMemcpyAsync(&sc->reqs[i0], wcs, sizeof(WalkConst) * m,
-                                        cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&sc->chunk_end[i0], ends, sizeof(long long) * m,
-                                cudaMemcpyHostToDevice, stream);
+        table_fill_kernel<<<1, kBatch, 0, stream>>>(sc, b, i0, m);
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
     }
     // The queue head is the only state that must start at zero.
     cudaError_t e = cudaMemsetAsync(&sc->head, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const LaunchShape s = queue_launch_shape(g, t, g->weighted);
-    int per_sm = 0;
-    if (g->weighted)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_queue_kernel<true>, s.threads,
-                                                      (size_t)s.threads * kLaneSharedBytes);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, static_queue_kernel<false>,
-                                                      s.threads, (size_t)s.threads * kLaneSharedBytes);
-    if (per_sm < 1) per_sm = 1;
+    const int w = g->weighted ? 1 : 0, c = g->counting ? 1 : 0;
+    int per_sm = t.blocks_per_sm;
+    if (per_sm <= 0 && threads == kDefaultThreads) per_sm = dev->per_sm[w][c];
+    if (per_sm <= 0) {
+        e = w ? (c ? occupancy<true, true>(threads, &per_sm) : occupancy<true, false>(threads, &per_sm))
+              : (c ? occupancy<false, true>(threads, &per_sm) : occupancy<false, false>(threads, &per_sm));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     const int blocks = g->num_sms * per_sm;
-    const size_t sh = (size_t)s.threads * kLaneSharedBytes;
-    if (g->weighted)
-        static_queue_kernel<true><<<blocks, s.threads, sh, stream>>>(
-            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
-    else
-        static_queue_kernel<false><<<blocks, s.threads, sh, stream>>>(
-            g->dev(), sc, total, n, cw, (unsigned)t.trial_cap, t.shorter_min, t.interp_search);
+    const size_t sh = (size_t)threads * kLaneSharedBytes;
+#define GRAPE_STATIC_LAUNCH(W, C)                                                              \
+    static_queue_kernel<W, C><<<blocks, threads, sh, stream>>>(                                 \
+        g->dev(), sc, total, n, cw, policy_of(t))
+    if (g->weighted) {
+        if (g->counting) GRAPE_STATIC_LAUNCH(true, true);
+        else GRAPE_STATIC_LAUNCH(true, false);
+    } else {
+        if (g->counting) GRAPE_STATIC_LAUNCH(false, true);
+        else GRAPE_STATIC_LAUNCH(false, false);
+    }
+#undef GRAPE_STATIC_LAUNCH
     return cuda_status(cudaGetLastError());
 }
 

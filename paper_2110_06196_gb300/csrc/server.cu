@@ -17,6 +17,7 @@
 // is running.  Shutdown raises the same flag, which the kernel reads before
 // taking each entry.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -126,7 +127,8 @@ struct grape_server {
     // device state
     char* arena_base = nullptr;
     WalkConst* d_reqs = nullptr;
-    unsigned long long* d_done = nullptr;
+    unsigned long long* d_done = nullptr;   // per slot: finished walks, transitions taken
+    unsigned long long* h_steps = nullptr;  // pinned: per slot, transitions of the finished request
     Chunk* d_chunks = nullptr;
     unsigned long long* d_ctl = nullptr;   // [0] head (next ticket), [1] tail, [2] heartbeat
     int* d_exit = nullptr;
@@ -141,6 +143,7 @@ struct grape_server {
     cudaStream_t compute = nullptr, copy = nullptr, ctl = nullptr;
     cudaEvent_t kernel_done = nullptr;
     bool kernel_launched = false;
+    std::atomic<bool> no_heartbeat{false};   // injected host failure: the heartbeat stops
     bool exit_raised = false;          // d_exit is set for the running kernel
     int64_t idle_since = 0;            // when the server last became idle (ns)
 
@@ -265,7 +268,8 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
         if (st != GRAPE_OK) return st;
         h_flags[q->slot] = 0u;
         e = cudaMemcpyAsync(d_reqs + q->slot, wc, sizeof(WalkConst), cudaMemcpyHostToDevice, ctl);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_done + q->slot, 0, sizeof(unsigned long long), ctl);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(d_done + 2 * q->slot, 0, 2 * sizeof(unsigned long long), ctl);
         if (e != cudaSuccess) return cuda_status(e);
         for (uint64_t c = 0; c < q->num_chunks; ++c) {
             if (nstaged == h_chunks_cap) {
@@ -338,10 +342,17 @@ void grape_server::finish_locked(std::shared_ptr<Req> q, St st, grape_status_t r
 // would leave the next request to the warps that happened to stay); after the
 // server has had nothing in flight for idle_exit_us, the driver raises the
 // exit flag and every warp leaves.  The kernel's own idle wait is only a
-// safety bound of about two seconds of polling for the case that the host
-// never raises the flag.
+// safety bound (kernel_wait_ms of sleep without a host heartbeat, 2 s by
+// default) for the case that the host stops: a warp whose wait runs out raises
+// bit 2 of the graph's status word and leaves.  A kernel that ends without
+// being asked to is counted in stats.kernel_timeouts; requests it left
+// unfinished fail with GRAPE_ERR_TIMEOUT (an entry published as its last warp
+// gave up may have no taker), and the next request relaunches it.
 void grape_server::run() {
-    const long long idle_spins = 2000000;   // an idle warp sleeps about 2 s in total before leaving
+    const int64_t wait_ms = cfg.kernel_wait_ms > 0 ? cfg.kernel_wait_ms : 2000;
+    const long long idle_spins = (long long)wait_ms * 1000;   // about a microsecond per unit
+    // the heartbeat comes several times within one wait bound
+    const int64_t beat_ns = std::min<int64_t>(100000000, wait_ms * 1000000 / 4);
     auto set_exit = [&](int v) {
         static thread_local int word;
         word = v;
@@ -436,8 +447,8 @@ void grape_server::run() {
         }
         const bool running = kernel_launched && cudaEventQuery(kernel_done) == cudaErrorNotReady;
         // Heartbeat for the kernel's waiting warps: their bounded wait only runs
-        // out if the host stops beating (about every 100 ms while a kernel runs).
-        if (running && now_ns() - last_beat > 100000000) {
+        // out if the host stops beating.
+        if (running && !no_heartbeat.load() && now_ns() - last_beat > beat_ns) {
             last_beat = now_ns();
             h_misc[1] += 1;
             cudaMemcpyAsync(d_ctl + 2, h_misc + 1, sizeof(unsigned long long),
@@ -466,37 +477,62 @@ void grape_server::run() {
                         finish_locked(q, St::Cancelled, GRAPE_ERR_CANCELLED);
                         continue;
                     }
-                    if (q->host_out) {
-                        cudaError_t e = cudaEventCreateWithFlags(&q->copied, cudaEventDisableTiming);
-                        if (e == cudaSuccess)
-                            e = cudaMemcpyAsync(q->host_out, arena_base + q->arena_off,
-                                                (size_t)q->out_bytes, cudaMemcpyDeviceToHost, copy);
-                        if (e == cudaSuccess) e = cudaEventRecord(q->copied, copy);
-                        if (e != cudaSuccess) {
-                            finish_locked(q, St::Failed, cuda_status(e));
-                            continue;
-                        }
-                        q->st = St::Copying;
-                    } else {
-                        // rows stay in the arena until wait() hands them over
-                        q->st = St::Done;
-                        q->t_done = now_ns();
-                        q->inflight = false;
-                        stats.inflight--;
-                        stats.completed++;
-                        finished.push_back(q->ticket);
-                        cv.notify_all();
+                    // the request's transition count, and its rows unless they
+                    // stay in the arena until wait() hands them over
+                    cudaError_t e = cudaEventCreateWithFlags(&q->copied, cudaEventDisableTiming);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(h_steps + q->slot, d_done + 2 * q->slot + 1,
+                                            sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                            copy);
+                    if (e == cudaSuccess && q->host_out)
+                        e = cudaMemcpyAsync(q->host_out, arena_base + q->arena_off,
+                                            (size_t)q->out_bytes, cudaMemcpyDeviceToHost, copy);
+                    if (e == cudaSuccess) e = cudaEventRecord(q->copied, copy);
+                    if (e != cudaSuccess) {
+                        finish_locked(q, St::Failed, cuda_status(e));
+                        continue;
                     }
+                    q->st = St::Copying;
                 } else if (q->st == St::Copying) {
                     const cudaError_t e = cudaEventQuery(q->copied);
                     if (e == cudaSuccess) {
                         busy = true;
-                        finish_locked(q, q->cancel ? St::Cancelled : St::Done,
-                                      q->cancel ? GRAPE_ERR_CANCELLED : GRAPE_OK);
+                        if (!q->cancel) stats.steps += (int64_t)h_steps[q->slot];
+                        if (q->cancel) {
+                            finish_locked(q, St::Cancelled, GRAPE_ERR_CANCELLED);
+                        } else if (q->host_out) {
+                            finish_locked(q, St::Done, GRAPE_OK);
+                        } else {
+                            // rows stay in the arena until wait() hands them over
+                            cudaEventDestroy(q->copied);
+                            q->copied = nullptr;
+                            q->st = St::Done;
+                            q->t_done = now_ns();
+                            q->inflight = false;
+                            stats.inflight--;
+                            stats.completed++;
+                            finished.push_back(q->ticket);
+                            cv.notify_all();
+                        }
                     } else if (e != cudaErrorNotReady) {
                         finish_locked(q, St::Failed, cuda_status(e));
                     }
                 }
+            }
+        }
+        // A kernel that ended without the exit flag: its waits ran out.  Its
+        // completion flags are final now; what it left unfinished fails.
+        if (kernel_launched && !exit_raised &&
+            cudaEventQuery(kernel_done) != cudaErrorNotReady) {
+            busy = true;
+            std::lock_guard<std::mutex> lk(mu);
+            kernel_launched = false;
+            stats.kernel_timeouts++;
+            const std::vector<int> snapshot = active;   // finish_locked edits active
+            for (const int slot : snapshot) {
+                const std::shared_ptr<Req> q = by_slot[(size_t)slot];
+                if (q && q->st == St::Admitted && ((volatile unsigned*)h_flags)[q->slot] == 0u)
+                    finish_locked(q, St::Failed, GRAPE_ERR_TIMEOUT);
             }
         }
         if (!busy) {
@@ -518,7 +554,7 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     *out = nullptr;
     if (!g || !cfg || cfg->output_cap_bytes < 4096 || cfg->max_inflight < 1 ||
         cfg->max_inflight > 65536 || cfg->chunk_walks < 0 || cfg->max_chunks < 1 ||
-        cfg->idle_exit_us < 1 || cfg->admit_timeout_ms < 0)
+        cfg->idle_exit_us < 1 || cfg->admit_timeout_ms < 0 || cfg->kernel_wait_ms < 0)
         return GRAPE_ERR_INVALID_ARG;
     grape_server* s = new (std::nothrow) grape_server();
     if (!s) return GRAPE_ERR_NOMEM;
@@ -538,7 +574,10 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = cudaMalloc(&s->arena_base, (size_t)cfg->output_cap_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_reqs, sizeof(WalkConst) * (size_t)slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_done, sizeof(unsigned long long) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_done, 2 * sizeof(unsigned long long) * (size_t)slots);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&s->h_steps, sizeof(unsigned long long) * (size_t)slots,
+                          cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_chunks, sizeof(Chunk) * (size_t)cfg->max_chunks);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctl, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_exit, sizeof(int));
@@ -679,6 +718,12 @@ grape_status_t grape_walk_server_cancel(grape_server_t* s, uint64_t ticket) {
     return GRAPE_OK;
 }
 
+grape_status_t grape_walk_server_inject_fault(grape_server_t* s, uint32_t faults) {
+    if (!s || (faults & ~GRAPE_FAULT_NO_HEARTBEAT) != 0u) return GRAPE_ERR_INVALID_ARG;
+    s->no_heartbeat.store((faults & GRAPE_FAULT_NO_HEARTBEAT) != 0u);
+    return GRAPE_OK;
+}
+
 grape_status_t grape_walk_server_stats(grape_server_t* s, grape_server_stats_t* out) {
     if (!s || !out) return GRAPE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -713,6 +758,7 @@ void grape_walk_server_destroy(grape_server_t* s) {
     if (s->copy) cudaStreamDestroy(s->copy);
     if (s->ctl) cudaStreamDestroy(s->ctl);
     if (s->h_flags) cudaFreeHost(s->h_flags);
+    if (s->h_steps) cudaFreeHost(s->h_steps);
     if (s->h_wc) cudaFreeHost(s->h_wc);
     if (s->h_tail) cudaFreeHost(s->h_tail);
     if (s->h_misc) cudaFreeHost(s->h_misc);

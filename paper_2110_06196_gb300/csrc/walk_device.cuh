@@ -48,7 +48,7 @@ struct __align__(16) NodeRec {
 
 enum Counter : int {
     C_STEPS = 0, C_TRIALS, C_GATHERS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_FILTERED,
-    C_COUNT
+    C_PIVOT_PROBES, C_COUNT
 };
 
 // Neighbour filters (unweighted graphs): a 96-bit one-hash Bloom filter of each
@@ -74,6 +74,9 @@ struct GraphDev {
     //                 unweighted: {filter of N(x) bits 0-31, bits 32-63, rev, bits 64-95}
     // rev = position of v in N(x) (-1 when absent), w_xv the weight there
     const int4* fat;
+    // sector pivots: piv[j] = dsts[8 j], the first id of each aligned 32-byte
+    // sector of dsts ([ceil(m / 8) + 8], padded), or nullptr
+    const int* piv;
     long long n;
     int* status;                // device status word (1 = bad start id)
     unsigned long long* counters;  // [C_COUNT] or nullptr
@@ -253,6 +256,8 @@ enum : unsigned {
     F_VEC = 8u,           // output rows may be written in whole 32-byte sectors
     F_KEY_T = 16u,        // the search looks for t in N(x) (else for x in N(t))
     F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
+    F_PIV = 64u,          // the search runs over the list's sector pivots, not the list
+    F_WARPQ = 128u,       // a new search waits for the warp to narrow its list (no probe yet)
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
@@ -266,11 +271,13 @@ struct Counts {
         for (int i = 0; i < C_COUNT; ++i) c[i] = 0;
     }
     __device__ __forceinline__ void add(int i) { c[i]++; }
+    __device__ __forceinline__ void add_n(int i, unsigned n) { c[i] += n; }
 };
 template <>
 struct Counts<false> {
     __device__ __forceinline__ void clear() {}
     __device__ __forceinline__ void add(int) {}
+    __device__ __forceinline__ void add_n(int, unsigned) {}
 };
 
 // The previous node's record and the entry the walk arrived by.  Read only
@@ -524,7 +531,7 @@ __device__ __forceinline__ bool begin_walk(const GraphDev& g, const WalkConst& w
     L.s = 1;
     L.k = 0;
     L.phase = PH_START;
-    L.flags &= ~(F_KEY_T | F_ACC_IN | F_ACC_OUT | F_BISECT);
+    L.flags &= ~(F_KEY_T | F_ACC_IN | F_ACC_OUT | F_BISECT | F_PIV | F_WARPQ);
     if (wc.walk_len <= 1) return false;
     if (r.deg == 0) {
         fill_dead(L, rowp, 1, wc.walk_len);
@@ -550,6 +557,49 @@ __device__ __forceinline__ void flush_counts(const GraphDev& g, Counts<true>& c)
 // Walk sources
 // ---------------------------------------------------------------------------
 
+// Completion signal of a per-call launch cut into slices of walk rows: every
+// slice has a device counter of finished walks and a flag in mapped host
+// memory, raised when its last walk is written, so the host can copy a
+// slice out while the launch goes on.  walks_per_slice = 0: no slices.
+struct SliceSink {
+    unsigned long long* done;    // [slices] finished walks (device)
+    unsigned* flags;             // [slices] host-mapped: 1 once the slice's rows are written
+    long long walks_per_slice;
+    long long num_walks;         // rows of the launch
+};
+
+// A lane's running count of finished walks in one slice (per-call launches do
+// not use the WRec slot, so the tally lives there).
+struct __align__(16) SliceTally {
+    long long slice;
+    unsigned count;
+};
+
+__device__ __forceinline__ SliceTally* slice_tally() {
+    extern __shared__ int4 stage_words[];
+    return reinterpret_cast<SliceTally*>(stage_words + 6 * blockDim.x) + threadIdx.x;
+}
+
+// Add the lane's tally to its slice's counter.  The add is a release, so this
+// lane's rows are visible before they count; the add that completes the slice
+// is followed by an acquire fence (every other lane's rows are then visible)
+// and a system fence before the host-visible flag goes up.
+__device__ __forceinline__ void flush_slice(const SliceSink& sk, SliceTally* st) {
+    if (st->count == 0 || st->slice < 0) return;
+    const long long sl = st->slice;
+    const long long left = sk.num_walks - sl * sk.walks_per_slice;
+    const unsigned long long size =
+        (unsigned long long)(left < sk.walks_per_slice ? left : sk.walks_per_slice);
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> c(sk.done[sl]);
+    const unsigned long long prev = c.fetch_add(st->count, cuda::memory_order_release);
+    if (prev + st->count == size) {
+        cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+        __threadfence_system();
+        *(volatile unsigned*)(sk.flags + sl) = 1u;
+    }
+    st->count = 0;
+}
+
 // Record the request constants of row `row` of wc for this lane (queue feeds).
 __device__ __forceinline__ void set_wrec(const WalkConst& wc, long long row) {
     WRec r;
@@ -568,6 +618,7 @@ template <bool SUSS>
 struct GridFeed {
     const WalkConst* wc;     // kernel-parameter copy
     const RoundKeys* rk;     // kernel-parameter copy: the Philox round keys of wc->seed
+    const SliceSink* sink;   // kernel-parameter copy: slice completion (walks_per_slice 0: none)
     long long next;
     long long stride;
 
@@ -591,8 +642,25 @@ struct GridFeed {
         return wc->out + (L.w - wc->walk_base) * (long long)wc->walk_len;
     }
 
+    // Rows of one lane finish in increasing walk-id order (grid stride), so a
+    // lane's tally moves through the slices in order and is added to a
+    // slice's counter when the lane moves past it.
     template <class C>
-    __device__ __forceinline__ void finish(int, C& cnt) { cnt.add(C_WALKS); }
+    __device__ __forceinline__ void finish(const Lane& L, C& cnt, int) {
+        cnt.add(C_WALKS);
+        if (sink->walks_per_slice <= 0) return;
+        const long long sl = (L.w - wc->walk_base) / sink->walks_per_slice;
+        SliceTally* st = slice_tally();
+        if (sl != st->slice) {
+            flush_slice(*sink, st);
+            st->slice = sl;
+        }
+        st->count++;
+    }
+    // After the lane's last walk.
+    __device__ __forceinline__ void drain() {
+        if (sink->walks_per_slice > 0) flush_slice(*sink, slice_tally());
+    }
     __device__ __forceinline__ void alphas(int, double& a_ret, double& a_out) const {
         a_ret = wc->a_ret;
         a_out = wc->a_out;
@@ -604,7 +672,7 @@ struct GridFeed {
             const long long row = next;
             next += stride;
             have = begin_walk(g, *wc, -1, row, L);
-            if (!have) finish(-1, cnt);
+            if (!have) finish(L, cnt, 0);
         }
         return have;
     }
@@ -638,7 +706,8 @@ struct QueueFeed {
     unsigned long long ring;     // ring capacity (entries)
     long long idle_spins;        // served: polls of an empty queue before giving up; 0 batched
     int* exit_flag;              // served: set when the kernel should stop
-    unsigned long long* done;    // served: per-request finished-walk counters, else nullptr
+    unsigned long long* done;    // served: per request, finished walks and transitions taken
+                                 // (done[2 r], done[2 r + 1]); batched: nullptr
     unsigned* done_flags;        // served: per-request host-mapped completion flags
     int* status;                 // the graph's device status word
     // warp-uniform state
@@ -660,15 +729,19 @@ struct QueueFeed {
     __device__ __forceinline__ int* row(const Lane&) const { return wrec()->row; }
     __device__ __forceinline__ int suss_k(const Lane&) const { return 0; }   // exact walks
 
+    __device__ __forceinline__ void drain() {}
+    // steps: transitions the finished walk took.
     template <class C>
-    __device__ __forceinline__ void finish(int req, C& cnt) {
+    __device__ __forceinline__ void finish(const Lane& L, C& cnt, int steps) {
         cnt.add(C_WALKS);
         if (done == nullptr) return;                 // batched: nothing to publish
+        const int req = L.req;
+        if (steps > 0) atomicAdd(done + 2 * req + 1, (unsigned long long)steps);
         // Each walk's count is a release: its rows are visible before it counts.
         // The walk that completes the request adds an acquire fence, so it has
         // seen every other walk's rows before it raises the host-visible flag.
         const long long nw = __ldcg(&reqs[req].num_walks);
-        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> c(done[req]);
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> c(done[2 * req]);
         const unsigned long long prev = c.fetch_add(1ull, cuda::memory_order_release);
         if (prev + 1 == (unsigned long long)nw) {
             cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
@@ -807,7 +880,7 @@ struct QueueFeed {
                 const WalkConst wc = load_walkconst(reqs + cur_req);
                 have = begin_walk(g, wc, cur_req, cur_lo + rank, L);
                 if (have) set_wrec(wc, cur_lo + rank);
-                else finish(cur_req, cnt);
+                else finish(L, cnt, 0);
             }
             cur_lo += give;
             cur_left -= give;
@@ -834,6 +907,10 @@ struct Engine {
     int shorter_min;             // undirected: search the shorter of N(t), N(x) when
                                  // deg_t exceeds this
     bool interp;                 // place probes by interpolation between the value bounds
+    int warp_min;                // new searches over lists longer than this are first narrowed
+                                 // by the whole warp (INT_MAX: never)
+    int pivot_min;               // lists of at least this many entries are searched over their
+                                 // sector pivots first (INT_MAX: never)
     Counts<COUNT>& cnt;
     int4& ld;                    // the gather in flight: a proposal entry or a probe
     int4& ld2;                   // sector, first and second 16 bytes
@@ -863,12 +940,12 @@ struct Engine {
         L.s++;
         L.k = 0;
         if (L.s >= len) {
-            feed.finish(L.req, cnt);
+            feed.finish(L, cnt, L.s - 1);
             return false;
         }
         if (deg == 0) {
             fill_dead(L, row, L.s, len);
-            feed.finish(L.req, cnt);
+            feed.finish(L, cnt, L.s - 1);
             return false;
         }
         return true;
@@ -961,10 +1038,106 @@ struct Engine {
         const bool use_x = g.undirected && deg_t > shorter_min && p.deg < deg_t;
         L.sb = use_x ? p.off : tr->off_t;
         L.sn = use_x ? p.deg : deg_t;
-        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT)) |
+        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT | F_PIV | F_WARPQ)) |
                   (p.acc_a ? F_ACC_IN : 0u) | (p.acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
         L.vlo = -1;                      // node ids lie in [0, n)
         L.vhi = (int)g.n;
+        // A long list is first searched over its sector pivots: piv[j] for the
+        // aligned sectors j0 < j <= j1 that start inside the list.  They bracket
+        // the one sector that can hold the key, which is then read.
+        if (g.piv != nullptr && L.sn >= pivot_min) {
+            const long long j0 = L.sb >> 3, j1 = (L.sb + L.sn - 1) >> 3;
+            if (j1 > j0) {
+                L.flags |= F_PIV;
+                L.sb = j0 + 1;
+                L.sn = (int)(j1 - j0);
+            }
+        }
+    }
+
+    // Bounds of the list under search (the row of x, parked, or of t).
+    __device__ __forceinline__ void list_bounds(const Lane& L, long long& b, int& n) const {
+        if (L.flags & F_KEY_T) {
+            const int4 a = parked_entry()[0];
+            b = (long long)(((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.z);
+            n = a.y;
+        } else {
+            const TRec* tr = trec();
+            b = tr->off_t;
+            n = tr->deg_t;
+        }
+    }
+
+    // The next probe of L's search: the aligned 32-byte sector of the list (or
+    // of its pivots) around the position interpolated between the value bounds
+    // (ids in a row are near-uniform after relabelling), or the midpoint.
+    __device__ __forceinline__ const int4* probe_addr(Lane& L) {
+        int pos = L.sn >> 1;
+        if (interp && !(L.flags & F_BISECT)) {
+            const int kk = (L.flags & F_KEY_T) ? L.t : L.x;
+            const float f = __fdividef((float)(kk - L.vlo), (float)(L.vhi - L.vlo));
+            pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
+        }
+        const long long bi = (L.sb + pos) & ~7LL;
+        const bool piv = (L.flags & F_PIV) != 0;
+        L.sd = (int)(bi - L.sb);
+        L.phase = PH_SEARCH;
+        cnt.add(C_PROBES);
+        if (piv) cnt.add(C_PIVOT_PROBES);
+        return reinterpret_cast<const int4*>((piv ? g.piv : g.dsts) + bi);
+    }
+
+    // Warp-cooperative narrowing (warp-collective; every lane calls it).  Each
+    // lane whose new search waits (F_WARPQ) is served in turn: the 32 lanes read
+    // the list at 32 evenly spaced positions and a ballot of (value <= key)
+    // leaves 1/33 of the range, until at most kWarpLeft entries remain or the
+    // key is met; then the lane issues its own first probe on what is left.
+    static constexpr int kWarpLeft = 256;
+    __device__ __forceinline__ void warp_search(Lane& L, bool have) {
+        unsigned q = __ballot_sync(FULL, have && (L.flags & F_WARPQ));
+        const int lane = threadIdx.x & 31;
+        while (q) {
+            const int src = __ffs(q) - 1;
+            q &= q - 1;
+            long long sb = __shfl_sync(FULL, L.sb, src);
+            int sn = __shfl_sync(FULL, L.sn, src);
+            const int key = __shfl_sync(FULL, (L.flags & F_KEY_T) ? L.t : L.x, src);
+            int vlo = __shfl_sync(FULL, L.vlo, src), vhi = __shfl_sync(FULL, L.vhi, src);
+            unsigned reads = 0;
+            while (sn > kWarpLeft) {
+                const int pos = (int)(((long long)(lane + 1) * sn) / 33);
+                const int v = __ldg(g.dsts + sb + pos);
+                reads += 32;
+                const unsigned eq = __ballot_sync(FULL, v == key);
+                if (eq) {                            // met: leave just that entry
+                    sb += __shfl_sync(FULL, pos, __ffs(eq) - 1);
+                    sn = 1;
+                    vlo = key - 1;
+                    vhi = key + 1;
+                    break;
+                }
+                const int c = __popc(__ballot_sync(FULL, v < key));   // lanes below the key
+                const int plo = __shfl_sync(FULL, pos, c == 0 ? 0 : c - 1);
+                const int vl = __shfl_sync(FULL, v, c == 0 ? 0 : c - 1);
+                const int phi = __shfl_sync(FULL, pos, c == 32 ? 31 : c);
+                const int vh = __shfl_sync(FULL, v, c == 32 ? 31 : c);
+                const int lo = c == 0 ? 0 : plo + 1;
+                const int hi = c == 32 ? sn : phi;
+                if (c > 0) vlo = vl;
+                if (c < 32) vhi = vh;
+                sb += lo;
+                sn = hi - lo;
+            }
+            if (lane == src) {
+                L.sb = sb;
+                L.sn = sn;
+                L.vlo = vlo;
+                L.vhi = vhi;
+                L.flags &= ~F_WARPQ;
+                cnt.add_n(C_PROBES, reads);
+                ld_sector(probe_addr(L), ld, ld2);
+            }
+        }
     }
 
     // One iteration for a lane that holds a walk.  Returns have.
@@ -1003,6 +1176,7 @@ struct Engine {
         // ---- outcome ----
         bool take = false;           // the walk moves to A (or to the searched proposal)
         bool probe = false;
+        bool fresh = false;          // a search began in this iteration
         if (phase == PH_CAND) {
             if (A.acc_a == A.acc_b || !HAS_Q) {
                 if (A.acc_a) take = true;
@@ -1013,10 +1187,26 @@ struct Engine {
                 else L.k++;
             } else {
                 begin_search(L, A);
+                fresh = true;
                 probe = true;
             }
         } else if (srch) {
-            if (s_done) {
+            if (s_done && !found && (L.flags & F_PIV)) {
+                // The pivots place the key in one sector of the list: pivots
+                // before position lo (of the narrowed range) are below it.
+                const long long sector = L.sb - 1 + lo;
+                long long rb;
+                int rn;
+                list_bounds(L, rb, rn);
+                const long long a = rb > 8 * sector ? rb : 8 * sector;
+                const long long b = (rb + rn) < (8 * sector + 8) ? (rb + rn) : (8 * sector + 8);
+                L.flags &= ~(F_PIV | F_BISECT);
+                L.sb = a;
+                L.sn = (int)(b - a);
+                L.vlo = vlo;
+                L.vhi = vhi;
+                probe = true;
+            } else if (s_done) {
                 if ((L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0) take = true;
                 else L.k++;
             } else {
@@ -1060,20 +1250,12 @@ struct Engine {
         }
         const int4* addr = nullptr;
         if (probe) {
-            // the aligned sector around the probe position: interpolated between
-            // the value bounds (ids in a row are near-uniform after relabelling),
-            // or the midpoint
-            int pos = L.sn >> 1;
-            if (interp && !(L.flags & F_BISECT)) {
-                const int kk = (L.flags & F_KEY_T) ? L.t : L.x;   // begin_search may have set it
-                const float f = __fdividef((float)(kk - L.vlo), (float)(L.vhi - L.vlo));
-                pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
+            if (fresh && L.sn > warp_min && !(L.flags & F_PIV)) {
+                L.flags |= F_WARPQ;          // warp_search issues this lane's first probe
+                L.phase = PH_SEARCH;
+            } else {
+                addr = probe_addr(L);
             }
-            const long long bi = (L.sb + pos) & ~7LL;
-            addr = reinterpret_cast<const int4*>(g.dsts + bi);
-            L.sd = (int)(bi - L.sb);
-            L.phase = PH_SEARCH;
-            cnt.add(C_PROBES);
         } else {
             // Draw proposals until one needs its entry read, at most
             // kDrawsPerIter of them.  Past the first step the lane knows where t
@@ -1125,9 +1307,17 @@ struct Engine {
     }
 };
 
+// Search and fallback policy of a launch (grape_tuning_t's fields).
+struct Policy {
+    unsigned trial_cap;
+    int shorter_min;
+    int interp_search;
+    int pivot_min;
+    int warp_search_min;
+};
+
 template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
-__device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigned trial_cap,
-                                          int shorter_min, int interp_search) {
+__device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, const Policy& pol) {
     Lane L;
     L.t = -1;
     L.req = -1;
@@ -1144,14 +1334,17 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, unsigne
     cnt.clear();
     int4 ld = make_int4(0, 0, 0, 0);
     int4 ld2 = make_int4(0, 0, 0, 0);
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, trial_cap, shorter_min,
-                                                    interp_search != 0, cnt, ld, ld2};
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, pol.trial_cap, pol.shorter_min,
+                                                    pol.interp_search != 0, pol.warp_search_min,
+                                                    pol.pivot_min, cnt, ld, ld2};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);
         if (!__any_sync(FULL, have)) break;
         if (have) have = eng.step(L);
+        if (pol.warp_search_min != 0x7fffffff) eng.warp_search(L, have);
     }
+    feed.drain();
     flush_counts(g, cnt);
 }
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -32,14 +33,19 @@ constexpr int kMinBlocksQueue = 4;
 // the general p, q specialisation.
 template <bool W, bool P, bool Q, bool COUNT, bool SUSS = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
-walk_kernel(GraphDev g, WalkConst wc, RoundKeys rk, unsigned trial_cap, int shorter_min,
-            int interp_search) {
+walk_kernel(GraphDev g, WalkConst wc, RoundKeys rk, SliceSink sink, Policy pol) {
     GridFeed<SUSS> f;
     f.wc = &wc;
     f.rk = &rk;
+    f.sink = &sink;
+    if (sink.walks_per_slice > 0) {
+        SliceTally* st = slice_tally();
+        st->slice = -1;
+        st->count = 0;
+    }
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
-    walk_loop<W, P, Q, COUNT>(g, f, trial_cap, shorter_min, interp_search);
+    walk_loop<W, P, Q, COUNT>(g, f, pol);
 }
 
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
@@ -47,8 +53,7 @@ template <bool W, bool COUNT>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksQueue)
 queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* ctl,
              unsigned long long ring, long long idle_spins, int* exit_flag,
-             unsigned long long* done, unsigned* done_flags, unsigned trial_cap, int shorter_min,
-             int interp_search) {
+             unsigned long long* done, unsigned* done_flags, Policy pol) {
     QueueFeed f;
     f.reqs = reqs;
     f.chunks = chunks;
@@ -65,7 +70,7 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.idle_polls = 0;
     if ((threadIdx.x & 31) == 0) *warp_ticket() = kNoTicket;
     __syncwarp();
-    walk_loop<W, true, true, COUNT>(g, f, trial_cap, shorter_min, interp_search);
+    walk_loop<W, true, true, COUNT>(g, f, pol);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint32_t* __restrict__ out) {
@@ -80,35 +85,99 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint
     }
 }
 
-// Random-sector gather probe: 8 independent sector reads in flight per thread.
-// mode selects the load's cache path: 0 ld.global.nc (read-only path through
-// L1), 1 ld.global.cg (L2 only), 2 ld.global.cs (streaming).
-template <int MODE>
+// Random-sector gather probe: the ceiling of independent random 32-byte
+// reads.  Each thread keeps LOADS reads in flight, each of WIDTH bytes (4, 16
+// or 32: one 32-bit, 128-bit or 256-bit load) at the start of a random aligned
+// 32-byte sector, then folds what arrived into a checksum.  MODE picks the
+// cache path: 0 ld.global.nc (read-only, through L1), 1 ld.global.cg (L2
+// only), 2 ld.global.cs (streaming).  Positions come from the SplitMix64 output
+// function of a per-thread counter (cheap next to a Philox block, so the
+// probe measures the memory system, not the generator).
+__device__ __forceinline__ unsigned long long probe_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One sector read of WIDTH bytes into w[0 .. WIDTH/4).  Volatile, so the
+// loads stay above the warp barrier that precedes the fold.
+template <int WIDTH, int MODE>
+__device__ __forceinline__ void probe_load(const char* p, unsigned* w) {
+    if (WIDTH == 4) {
+        if (MODE == 0) asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(w[0]) : "l"(p));
+        else if (MODE == 1) asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(w[0]) : "l"(p));
+        else asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(w[0]) : "l"(p));
+    } else if (WIDTH == 16) {
+        if (MODE == 0)
+            asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+        else if (MODE == 1)
+            asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+        else
+            asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+    } else {
+        if (MODE == 0)
+            asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                  "=r"(w[6]), "=r"(w[7]) : "l"(p));
+        else if (MODE == 1)
+            asm volatile("ld.global.cg.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                  "=r"(w[6]), "=r"(w[7]) : "l"(p));
+        else
+            asm volatile("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                  "=r"(w[6]), "=r"(w[7]) : "l"(p));
+    }
+}
+
+template <int LOADS, int WIDTH, int MODE>
 __global__ void __launch_bounds__(256)
-sector_probe_kernel(const int4* __restrict__ buf, unsigned long long nsec, long long reads_per_thread,
+sector_probe_kernel(const char* __restrict__ buf, unsigned long long nsec, long long rounds,
                     unsigned long long seed, uint32_t* sink) {
-    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    constexpr int WORDS = WIDTH / 4;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    unsigned long long ctr = probe_mix(seed ^ (tid * 0x9E3779B97F4A7C15ull));
     unsigned acc = 0;
-    for (long long j = 0; j < reads_per_thread; j += 8) {
-        unsigned long long idx[8];
+    for (long long j = 0; j < rounds; ++j) {
+        unsigned v[LOADS * WORDS];
 #pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            const uint4 r = trial_block(seed, tid, (int)(j >> 3), (unsigned)u);
-            const unsigned long long a = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
-            const unsigned long long b = (unsigned long long)r.z | ((unsigned long long)r.w << 32);
-            idx[u] = __umul64hi(a, nsec);
-            idx[u + 1] = __umul64hi(b, nsec);
+        for (int u = 0; u < LOADS; ++u) {
+            ctr += 0x9E3779B97F4A7C15ull;
+            const unsigned long long idx = __umul64hi(probe_mix(ctr), nsec);
+            probe_load<WIDTH, MODE>(buf + 32 * idx, v + u * WORDS);
         }
-        int4 v[8];
+        // The fold mixes in a value read after the last load is issued, so no
+        // fold can start before every read of the round is in flight.
+        unsigned k;
+        asm volatile("mov.u32 %0, %%clock;" : "=r"(k));
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int4* p = buf + 2 * idx[u];
-            v[u] = MODE == 0 ? __ldg(p) : (MODE == 1 ? __ldcg(p) : __ldcs(p));
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc ^= (unsigned)(v[u].x ^ v[u].w);
+        for (int u = 0; u < LOADS * WORDS; ++u) acc ^= v[u] + k;
     }
     if (acc == 0x9e3779b9u) atomicXor(sink, acc);   // practically never; keeps the loads live
+}
+
+// The probe's (loads, width) pairs: at most 128 registers of loads in flight.
+template <int LOADS, int WIDTH>
+cudaError_t launch_probe_lw(int mode, const char* buf, unsigned long long nsec, long long n_reads,
+                            unsigned long long seed, uint32_t* sink, int num_sms, int blocks_per_sm,
+                            int* resident, long long* reads_done, cudaStream_t st) {
+    auto k = mode == 0 ? sector_probe_kernel<LOADS, WIDTH, 0>
+                       : (mode == 1 ? sector_probe_kernel<LOADS, WIDTH, 1>
+                                    : sector_probe_kernel<LOADS, WIDTH, 2>);
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, occ) : occ;
+    const long long threads = (long long)num_sms * per_sm * 256;
+    const long long rounds = std::max<long long>(1, (n_reads + threads * LOADS - 1) / (threads * LOADS));
+    k<<<(unsigned)(num_sms * per_sm), 256, 0, st>>>(buf, nsec, rounds, seed, sink);
+    if (resident) *resident = per_sm;
+    if (reads_done) *reads_done = rounds * threads * LOADS;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -129,7 +198,7 @@ int occupancy_blocks(K kernel, int threads) {
 
 template <bool W, bool P, bool Q, bool C, bool S = false>
 cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
-                          cudaStream_t stream) {
+                          const SliceSink& sink, cudaStream_t stream) {
     const int threads = std::min(t.block_threads, kMaxThreads);
     int per_sm = t.blocks_per_sm;
     if (per_sm <= 0) per_sm = occupancy_blocks(walk_kernel<W, P, Q, C, S>, threads);
@@ -137,44 +206,53 @@ cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const W
     const long long cap = (long long)g->num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    walk_kernel<W, P, Q, C, S><<<(unsigned)blocks, threads, stage_bytes(threads), stream>>>(
-        g->dev(), wc, round_keys(wc.seed), (unsigned)t.trial_cap, t.shorter_min,
-        t.interp_search);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = stage_bytes(threads);
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = (unsigned)walk_launch_attrs(g, t, attr);
+    return cudaLaunchKernelEx(&cfg, walk_kernel<W, P, Q, C, S>, g->dev(), wc, round_keys(wc.seed),
+                              sink, policy_of(t));
 }
 
 template <bool W, bool P, bool Q>
 cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
-                        cudaStream_t stream) {
-    return g->counting ? launch_walk_c<W, P, Q, true>(g, t, wc, stream)
-                       : launch_walk_c<W, P, Q, false>(g, t, wc, stream);
+                        const SliceSink& k, cudaStream_t stream) {
+    return g->counting ? launch_walk_c<W, P, Q, true>(g, t, wc, k, stream)
+                       : launch_walk_c<W, P, Q, false>(g, t, wc, k, stream);
 }
 
+constexpr SliceSink kNoSlices = {nullptr, nullptr, 0, 0};
+
 cudaError_t dispatch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
-                          bool has_p, bool has_q, cudaStream_t s) {
+                          bool has_p, bool has_q, cudaStream_t s,
+                          const SliceSink& k = kNoSlices) {
     if (wc.suss_k > 0) {
         if (g->weighted)
-            return g->counting ? launch_walk_c<true, true, true, true, true>(g, t, wc, s)
-                               : launch_walk_c<true, true, true, false, true>(g, t, wc, s);
-        return g->counting ? launch_walk_c<false, true, true, true, true>(g, t, wc, s)
-                           : launch_walk_c<false, true, true, false, true>(g, t, wc, s);
+            return g->counting ? launch_walk_c<true, true, true, true, true>(g, t, wc, k, s)
+                               : launch_walk_c<true, true, true, false, true>(g, t, wc, k, s);
+        return g->counting ? launch_walk_c<false, true, true, true, true>(g, t, wc, k, s)
+                           : launch_walk_c<false, true, true, false, true>(g, t, wc, k, s);
     }
     if (g->weighted) {
-        if (has_p) return has_q ? launch_walk<true, true, true>(g, t, wc, s)
-                                : launch_walk<true, true, false>(g, t, wc, s);
-        return has_q ? launch_walk<true, false, true>(g, t, wc, s)
-                     : launch_walk<true, false, false>(g, t, wc, s);
+        if (has_p) return has_q ? launch_walk<true, true, true>(g, t, wc, k, s)
+                                : launch_walk<true, true, false>(g, t, wc, k, s);
+        return has_q ? launch_walk<true, false, true>(g, t, wc, k, s)
+                     : launch_walk<true, false, false>(g, t, wc, k, s);
     }
-    if (has_p) return has_q ? launch_walk<false, true, true>(g, t, wc, s)
-                            : launch_walk<false, true, false>(g, t, wc, s);
-    return has_q ? launch_walk<false, false, true>(g, t, wc, s)
-                 : launch_walk<false, false, false>(g, t, wc, s);
+    if (has_p) return has_q ? launch_walk<false, true, true>(g, t, wc, k, s)
+                            : launch_walk<false, true, false>(g, t, wc, k, s);
+    return has_q ? launch_walk<false, false, true>(g, t, wc, k, s)
+                 : launch_walk<false, false, false>(g, t, wc, k, s);
 }
 
 bool valid_pq(double x) { return std::isfinite(x) && x > 0.0; }
 
 // grape_walks_host: at most this many slices, of at least this many bytes.
-constexpr size_t kHostSlices = 16;
+constexpr int kHostSlices = 64;
 constexpr size_t kHostSliceBytes = 64u << 20;
 
 // One non-blocking stream per device for grape_walks_host's copies out.
@@ -192,6 +270,43 @@ cudaError_t host_copy_stream(cudaStream_t* out) {
     }
     *out = streams[dev];
     return cudaSuccess;
+}
+
+// Slice-completion flags in mapped host memory (kHostSlices per array), kept
+// per device and reused: a call takes an array and gives it back, so
+// concurrent calls never share one and no call pays for a pinned allocation
+// after the first.
+struct SliceFlags {
+    unsigned* host = nullptr;
+    unsigned* dev = nullptr;
+};
+
+std::mutex g_flags_mu;
+std::vector<SliceFlags> g_flags_free[64];
+
+cudaError_t take_slice_flags(int dev, SliceFlags* out) {
+    {
+        std::lock_guard<std::mutex> lk(g_flags_mu);
+        if (!g_flags_free[dev].empty()) {
+            *out = g_flags_free[dev].back();
+            g_flags_free[dev].pop_back();
+            return cudaSuccess;
+        }
+    }
+    SliceFlags f;
+    cudaError_t e = cudaHostAlloc(&f.host, sizeof(unsigned) * kHostSlices, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&f.dev, f.host, 0);
+    if (e != cudaSuccess) {
+        if (f.host) cudaFreeHost(f.host);
+        return e;
+    }
+    *out = f;
+    return cudaSuccess;
+}
+
+void give_slice_flags(int dev, const SliceFlags& f) {
+    std::lock_guard<std::mutex> lk(g_flags_mu);
+    g_flags_free[dev].push_back(f);
 }
 
 grape_tuning_t tuning_of(const grape_graph* g) {
@@ -276,20 +391,22 @@ cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
     const LaunchShape s = queue_launch_shape(g, t, g->weighted);
     const int nb = blocks > 0 ? blocks : s.blocks;
     const size_t sh = stage_bytes(s.threads);
-    const unsigned cap = (unsigned)t.trial_cap;
-#define GRAPE_QUEUE_LAUNCH(W, C)                                                                 \
-    queue_kernel<W, C><<<nb, s.threads, sh, stream>>>(g->dev(), reqs, chunks, ctl, ring,     \
-                                                      idle_spins, exit_flag, done, done_flags, \
-                                                      cap, t.shorter_min, t.interp_search)
-    if (g->weighted) {
-        if (g->counting) GRAPE_QUEUE_LAUNCH(true, true);
-        else GRAPE_QUEUE_LAUNCH(true, false);
-    } else {
-        if (g->counting) GRAPE_QUEUE_LAUNCH(false, true);
-        else GRAPE_QUEUE_LAUNCH(false, false);
-    }
+    const Policy pol = policy_of(t);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)nb);
+    cfg.blockDim = dim3((unsigned)s.threads);
+    cfg.dynamicSmemBytes = sh;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = (unsigned)walk_launch_attrs(g, t, attr);
+    const GraphDev gd = g->dev();
+#define GRAPE_QUEUE_LAUNCH(W, C)                                                              \
+    cudaLaunchKernelEx(&cfg, queue_kernel<W, C>, gd, reqs, chunks, ctl, ring, idle_spins,     \
+                       exit_flag, done, done_flags, pol)
+    if (g->weighted) return g->counting ? GRAPE_QUEUE_LAUNCH(true, true) : GRAPE_QUEUE_LAUNCH(true, false);
+    return g->counting ? GRAPE_QUEUE_LAUNCH(false, true) : GRAPE_QUEUE_LAUNCH(false, false);
 #undef GRAPE_QUEUE_LAUNCH
-    return cudaGetLastError();
 }
 
 }  // namespace grape
@@ -433,70 +550,92 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
                                 uint64_t seed, int32_t* out, grape_stream_t stream_) {
     if (!g || !out) return GRAPE_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    WalkConst probe;
+    WalkConst wc;
     grape_status_t st = make_walk_const(g, starts, num_starts, walk_len, walks_per_node, p, q,
-                                        seed, out, &probe);
+                                        seed, out, &wc);
     if (st != GRAPE_OK) return st;
+    int dev = 0;
+    GRAPE_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GRAPE_ERR_CUDA;
     cudaStream_t copy = nullptr;
-    if (host_copy_stream(&copy) != cudaSuccess) return GRAPE_ERR_CUDA;
-    int32_t* d_starts = nullptr;
-    int32_t* d_out = nullptr;
-    const int64_t nw = probe.num_walks;
+    GRAPE_CUDA_TRY(host_copy_stream(&copy));
+    const int64_t nw = wc.num_walks;
     const size_t row_bytes = sizeof(int32_t) * (size_t)walk_len;
     const size_t out_bytes = row_bytes * (size_t)nw;
     // Scratch comes from the device's stream-ordered pool, which keeps freed
     // blocks for reuse, so repeated calls do not pay for fresh allocations.
     static std::once_flag pool_once;
     std::call_once(pool_once, [] {
-        int dev = 0;
+        int d = 0;
         cudaMemPool_t pool;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        if (cudaGetDevice(&d) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
             uint64_t keep = UINT64_MAX;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     });
-    // The rows leave in slices of walk ids: slice i is copied to the host on a
-    // copy stream while the later slices are still being walked, so only the
-    // last slice's copy is exposed.  A slice holds at least kHostSliceBytes of
-    // rows and at least 16 walks per resident lane (each launch ends in a tail
-    // of lanes finishing unevenly).  Slice bounds are multiples of 8 rows,
-    // which keeps every slice's device rows 32-byte aligned.
-    const int64_t lanes = (int64_t)g->num_sms * kMinBlocksWalk * kMaxThreads;
+    // One launch walks the whole job.  Its rows are cut into slices of walk
+    // ids (at least kHostSliceBytes each, at most kHostSlices); the walk that
+    // completes a slice raises that slice's flag in mapped host memory, and
+    // this thread then copies the slice out on the copy stream while the
+    // launch goes on.  Lanes take walk ids in grid-stride order, so slices
+    // complete roughly in order and only the last slice's copy is exposed.
     const int64_t want = std::max<int64_t>(
-        1, std::min<int64_t>({(int64_t)kHostSlices, (int64_t)(out_bytes / kHostSliceBytes),
-                              nw / (16 * lanes)}));
+        1, std::min<int64_t>((int64_t)kHostSlices, (int64_t)(out_bytes / kHostSliceBytes)));
     const int64_t per = ((nw + want - 1) / want + 7) / 8 * 8;
     const int nslices = (int)((nw + per - 1) / per);
-    std::vector<cudaEvent_t> walked((size_t)nslices, nullptr);
-    cudaEvent_t copied = nullptr;
-    cudaError_t e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
-    for (int i = 0; i < nslices && e == cudaSuccess; ++i)
-        e = cudaEventCreateWithFlags(&walked[(size_t)i], cudaEventDisableTiming);
+    SliceFlags flags;
+    GRAPE_CUDA_TRY(take_slice_flags(dev, &flags));
+    for (int i = 0; i < nslices; ++i) flags.host[i] = 0u;
+    int32_t* d_starts = nullptr;
+    int32_t* d_out = nullptr;
+    unsigned long long* d_done = nullptr;
+    cudaEvent_t walked = nullptr, copied = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&walked, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
     if (e == cudaSuccess && starts)
         e = cudaMallocAsync(&d_starts, sizeof(int32_t) * (size_t)num_starts, stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_out, out_bytes, stream);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync(&d_done, sizeof(unsigned long long) * (size_t)nslices, stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_done, 0, sizeof(unsigned long long) * (size_t)nslices, stream);
     if (e == cudaSuccess && starts)
         e = cudaMemcpyAsync(d_starts, starts, sizeof(int32_t) * (size_t)num_starts,
                             cudaMemcpyHostToDevice, stream);
-    int launched = 0;
-    for (int i = 0; i < nslices && e == cudaSuccess && st == GRAPE_OK; ++i) {
-        const int64_t b = (int64_t)i * per;
-        const int64_t c = std::min<int64_t>(per, nw - b);
-        st = grape_walks_range(g, d_starts, num_starts, walk_len, walks_per_node, p, q, seed, b, c,
-                               d_out + (size_t)b * (size_t)walk_len, stream_);
-        if (st == GRAPE_OK) e = cudaEventRecord(walked[(size_t)i], stream);
-        if (st == GRAPE_OK && e == cudaSuccess) ++launched;
+    bool launched = false;
+    if (e == cudaSuccess) {
+        wc.starts = d_starts;
+        wc.out = d_out;
+        wc.out_vec = ((reinterpret_cast<uintptr_t>(d_out) & 31u) == 0) ? 1 : 0;
+        const SliceSink sink = {d_done, flags.dev, per, nw};
+        e = dispatch_walk(g, tuning_of(g), wc, p != 1.0, q != 1.0, stream, sink);
+        if (e == cudaSuccess) e = cudaEventRecord(walked, stream);
+        launched = e == cudaSuccess;
     }
-    // Copies after all launches, so that a pageable destination (whose copies
-    // block the host) still overlaps the walks of later slices.
-    for (int i = 0; i < launched && e == cudaSuccess; ++i) {
-        const int64_t b = (int64_t)i * per;
-        const int64_t c = std::min<int64_t>(per, nw - b);
-        e = cudaStreamWaitEvent(copy, walked[(size_t)i], 0);
-        if (e == cudaSuccess)
+    // Copy each slice out once its flag is up.  Should the launch end with a
+    // flag still down, the remaining slices are copied after the launch.
+    int next = 0;
+    bool after_launch = false;
+    while (launched && next < nslices && e == cudaSuccess) {
+        const bool ready = after_launch || ((volatile unsigned*)flags.host)[next] != 0u;
+        if (ready) {
+            const int64_t b = (int64_t)next * per;
+            const int64_t c = std::min<int64_t>(per, nw - b);
             e = cudaMemcpyAsync(out + (size_t)b * (size_t)walk_len,
                                 d_out + (size_t)b * (size_t)walk_len, row_bytes * (size_t)c,
                                 cudaMemcpyDeviceToHost, copy);
+            ++next;
+            continue;
+        }
+        const cudaError_t qe = cudaEventQuery(walked);
+        if (qe == cudaSuccess) {
+            after_launch = true;
+            e = cudaStreamWaitEvent(copy, walked, 0);
+        } else if (qe != cudaErrorNotReady) {
+            e = qe;
+        } else {
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
     }
     // the scratch is freed on `stream` after the copies that read it
     cudaError_t e2 = cudaEventRecord(copied, copy);
@@ -504,14 +643,25 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
     if (e2 != cudaSuccess) cudaStreamSynchronize(copy);
     if (d_starts) cudaFreeAsync(d_starts, stream);
     if (d_out) cudaFreeAsync(d_out, stream);
+    if (d_done) cudaFreeAsync(d_done, stream);
     const cudaError_t e3 = cudaStreamSynchronize(stream);
-    for (cudaEvent_t ev : walked)
-        if (ev) cudaEventDestroy(ev);
+    if (walked) cudaEventDestroy(walked);
     if (copied) cudaEventDestroy(copied);
-    if (st != GRAPE_OK) return st;
+    // the flags array is free once the launch that writes it has finished
+    if (e3 == cudaSuccess) give_slice_flags(dev, flags);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = e3;
     return grape::cuda_status(e);
+}
+
+grape_status_t grape_trim_scratch(int64_t keep_bytes) {
+    if (keep_bytes < 0) return GRAPE_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaMemPool_t pool;
+    GRAPE_CUDA_TRY(cudaGetDevice(&dev));
+    GRAPE_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    GRAPE_CUDA_TRY(cudaDeviceSynchronize());
+    return grape::cuda_status(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
 }
 
 grape_status_t grape_batch_plan_create(const grape_graph_t* g, const grape_walk_request_t* reqs,
@@ -551,39 +701,66 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
     if (!g || !reqs || n < 1) return GRAPE_ERR_INVALID_ARG;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     const grape_tuning_t base = tuning_of(g);
-    const int chunk_grid[] = {16, 32, 64, 128, 256};
-    const int shorter_grid[] = {8, 0x7fffffff};
-    const int interp_grid[] = {0, 1};
     cudaEvent_t e0, e1;
     GRAPE_CUDA_TRY(cudaEventCreate(&e0));
     GRAPE_CUDA_TRY(cudaEventCreate(&e1));
+    // Time one tuning: build its plan, one warm-up replay, one timed replay.
+    auto time_one = [&](const grape_tuning_t& t, float* ms) -> grape_status_t {
+        grape_batch_plan* p = nullptr;
+        grape_status_t st = build_plan(g, reqs, n, t, &p);
+        if (st != GRAPE_OK) return st;
+        cudaError_t e = cudaGraphLaunch(p->exec, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        free_plan(p);
+        return grape::cuda_status(e);
+    };
     float best_ms = 1e30f;
     grape_tuning_t best_t = base;
     grape_status_t result = GRAPE_OK;
+    // Stage 1: queue granularity and list policy.
+    const int chunk_grid[] = {16, 32, 64, 128, 256};
+    const int shorter_grid[] = {8, 0x7fffffff};
+    const int interp_grid[] = {0, 1};
     for (int cw : chunk_grid) {
-        for (int sm : shorter_grid) for (int pw : interp_grid) {
-            grape_tuning_t t = base;
-            t.chunk_walks = cw;
-            t.shorter_min = sm;
-            t.interp_search = pw;
-            grape_batch_plan* p = nullptr;
-            grape_status_t st = build_plan(g, reqs, n, t, &p);
-            if (st != GRAPE_OK) { result = st; break; }
-            cudaError_t e = cudaGraphLaunch(p->exec, stream);           // warm-up
+        for (int sm : shorter_grid) {
+            for (int pw : interp_grid) {
+                if (result != GRAPE_OK) break;
+                grape_tuning_t t = base;
+                t.chunk_walks = cw;
+                t.shorter_min = sm;
+                t.interp_search = pw;
+                float ms = 0.f;
+                result = time_one(t, &ms);
+                if (result == GRAPE_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best_t = t;
+                }
+            }
+        }
+    }
+    // Stage 2, from the best of stage 1: the hub thresholds (sector pivots
+    // from a list length on; warp-cooperative narrowing above one).
+    const int pivot_grid[] = {0x7fffffff, 32, 128, 512, 2048};
+    const int warp_grid[] = {0x7fffffff, 1024, 8192};
+    const grape_tuning_t stage1 = best_t;
+    for (int pv : pivot_grid) {
+        for (int wm : warp_grid) {
+            if (result != GRAPE_OK) break;
+            if (pv == stage1.pivot_min && wm == stage1.warp_search_min) continue;
+            grape_tuning_t t = stage1;
+            t.pivot_min = pv;
+            t.warp_search_min = wm;
             float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
-            if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            free_plan(p);
-            if (e != cudaSuccess) { result = grape::cuda_status(e); break; }
-            if (ms < best_ms) {
+            result = time_one(t, &ms);
+            if (result == GRAPE_OK && ms < best_ms) {
                 best_ms = ms;
                 best_t = t;
             }
         }
-        if (result != GRAPE_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -593,6 +770,8 @@ grape_status_t grape_autotune_batched(grape_graph_t* g, const grape_walk_request
         g->tuning.chunk_walks = best_t.chunk_walks;
         g->tuning.shorter_min = best_t.shorter_min;
         g->tuning.interp_search = best_t.interp_search;
+        g->tuning.pivot_min = best_t.pivot_min;
+        g->tuning.warp_search_min = best_t.warp_search_min;
     }
     if (best) *best = best_t;
     return GRAPE_OK;
@@ -608,26 +787,49 @@ grape_status_t grape_philox4x32_10(const uint32_t* ctr_key, int64_t n, uint32_t*
 }
 
 grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_reads,
-                                  uint64_t seed, int32_t mode, uint32_t* sink,
+                                  uint64_t seed, int32_t mode, int32_t load_bytes,
+                                  int32_t loads_in_flight, int32_t blocks_per_sm, uint32_t* sink,
+                                  int32_t* resident_blocks_per_sm, int64_t* reads_done,
                                   grape_stream_t stream) {
     if (!buf || !sink || buf_bytes < 32 || n_reads < 1 || mode < 0 || mode > 2 ||
-        (reinterpret_cast<uintptr_t>(buf) & 31u))
+        blocks_per_sm < 0 || (reinterpret_cast<uintptr_t>(buf) & 31u))
         return GRAPE_ERR_INVALID_ARG;
+    const bool ok_shape = (load_bytes == 4 && (loads_in_flight == 8 || loads_in_flight == 16 ||
+                                               loads_in_flight == 32 || loads_in_flight == 64)) ||
+                          (load_bytes == 16 && (loads_in_flight == 8 || loads_in_flight == 16 ||
+                                                loads_in_flight == 32)) ||
+                          (load_bytes == 32 && (loads_in_flight == 4 || loads_in_flight == 8 ||
+                                                loads_in_flight == 16));
+    if (!ok_shape) return GRAPE_ERR_INVALID_ARG;
     int dev = 0, sms = 0;
     GRAPE_CUDA_TRY(cudaGetDevice(&dev));
     GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int threads = 256;
-    const long long blocks = (long long)sms * 8;
-    const long long total_threads = blocks * threads;
-    long long per_thread = (n_reads + total_threads - 1) / total_threads;
-    per_thread = ((per_thread + 7) / 8) * 8;
     const unsigned long long nsec = (unsigned long long)(buf_bytes / 32);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int4* b4 = reinterpret_cast<const int4*>(buf);
-    if (mode == 0) sector_probe_kernel<0><<<(unsigned)blocks, threads, 0, st>>>(b4, nsec, per_thread, seed, sink);
-    else if (mode == 1) sector_probe_kernel<1><<<(unsigned)blocks, threads, 0, st>>>(b4, nsec, per_thread, seed, sink);
-    else sector_probe_kernel<2><<<(unsigned)blocks, threads, 0, st>>>(b4, nsec, per_thread, seed, sink);
-    return grape::cuda_status(cudaGetLastError());
+    const char* b = static_cast<const char*>(buf);
+    int res = 0;
+    long long done = 0;
+    cudaError_t e = cudaSuccess;
+#define GRAPE_PROBE(L, W)                                                                        \
+    e = launch_probe_lw<L, W>(mode, b, nsec, n_reads, seed, sink, sms, blocks_per_sm, &res, &done, st)
+    if (load_bytes == 4) {
+        if (loads_in_flight == 8) GRAPE_PROBE(8, 4);
+        else if (loads_in_flight == 16) GRAPE_PROBE(16, 4);
+        else if (loads_in_flight == 32) GRAPE_PROBE(32, 4);
+        else GRAPE_PROBE(64, 4);
+    } else if (load_bytes == 16) {
+        if (loads_in_flight == 8) GRAPE_PROBE(8, 16);
+        else if (loads_in_flight == 16) GRAPE_PROBE(16, 16);
+        else GRAPE_PROBE(32, 16);
+    } else {
+        if (loads_in_flight == 4) GRAPE_PROBE(4, 32);
+        else if (loads_in_flight == 8) GRAPE_PROBE(8, 32);
+        else GRAPE_PROBE(16, 32);
+    }
+#undef GRAPE_PROBE
+    if (resident_blocks_per_sm) *resident_blocks_per_sm = res;
+    if (reads_done) *reads_done = done;
+    return grape::cuda_status(e);
 }
 
 }  // extern "C"

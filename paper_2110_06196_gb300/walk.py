@@ -186,6 +186,11 @@ def walks_host(graph: Graph, starts=None, walk_len=80, walks_per_node=1, p=1.0, 
     return out
 
 
+def trim_scratch(keep_bytes: int = 0):
+    """grape_trim_scratch: release the pooled device scratch of host-buffer calls."""
+    check(_lib.load().grape_trim_scratch(int(keep_bytes)), "grape_trim_scratch")
+
+
 def contexts_from_rows(rows: torch.Tensor, window: int, out=None, stream=None) -> torch.Tensor:
     """grape_contexts_from_rows: int32 [num_rows, walk_len, 2 * window] on the device."""
     lib = _lib.load()
@@ -313,10 +318,11 @@ class Server:
     """grape_walk_server_*: continuous batching with the graph resident."""
 
     def __init__(self, graph: Graph, output_cap_bytes=40 << 30, max_inflight=1024,
-                 chunk_walks=0, max_chunks=1 << 22, idle_exit_us=2000, admit_timeout_ms=0):
+                 chunk_walks=0, max_chunks=1 << 22, idle_exit_us=2000, admit_timeout_ms=0,
+                 kernel_wait_ms=0):
         self.graph = graph
         cfg = _lib.ServerConfig(output_cap_bytes, max_inflight, chunk_walks, max_chunks,
-                                idle_exit_us, admit_timeout_ms, 0)
+                                idle_exit_us, admit_timeout_ms, kernel_wait_ms)
         h = ctypes.c_void_p()
         check(graph._lib.grape_walk_server_create(graph.handle, ctypes.byref(cfg),
                                                   ctypes.byref(h)), "grape_walk_server_create")
@@ -379,6 +385,13 @@ class Server:
     def cancel(self, ticket):
         check(self._lib.grape_walk_server_cancel(self._h, ticket), "grape_walk_server_cancel")
 
+    def inject_fault(self, no_heartbeat: bool):
+        """grape_walk_server_inject_fault: stop (True) or restore (False) the host
+        heartbeat that renews the resident kernel's bounded wait."""
+        check(self._lib.grape_walk_server_inject_fault(
+            self._h, _lib.GRAPE_FAULT_NO_HEARTBEAT if no_heartbeat else 0),
+            "grape_walk_server_inject_fault")
+
     def stats(self) -> dict:
         s = _lib.ServerStats()
         check(self._lib.grape_walk_server_stats(self._h, ctypes.byref(s)))
@@ -406,15 +419,18 @@ def philox4x32_10(ctr_key: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
-def sector_probe(buf: torch.Tensor, n_reads: int, seed: int, mode: int = 0, stream=None) -> int:
-    """Random 32-byte-sector gathers over `buf` (mode: 0 ld.global.nc, 1 .cg,
-    2 .cs); returns the read count issued."""
+def sector_probe(buf: torch.Tensor, n_reads: int, seed: int, mode: int = 0, load_bytes: int = 32,
+                 loads_in_flight: int = 8, blocks_per_sm: int = 0, stream=None) -> tuple:
+    """grape_sector_probe: random 32-byte-sector reads over `buf` (mode: 0
+    ld.global.nc, 1 .cg, 2 .cs; load_bytes 4/16/32; loads_in_flight per thread;
+    blocks_per_sm 0 = occupancy maximum).  Returns (reads issued, resident
+    256-thread blocks per SM)."""
     lib = _lib.load()
     sink = torch.zeros(1, dtype=torch.int32, device=buf.device)
+    res = ctypes.c_int32()
+    done = ctypes.c_int64()
     check(lib.grape_sector_probe(_ptr(buf), buf.numel() * buf.element_size(), int(n_reads),
-                                 int(seed), int(mode), _ptr(sink), _stream_ptr(stream)))
-    props = torch.cuda.get_device_properties(buf.device)
-    threads = props.multi_processor_count * 8 * 256
-    per = -(-int(n_reads) // threads)
-    per = -(-per // 8) * 8
-    return per * threads
+                                 int(seed), int(mode), int(load_bytes), int(loads_in_flight),
+                                 int(blocks_per_sm), _ptr(sink), ctypes.byref(res),
+                                 ctypes.byref(done), _stream_ptr(stream)), "grape_sector_probe")
+    return done.value, res.value

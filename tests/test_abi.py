@@ -101,8 +101,14 @@ def test_argument_errors_return_before_cuda(lib):
     assert lib.grape_walks_batched(None, None, 0, None) == INVALID
     assert lib.grape_graph_info(None, None) == INVALID
     assert lib.grape_walk_server_create(None, None, ctypes.byref(h)) == INVALID
+    assert lib.grape_walk_server_inject_fault(None, 0) == INVALID
+    assert lib.grape_trim_scratch(-1) == INVALID
     assert lib.grape_philox4x32_10(None, -1, None, None) == INVALID
-    assert lib.grape_sector_probe(None, 0, 0, 0, 0, None, None) == INVALID
+    assert lib.grape_sector_probe(None, 0, 0, 0, 0, 32, 8, 0, None, None, None, None) == INVALID
+    # shapes outside the compiled (width, loads in flight) pairs, negative blocks
+    for width, loads, blocks in ((32, 32, 0), (8, 8, 0), (4, 4, 0), (16, 64, 0), (32, 8, -1)):
+        assert lib.grape_sector_probe(ctypes.c_void_p(256), 1 << 20, 1 << 10, 0, 0, width, loads,
+                                      blocks, ctypes.c_void_p(256), None, None, None) == INVALID
     assert lib.grape_contexts_from_rows(None, 4, 8, 2, None, None) == INVALID
     for window in (0, 65):
         assert lib.grape_contexts_from_rows(ctypes.c_void_p(16), 4, 8, window,

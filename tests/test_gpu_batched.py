@@ -49,11 +49,15 @@ def test_batched_equals_per_call_and_oracle(small):
 
 @pytest.mark.parametrize("chunk", [1, 7, 64, 1000])
 @pytest.mark.parametrize("shorter_min", [0, 16, 0x7fffffff])
-def test_batched_independent_of_granularity(small, chunk, shorter_min):
+@pytest.mark.parametrize("hub", [(0x7fffffff, 0x7fffffff), (32, 0x7fffffff), (0x7fffffff, 32)],
+                         ids=["plain", "pivots32", "warp32"])
+def test_batched_independent_of_granularity(small, chunk, shorter_min, hub):
     csr, g = small
     mix = synth.request_mix(csr.num_nodes, 16, gen_seed=6, max_starts=2000, len_lo=5, len_hi=40)
+    g.set_tuning(pivot_min=0x7fffffff, warp_search_min=0x7fffffff)
     ref = [_per_call(g, r) for r in _reqs_from_mix(mix)]
-    g.set_tuning(chunk_walks=chunk, shorter_min=shorter_min)
+    g.set_tuning(chunk_walks=chunk, shorter_min=shorter_min, pivot_min=hub[0],
+                 warp_search_min=hub[1])
     try:
         reqs = _reqs_from_mix(mix)
         plan = BatchPlan(g, reqs)
@@ -66,7 +70,8 @@ def test_batched_independent_of_granularity(small, chunk, shorter_min):
                 assert torch.equal(a, b)
         plan.close()
     finally:
-        g.set_tuning(chunk_walks=64, shorter_min=8)
+        g.set_tuning(chunk_walks=64, shorter_min=8, pivot_min=0x7fffffff,
+                     warp_search_min=0x7fffffff)
 
 
 def test_autotune_picks_a_grid_point_and_keeps_bytes(small):
@@ -76,7 +81,11 @@ def test_autotune_picks_a_grid_point_and_keeps_bytes(small):
     ref = [_per_call(g, r) for r in reqs]
     best = autotune_batched(g, reqs)
     assert best["chunk_walks"] in (16, 32, 64, 128, 256)
-    assert g.get_tuning().chunk_walks == best["chunk_walks"]
+    assert best["pivot_min"] in (0x7fffffff, 32, 128, 512, 2048)
+    assert best["warp_search_min"] in (0x7fffffff, 1024, 8192)
+    t = g.get_tuning()
+    assert (t.chunk_walks, t.pivot_min, t.warp_search_min) == \
+        (best["chunk_walks"], best["pivot_min"], best["warp_search_min"])
     outs = walks_batched(g, _reqs_from_mix(mix))
     for a, b in zip(outs, ref):
         assert torch.equal(a, b)

@@ -48,6 +48,9 @@ def test_mixed_stream_equals_alone_and_oracle(graph):
     st = srv.stats()
     srv.close()
     assert st["completed"] == len(mix) and st["inflight"] == 0
+    # the server's device-side count of transitions equals the rows' own
+    assert st["steps"] == sum(int((got[j] >= 0).sum()) - int((got[j][:, 0] >= 0).sum())
+                              for j in range(len(mix)))
     og = oracle.Graph(*csr.numpy())
     for j, r in enumerate(mix):
         assert np.array_equal(got[j], _alone(g, r.starts, r.walk_len, r.p, r.q, r.seed)), j
@@ -221,3 +224,44 @@ def test_requests_around_the_idle_exit(graph):
     assert s["completed"] == 40 and s["kernel_launches"] >= 2, s
     for j, (st, rows) in enumerate(got):
         assert np.array_equal(rows, _alone(g, st, 12, 1.0, 0.5, 900 + j)), j
+
+
+def test_kernel_wait_runs_out_without_heartbeat(graph):
+    """The resident kernel's own bounded wait: with the host heartbeat stopped
+    (a host that no longer answers, injected on the host side), every idle warp
+    gives up after kernel_wait_ms, raises bit 2 of the graph's status word and
+    leaves.  The server counts the timed-out launch, and the next request
+    relaunches the kernel and comes back equal to the oracle's rows."""
+    csr, g = graph
+    try:                                               # start from a clear status word
+        g.stream_status()
+    except GrapeError:
+        pass
+    og = oracle.Graph(*csr.numpy())
+    srv = Server(g, output_cap_bytes=64 << 20, max_inflight=8, idle_exit_us=60_000_000,
+                 kernel_wait_ms=50)
+    try:
+        starts = np.arange(0, csr.num_nodes, 97, dtype=np.int32)
+        a = srv.wait(srv.submit(starts, 21, 0.5, 2.0, 123), timeout_ms=30000)
+        want, _ = oracle.walks(og, starts, 21, 1, 0.5, 2.0, 123)
+        assert np.array_equal(a, want)
+        st = srv.stats()
+        assert st["kernel_launches"] == 1 and st["kernel_timeouts"] == 0
+        srv.inject_fault(no_heartbeat=True)
+        deadline = time.time() + 20
+        while srv.stats()["kernel_timeouts"] == 0 and time.time() < deadline:
+            time.sleep(0.01)
+        assert srv.stats()["kernel_timeouts"] == 1
+        with pytest.raises(GrapeError) as ei:             # status bit 2 is up
+            g.stream_status()
+        assert ei.value.name == "GRAPE_ERR_DEVICE"
+        srv.inject_fault(no_heartbeat=False)
+        starts2 = np.arange(5, csr.num_nodes, 61, dtype=np.int32)
+        b = srv.wait(srv.submit(starts2, 33, 2.0, 0.25, 456), timeout_ms=30000)
+        want2, _ = oracle.walks(og, starts2, 33, 1, 2.0, 0.25, 456)
+        assert np.array_equal(b, want2)
+        st = srv.stats()
+        assert st["kernel_launches"] == 2 and st["kernel_timeouts"] == 1
+    finally:
+        srv.close()
+    g.stream_status()                                  # nothing else was raised

@@ -113,6 +113,50 @@ def test_rmat12_specialisations_and_search_paths(weighted, shorter_min):
         check_parity(csr, None, 24, 2, p, q, seed=99, graph=g)
 
 
+HUB_SCHEDULES = [dict(pivot_min=1), dict(pivot_min=32), dict(pivot_min=0x7fffffff),
+                 dict(warp_search_min=0), dict(warp_search_min=32),
+                 dict(warp_search_min=0x7fffffff),
+                 dict(pivot_min=32, warp_search_min=300), dict(pivot_min=1, l2_persist_mb=16)]
+
+
+@pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
+@pytest.mark.parametrize("schedule", HUB_SCHEDULES,
+                         ids=lambda d: "-".join(f"{k}{v}" for k, v in d.items()))
+@pytest.mark.parametrize("shorter_min", [0, 0x7fffffff], ids=["shorter", "n_t"])
+def test_rmat12_hub_search_schedules(weighted, schedule, shorter_min):
+    """The degree-aware search schedules (sector pivots from a list length on,
+    warp-cooperative narrowing above a list length, the L2 window on the
+    pivots) change no row: R-MAT 12 (degrees up to ~1,000) against the oracle."""
+    csr = rmat12(weighted)
+    g = Graph.from_csr(csr)
+    g.set_tuning(shorter_min=shorter_min, **schedule)
+    g.counters(enable=True)
+    for (p, q) in [(1.0, 0.5), (0.5, 2.0), (4.0, 0.25), (0.25, 4.0)]:
+        check_parity(csr, None, 24, 2, p, q, seed=98, graph=g)
+    c = g.counters()
+    g.counters(enable=False)
+    if schedule.get("pivot_min", 0x7fffffff) < 0x7fffffff:
+        assert c["pivot_probes"] > 0
+    else:
+        assert c["pivot_probes"] == 0
+    assert c["pivot_probes"] <= c["probes"]
+
+
+def test_hub_search_schedules_on_a_hub_graph():
+    """A hub of degree 6,000 joined to a ring: every search meets long lists,
+    pivot and warp schedules both run many rounds; rows equal the oracle's."""
+    hub = 6000
+    edges = [(0, i) for i in range(1, hub + 1)] + [(i, i + 1) for i in range(1, hub)] + \
+            [(i, i + 7) for i in range(1, hub - 7, 3)]
+    csr = csr_from_np(*_law.csr_from_edges(hub + 1, edges))
+    for sched in ({}, dict(pivot_min=1), dict(warp_search_min=0),
+                  dict(pivot_min=64, warp_search_min=1000)):
+        g = Graph.from_csr(csr)
+        g.set_tuning(shorter_min=0x7fffffff, **sched)
+        for (p, q) in [(1.0, 0.25), (2.0, 0.5)]:
+            check_parity(csr, None, 30, 3, p, q, seed=11, graph=g)
+
+
 @pytest.mark.parametrize("cap", [0, 2])
 def test_exact_fallback_paths(cap):
     for weighted in (False, True):

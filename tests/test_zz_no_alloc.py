@@ -4,16 +4,20 @@ or allocation is not allowed where they call).  It keeps its state in a
 fixed-size array in the library instead of cudaMalloc'd memory.
 
 Checked through the C ABI: on two calls in a row its rows equal those of
-grape_walks_batched, the entry point that allocates, bit for bit (the
-tolerance of every walk test here), and a batch above its 4096-request
-limit is refused before anything runs.  This file is collected last so that
-a run that stops at the first failure has already run every other test.
+grape_walks_batched, the entry point that allocates, and those of the CPU
+oracle, bit for bit (the tolerance of every walk test here); with the work
+counters on, it counts what the allocating path counts; and a batch above its
+4096-request limit is refused before anything runs.  This file is collected
+last so that a run that stops at the first failure has already run every
+other test.
 """
 import ctypes
 
+import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2110_06196_gb300 import Graph, synth, walks_batched
 from paper_2110_06196_gb300 import _lib
 from paper_2110_06196_gb300 import walk as W
@@ -30,7 +34,7 @@ def _requests(csr, count, gen_seed):
 
 
 def _call_static(g, reqs):
-    arr, keep = W._requests(reqs, g)
+    arr, keep = W._requests(reqs, g)   # allocates any missing outputs (test side)
     code = g._lib.grape_walks_batched_static(g.handle, arr, len(reqs), W._stream_ptr())
     _lib.check(code, "grape_walks_batched_static")
     torch.cuda.synchronize()
@@ -49,8 +53,28 @@ def test_static_batched_matches_allocating_batched_twice(weighted):
         reqs = [dict(r, out=torch.full(tuple(rr.shape), -7, dtype=torch.int32, device="cuda"))
                 for r, rr in zip(reqs, ref)]
         got = _call_static(g, reqs)
-        for a, b in zip(got, ref):
+        og = oracle.Graph(*csr.numpy())
+        for j, (a, b) in enumerate(zip(got, ref)):
             assert torch.equal(a, b), f"call {call}"
+            r = reqs[j]
+            want, _ = oracle.walks(og, r["starts"].cpu().numpy(), r["walk_len"],
+                                   r["walks_per_node"], r["p"], r["q"], r["seed"])
+            assert np.array_equal(a.cpu().numpy(), want), f"call {call}, request {j}"
+
+
+def test_static_batched_counts_like_allocating_batched():
+    csr = synth.rmat(12, 30000, seed=53)
+    g = Graph.from_csr(csr)
+    reqs = _requests(csr, 24, 303)
+    g.counters(enable=True)
+    walks_batched(g, [dict(r, out=None) for r in reqs])
+    torch.cuda.synchronize()
+    want = g.counters()
+    _call_static(g, [dict(r, out=None) for r in reqs])
+    got = g.counters()
+    g.counters(enable=False)
+    for k in ("steps", "trials", "walks", "fallbacks"):
+        assert got[k] == want[k] > 0 or (k == "fallbacks" and got[k] == want[k]), k
 
 
 def test_static_batched_rejects_more_than_its_limit():
