@@ -99,6 +99,10 @@ def parse():
     ap.add_argument("--serve-saturation", type=int, default=400,
                     help="requests submitted at once for the served-vs-per-request ratio")
     ap.add_argument("--serve-graph", default="rmat26")
+    ap.add_argument("--serve-warm-requests", type=int, default=500,
+                    help="requests of the lowest rate served again with the kernel kept warm")
+    ap.add_argument("--serve-host-gib", type=int, default=16,
+                    help="pinned host arena for served rows (GiB)")
     return ap.parse_args()
 
 
@@ -963,24 +967,40 @@ def bench_batched(g, csr, dev):
 # ---------------------------------------------------------------------------
 # serving
 # ---------------------------------------------------------------------------
-class PinnedPool:
-    """Reusable pinned host buffers for served rows: a request takes the
-    smallest free buffer that holds its rows and gives it back once its rows
-    are counted, so a long arrival stream holds only what is in flight."""
+class PinnedArena:
+    """Served rows land in one pinned host arena allocated before the arrivals
+    start (a pinned allocation during the run can stall the device), carved
+    first-fit into per-request slices and given back once a request's rows
+    are counted.  Should the arena be full, a request gets a buffer of its own."""
 
-    def __init__(self):
-        self.free = []
+    def __init__(self, elems):
+        self.buf = torch.empty(elems, dtype=torch.int32, pin_memory=True)
+        self.free = [(0, elems)]                 # sorted (offset, length)
+        self.extra = 0
 
     def take(self, elems):
-        fit = [j for j, b in enumerate(self.free) if b.numel() >= elems]
-        if fit:
-            j = min(fit, key=lambda k: self.free[k].numel())
-            return self.free.pop(j)
-        size = 1 << max(20, (elems - 1).bit_length())
-        return torch.empty(size, dtype=torch.int32, pin_memory=True)
+        elems = (elems + 63) // 64 * 64
+        for i, (o, n) in enumerate(self.free):
+            if n >= elems:
+                self.free[i:i + 1] = [(o + elems, n - elems)] if n > elems else []
+                return ("arena", o, elems), self.buf[o:o + elems]
+        self.extra += 1
+        t = torch.empty(elems, dtype=torch.int32, pin_memory=True)
+        return ("own", 0, elems), t
 
-    def give(self, b):
-        self.free.append(b)
+    def give(self, key):
+        kind, o, n = key
+        if kind != "arena":
+            return
+        self.free.append((o, n))
+        self.free.sort()
+        merged = []
+        for a, m in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == a:
+                merged[-1] = (merged[-1][0], merged[-1][1] + m)
+            else:
+                merged.append((a, m))
+        self.free = merged
 
 
 def bench_serve(args, dev):
@@ -998,16 +1018,23 @@ def bench_serve(args, dev):
     deg = csr.degrees().cpu().numpy()
     del csr
     torch.cuda.empty_cache()
-    pool = PinnedPool()
+    pool = PinnedArena(args.serve_host_gib << 28)   # GiB of int32
     results = []
-    for ri, rate in enumerate(float(x) for x in args.serve_rates.split(",")):
-        count = int(min(args.serve_requests, max(1, rate * args.serve_max_s)))
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    # (rate index, idle exit): every rate with the default 2 ms idle exit, and
+    # the lowest rate again with the resident kernel kept warm between requests
+    runs = [(ri, 2000, args.serve_requests) for ri in range(len(rates))]
+    if args.serve_warm_requests > 0:
+        runs.append((0, 200_000, args.serve_warm_requests))
+    for ri, idle_us, nreq in runs:
+        rate = rates[ri]
+        count = int(min(nreq, max(1, rate * args.serve_max_s)))
         mix = synth.request_mix(n, count, gen_seed=77 + ri, max_starts=1_000_000, len_lo=20,
                                 len_hi=120, first_seed=10_000 * ri)
         arrivals = synth.poisson_arrivals(rate, len(mix), seed=5 + ri)
-        log(f"serving {len(mix)} requests at {rate:g}/s")
+        log(f"serving {len(mix)} requests at {rate:g}/s, idle exit {idle_us} us")
         srv = Server(g, output_cap_bytes=40 << 30, max_inflight=4096, chunk_walks=0,
-                     max_chunks=1 << 24, idle_exit_us=2000)
+                     max_chunks=1 << 24, idle_exit_us=idle_us)
         bufs = {}
         lat = []
         mu = threading.Lock()
@@ -1017,7 +1044,7 @@ def bench_serve(args, dev):
             while len(lat) < len(mix):
                 t, l, rows = srv.wait_any(timeout_ms=600_000)
                 with mu:
-                    j, buf = bufs.pop(t)
+                    j, key = bufs.pop(t)
                 lat.append(l)
                 if j % 50 == 0:                 # rows follow the job's step count
                     r = mix[j]
@@ -1025,7 +1052,8 @@ def bench_serve(args, dev):
                     got = int((rows >= 0).sum()) - int((rows[:, 0] >= 0).sum())
                     checked[0] += 1
                     checked[1] += int(got != want)
-                pool.give(buf)
+                with mu:
+                    pool.give(key)
 
         th = threading.Thread(target=collect)
         th.start()
@@ -1037,18 +1065,19 @@ def bench_serve(args, dev):
                 time.sleep(delay)
             elems = len(r.starts) * r.walk_len
             with mu:
-                buf = pool.take(elems)
+                key, buf = pool.take(elems)
             out = buf[:elems].view(len(r.starts), r.walk_len)
             t = srv.submit(r.starts, r.walk_len, r.p, r.q, r.seed, out=out)
             with mu:
-                bufs[t] = (j, buf)
+                bufs[t] = (j, key)
         th.join()
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
         lat_ms = np.array(lat) * 1e3
         offered = sum(int((deg[r.starts] > 0).sum()) * (r.walk_len - 1) for r in mix)
-        results.append({"rate_req_s": rate, "requests": len(mix), "wall_s": wall,
+        results.append({"rate_req_s": rate, "idle_exit_us": idle_us, "requests": len(mix),
+                        "wall_s": wall,
                         "steps_per_s": (st["steps"] - st0) / wall,
                         "offered_steps_per_s": offered / arrivals[-1],
                         "p50_ms": float(np.percentile(lat_ms, 50)),
@@ -1056,6 +1085,7 @@ def bench_serve(args, dev):
                         "max_ms": float(lat_ms.max()),
                         "kernel_launches": st["kernel_launches"],
                         "kernel_timeouts": st["kernel_timeouts"],
+                        "host_buffers_outside_arena": pool.extra,
                         "requests_step_checked": checked[0],
                         "requests_step_mismatch": checked[1]})
     # Saturation: every request of one mix at once through the server, then the

@@ -125,6 +125,7 @@ typedef struct grape_graph_info {
     int32_t undirected;      /* 1 when GRAPE_UNDIRECTED was given */
     int32_t pad;
     int64_t device_bytes;    /* device memory held by the graph */
+    int64_t edge_hash_bytes; /* of which the edge hash (0 when the graph has none) */
 } grape_graph_info_t;
 
 grape_status_t grape_graph_info(const grape_graph_t* graph, grape_graph_info_t* info);
@@ -152,15 +153,22 @@ typedef struct grape_tuning {
     int32_t pivot_min;        /* membership searches over lists of at least this many entries
                                  first search the list's sector pivots (the first id of every
                                  aligned 32-byte sector of the sorted rows, held beside them),
-                                 which leaves one sector of the list to read; INT32_MAX: never */
+                                 which leaves one sector of the list to read; INT32_MAX
+                                 (default): never */
     int32_t warp_search_min;  /* membership searches over lists of more than this many entries
                                  are first narrowed by the whole warp, 32 probes at once, one
-                                 lane's search at a time; INT32_MAX (default): never */
+                                 lane's search at a time; INT32_MAX (default): never.
+                                 pivot_min or warp_search_min below INT32_MAX selects kernels
+                                 that carry these schedules (general p, q specialisation); the
+                                 default kernels compile them out.  grape_walks_batched_static
+                                 does not use them. */
     int32_t l2_persist_mb;    /* 0: none; else ask the L2 to keep up to this many MB of the
                                  sector pivots resident (a persisting access-policy window on
                                  each walk launch; cudaLimitPersistingL2CacheSize, a per-context
                                  limit, is raised to it when this tuning is applied) */
-    int32_t pad;
+    int32_t edge_hash;        /* 1 (default): membership tests read the graph's edge hash, one
+                                 32-byte bucket, and search the rows only when that bucket
+                                 overflowed; 0: always search the rows */
 } grape_tuning_t;
 
 grape_status_t grape_graph_get_tuning(const grape_graph_t* graph, grape_tuning_t* tuning);
@@ -393,6 +401,7 @@ typedef struct grape_walk_counters {
     int64_t filtered;     /* membership tests settled by the neighbour filters of an
                              unweighted graph, without reading a row */
     int64_t pivot_probes; /* of the probes, 32-byte sectors of the sector pivots */
+    int64_t hash_probes;  /* of the probes, 32-byte buckets of the edge hash */
 } grape_walk_counters_t;
 
 grape_status_t grape_counters_enable(grape_graph_t* graph, int32_t enable);

@@ -34,14 +34,14 @@ class GrapeError(RuntimeError):
 class GraphInfo(ctypes.Structure):
     _fields_ = [("num_nodes", c_i64), ("num_entries", c_i64), ("max_degree", c_i32),
                 ("weighted", c_i32), ("undirected", c_i32), ("pad", c_i32),
-                ("device_bytes", c_i64)]
+                ("device_bytes", c_i64), ("edge_hash_bytes", c_i64)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("trial_cap", c_i64), ("shorter_min", c_i32), ("block_threads", c_i32),
                 ("blocks_per_sm", c_i32), ("chunk_walks", c_i32), ("interp_search", c_i32),
                 ("l2_fetch_bytes", c_i32), ("pivot_min", c_i32), ("warp_search_min", c_i32),
-                ("l2_persist_mb", c_i32), ("pad", c_i32)]
+                ("l2_persist_mb", c_i32), ("edge_hash", c_i32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
@@ -56,7 +56,7 @@ class WalkRequest(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("steps", c_i64), ("trials", c_i64), ("gathers", c_i64), ("searches", c_i64),
                 ("probes", c_i64), ("fallbacks", c_i64), ("walks", c_i64),
-                ("filtered", c_i64), ("pivot_probes", c_i64)]
+                ("filtered", c_i64), ("pivot_probes", c_i64), ("hash_probes", c_i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

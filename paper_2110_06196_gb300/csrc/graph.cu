@@ -193,11 +193,46 @@ __global__ void build_pivots_kernel(const int32_t* __restrict__ dsts, long long 
         piv[j] = j < sectors ? dsts[8 * j] : 0x7fffffff;
 }
 
+// Edge hash: one warp per row inserts the row's pairs (undirected graphs: the
+// pairs with v <= x, each pair once).  A slot is claimed by counting the
+// bucket's pairs; the ninth and later pairs of a bucket are not stored.
+__global__ void build_edge_hash_kernel(const int4* __restrict__ rec,
+                                       const int32_t* __restrict__ dsts, long long n, int k, int b,
+                                       int undirected, unsigned* __restrict__ table,
+                                       unsigned* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    const int K = 2 * k;
+    const unsigned long long rmask = (K - b >= 64) ? ~0ull : ((1ull << (K - b)) - 1ull);
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+        const int4 r = rec[v];
+        const long long a = (long long)(((unsigned long long)(unsigned)r.y << 32) | (unsigned)r.x);
+        for (long long e = a + lane; e < a + r.z; e += 32) {
+            const long long x = dsts[e];
+            if (undirected && x < v) continue;
+            const unsigned long long key = ((unsigned long long)v << k) | (unsigned long long)x;
+            const unsigned long long h = grape::edge_hash_mix(key, K);
+            const unsigned long long bucket = h >> (K - b);
+            const unsigned slot = atomicAdd(count + bucket, 1u);
+            if (slot < 8) table[8 * bucket + slot] = (unsigned)(h & rmask) + 1u;
+        }
+    }
+}
+
+__global__ void mark_edge_hash_overflow_kernel(unsigned* __restrict__ table,
+                                               const unsigned* __restrict__ count,
+                                               long long buckets) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < buckets;
+         i += (long long)gridDim.x * blockDim.x)
+        if (count[i] > 8) table[8 * i + 7] = grape::kHashOverflow;
+}
+
 void free_graph(grape_graph* g) {
     if (!g) return;
     cudaFree(g->rec);
     cudaFree(g->dsts);
     cudaFree(g->piv);
+    cudaFree(g->eh);
     cudaFree(g->fat);
     cudaFree(g->status);
     cudaFree(g->counters);
@@ -341,7 +376,52 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
             return grape::cuda_status(e);
         }
     }
-    // 4. Symmetry.
+    // 4. Edge hash (membership by one 32-byte read).  Sized for about 3.5
+    //    pairs per 8-slot bucket; the remainder must fit 31 bits.  Left out when
+    //    it would be larger than the sorted rows twice over.
+    if (num_entries > 0 && e == cudaSuccess) {
+        int k = 1;
+        while (k < 31 && (1LL << k) < num_nodes) ++k;
+        const int K = 2 * k;
+        const double pairs = g->undirected ? 0.5 * (double)num_entries : (double)num_entries;
+        int b = 0;
+        while (b < K && (double)(1ULL << b) * 3.5 < pairs) ++b;
+        if (K - b > 31) b = K - 31;
+        const long long buckets = 1LL << b;
+        const size_t bytes = sizeof(unsigned) * 8 * (size_t)buckets;
+        if (bytes <= std::max<size_t>(2 * sizeof(int32_t) * m_alloc, (size_t)64 << 20)) {
+            unsigned* count = nullptr;
+            e = cudaMalloc(&g->eh, bytes);
+            if (e == cudaSuccess) e = cudaMemsetAsync(g->eh, 0, bytes, stream);
+            if (e == cudaSuccess) e = cudaMallocAsync(&count, sizeof(unsigned) * (size_t)buckets, stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned) * (size_t)buckets, stream);
+            if (e == cudaSuccess) {
+                build_edge_hash_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
+                    g->rec, g->dsts, num_nodes, k, b, g->undirected ? 1 : 0, g->eh, count);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                mark_edge_hash_overflow_kernel<<<grid_for(g->num_sms, buckets, 256), 256, 0, stream>>>(
+                    g->eh, count, buckets);
+                e = cudaGetLastError();
+            }
+            if (count) {
+                const cudaError_t ef = cudaFreeAsync(count, stream);
+                if (e == cudaSuccess) e = ef;
+            }
+            if (e == cudaSuccess) {
+                g->eh_k = k;
+                g->eh_b = b;
+                g->eh_bytes = (int64_t)bytes;
+                g->device_bytes += (int64_t)bytes;
+            }
+        }
+        if (e != cudaSuccess) {
+            free_graph(g);
+            return grape::cuda_status(e);
+        }
+    }
+    // 5. Symmetry.
     if ((flags & GRAPE_VALIDATE) && g->undirected) {
         check_symmetry_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0, stream>>>(
             g->rec, g->dsts, g->fat, g->weighted ? 1 : 0, num_nodes, scratch + 1);
@@ -371,6 +451,7 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
     g->tuning.pivot_min = 0x7fffffff;
     g->tuning.warp_search_min = 0x7fffffff;
     g->tuning.l2_persist_mb = 0;
+    g->tuning.edge_hash = 1;
     *out = g;
     return GRAPE_OK;
 }
@@ -390,6 +471,7 @@ grape_status_t grape_graph_info(const grape_graph_t* g, grape_graph_info_t* info
     info->weighted = g->weighted ? 1 : 0;
     info->undirected = g->undirected ? 1 : 0;
     info->device_bytes = g->device_bytes;
+    info->edge_hash_bytes = g->eh_bytes;
     return GRAPE_OK;
 }
 
@@ -407,7 +489,8 @@ grape_status_t grape_graph_set_tuning(grape_graph_t* g, const grape_tuning_t* t)
         t->blocks_per_sm < 0 || t->chunk_walks < 1 || (t->interp_search != 0 && t->interp_search != 1) ||
         (t->l2_fetch_bytes != 0 && t->l2_fetch_bytes != 32 && t->l2_fetch_bytes != 64 &&
          t->l2_fetch_bytes != 128) ||
-        t->pivot_min < 1 || t->warp_search_min < 0 || t->l2_persist_mb < 0)
+        t->pivot_min < 1 || t->warp_search_min < 0 || t->l2_persist_mb < 0 ||
+        (t->edge_hash != 0 && t->edge_hash != 1))
         return GRAPE_ERR_INVALID_ARG;
     if (t->l2_persist_mb > 0) {
         // A per-context limit (released with the context): the L2 set-aside
@@ -466,6 +549,7 @@ grape_status_t grape_counters_read(grape_graph_t* g, grape_walk_counters_t* out)
     out->walks = (int64_t)c[grape::C_WALKS];
     out->filtered = (int64_t)c[grape::C_FILTERED];
     out->pivot_probes = (int64_t)c[grape::C_PIVOT_PROBES];
+    out->hash_probes = (int64_t)c[grape::C_HASH_PROBES];
     return GRAPE_OK;
 }
 

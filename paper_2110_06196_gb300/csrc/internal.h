@@ -21,6 +21,9 @@ struct grape_graph {
     int4* rec = nullptr;          // NodeRec[n]
     int32_t* dsts = nullptr;      // [m + 8]
     int32_t* piv = nullptr;       // [ceil(m / 8) + 8] sector pivots: piv[j] = dsts[8 j]
+    unsigned* eh = nullptr;       // edge hash [2^eh_b][8] (see walk_device.cuh), or nullptr
+    int eh_k = 0, eh_b = 0;
+    int64_t eh_bytes = 0;
     int4* fat = nullptr;          // [m] proposal entries (edge-inlined records)
     int* status = nullptr;        // device status word
     unsigned long long* counters = nullptr;  // [grape::C_COUNT]
@@ -35,6 +38,9 @@ struct grape_graph {
         g.dsts = dsts;
         g.fat = fat;
         g.piv = piv;
+        g.eh = eh;
+        g.eh_k = eh_k;
+        g.eh_b = eh_b;
         g.n = n;
         g.status = status;
         g.counters = counting ? counters : nullptr;
@@ -85,6 +91,7 @@ inline Policy policy_of(const grape_tuning_t& t) {
     p.interp_search = t.interp_search;
     p.pivot_min = t.pivot_min;
     p.warp_search_min = t.warp_search_min;
+    p.edge_hash = t.edge_hash;
     return p;
 }
 

@@ -48,7 +48,7 @@ struct __align__(16) NodeRec {
 
 enum Counter : int {
     C_STEPS = 0, C_TRIALS, C_GATHERS, C_SEARCHES, C_PROBES, C_FALLBACKS, C_WALKS, C_FILTERED,
-    C_PIVOT_PROBES, C_COUNT
+    C_PIVOT_PROBES, C_HASH_PROBES, C_COUNT
 };
 
 // Neighbour filters (unweighted graphs): a 96-bit one-hash Bloom filter of each
@@ -65,6 +65,29 @@ __host__ __device__ __forceinline__ bool filter_has(unsigned f0, unsigned f1, un
     return (word >> (b & 31)) & 1u;
 }
 
+// Edge hash: membership of a pair in the graph by one 32-byte read.
+// The key of a pair (a, b) is a * 2^k + b over K = 2k bits, with k bits per node
+// id and (undirected graphs) a <= b.  A bijection of the K-bit keys (xor-shifts
+// and multiplications by odd constants, modulo 2^K) spreads them; its top B
+// bits pick a bucket of eight 32-bit slots, and its low K - B bits, plus one,
+// are what the bucket stores (0 marks an empty slot).  Because the map is a
+// bijection, (bucket, remainder) identifies the pair exactly.  A bucket that
+// received more than eight pairs holds kHashOverflow in its last slot: a pair
+// not found there must be searched in the sorted rows.
+constexpr unsigned kHashOverflow = 0xffffffffu;
+
+__host__ __device__ __forceinline__ unsigned long long edge_hash_mix(unsigned long long x, int K) {
+    const unsigned long long mask = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
+    const int r = K / 2 + 1;
+    x &= mask;
+    x ^= x >> r;
+    x = (x * 0x9E3779B97F4A7C15ull) & mask;
+    x ^= x >> (K / 3 + 1);
+    x = (x * 0xD6E8FEB86659FD93ull) & mask;
+    x ^= x >> r;
+    return x;
+}
+
 struct GraphDev {
     const int4* rec;            // [n] NodeRec viewed as int4
     const int* dsts;            // [m + 8] sorted rows (membership search, fallback)
@@ -77,6 +100,9 @@ struct GraphDev {
     // sector pivots: piv[j] = dsts[8 j], the first id of each aligned 32-byte
     // sector of dsts ([ceil(m / 8) + 8], padded), or nullptr
     const int* piv;
+    // edge hash: [2^eh_b buckets][8] slots, or nullptr; eh_k bits per node id
+    const unsigned* eh;
+    int eh_k, eh_b;
     long long n;
     int* status;                // device status word (1 = bad start id)
     unsigned long long* counters;  // [C_COUNT] or nullptr
@@ -258,9 +284,13 @@ enum : unsigned {
     F_BISECT = 32u,       // the next probe bisects (the last interpolated one did not halve)
     F_PIV = 64u,          // the search runs over the list's sector pivots, not the list
     F_WARPQ = 128u,       // a new search waits for the warp to narrow its list (no probe yet)
+    F_HASH = 4u,          // the probe in flight is the pair's edge-hash bucket
     // bits 8-10: offset of the row's first entry inside its 32-byte sector
 };
 constexpr int F_PHASE_SHIFT = 8;
+static_assert(((F_ACC_IN | F_ACC_OUT | F_HASH | F_VEC | F_KEY_T | F_BISECT | F_PIV | F_WARPQ) &
+               (7u << F_PHASE_SHIFT)) == 0,
+              "lane flags must leave the output phase bits (8-10) alone");
 
 // Work counters, kept only by the counting instantiation of the kernels.
 template <bool ON>
@@ -899,7 +929,10 @@ struct Prop {
     bool acc_a, acc_b;    // accept if x in N(t) / if not (equal when the class is known)
 };
 
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
+// HUB: the instantiation that carries the optional search schedules for long
+// lists (sector pivots, warp-cooperative narrowing); without it they are
+// compiled out and those tuning knobs have no effect.
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed, bool HUB = false>
 struct Engine {
     const GraphDev& g;
     Feed& feed;
@@ -909,6 +942,7 @@ struct Engine {
     bool interp;                 // place probes by interpolation between the value bounds
     int warp_min;                // new searches over lists longer than this are first narrowed
                                  // by the whole warp (INT_MAX: never)
+    bool edge_hash;              // membership tests read the edge hash first (when the graph has one)
     int pivot_min;               // lists of at least this many entries are searched over their
                                  // sector pivots first (INT_MAX: never)
     Counts<COUNT>& cnt;
@@ -1033,19 +1067,45 @@ struct Engine {
         pe[0] = ld;
         pe[1] = ld2;
         L.x = p.x;
+        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT | F_PIV | F_WARPQ |
+                               F_HASH)) |
+                  (p.acc_a ? F_ACC_IN : 0u) | (p.acc_b ? F_ACC_OUT : 0u);
+        if (g.eh != nullptr && edge_hash) {
+            // the pair (t, x), smaller id first on undirected graphs: its bucket
+            // (as a slot index) and its tag
+            unsigned long long a = (unsigned)L.t, b = (unsigned)p.x;
+            if (g.undirected && b < a) {
+                const unsigned long long c = a;
+                a = b;
+                b = c;
+            }
+            const int K = 2 * g.eh_k;
+            const unsigned long long h = edge_hash_mix((a << g.eh_k) | b, K);
+            L.sb = (long long)(h >> (K - g.eh_b)) * 8;
+            L.vlo = (int)(h & ((1ull << (K - g.eh_b)) - 1ull)) + 1;
+            L.sn = 8;
+            L.flags |= F_HASH;
+            return;
+        }
+        begin_list_search(L, p.off, p.deg);
+    }
+
+    // The sorted-list search of the membership test: x in N(t), or (undirected
+    // graphs) t in N(x) when that row is the shorter (off_x, deg_x: x's row).
+    __device__ __forceinline__ void begin_list_search(Lane& L, long long off_x, int deg_x) {
         const TRec* tr = trec();
         const int deg_t = tr->deg_t;
-        const bool use_x = g.undirected && deg_t > shorter_min && p.deg < deg_t;
-        L.sb = use_x ? p.off : tr->off_t;
-        L.sn = use_x ? p.deg : deg_t;
-        L.flags = (L.flags & ~(F_ACC_IN | F_ACC_OUT | F_KEY_T | F_BISECT | F_PIV | F_WARPQ)) |
-                  (p.acc_a ? F_ACC_IN : 0u) | (p.acc_b ? F_ACC_OUT : 0u) | (use_x ? F_KEY_T : 0u);
+        const bool use_x = g.undirected && deg_t > shorter_min && deg_x < deg_t;
+        L.sb = use_x ? off_x : tr->off_t;
+        L.sn = use_x ? deg_x : deg_t;
+        L.flags = (L.flags & ~(F_KEY_T | F_BISECT | F_PIV | F_WARPQ | F_HASH)) |
+                  (use_x ? F_KEY_T : 0u);
         L.vlo = -1;                      // node ids lie in [0, n)
         L.vhi = (int)g.n;
         // A long list is first searched over its sector pivots: piv[j] for the
         // aligned sectors j0 < j <= j1 that start inside the list.  They bracket
         // the one sector that can hold the key, which is then read.
-        if (g.piv != nullptr && L.sn >= pivot_min) {
+        if (HUB && g.piv != nullptr && L.sn >= pivot_min) {
             const long long j0 = L.sb >> 3, j1 = (L.sb + L.sn - 1) >> 3;
             if (j1 > j0) {
                 L.flags |= F_PIV;
@@ -1072,6 +1132,13 @@ struct Engine {
     // of its pivots) around the position interpolated between the value bounds
     // (ids in a row are near-uniform after relabelling), or the midpoint.
     __device__ __forceinline__ const int4* probe_addr(Lane& L) {
+        L.phase = PH_SEARCH;
+        cnt.add(C_PROBES);
+        if (L.flags & F_HASH) {
+            L.sd = 0;
+            cnt.add(C_HASH_PROBES);
+            return reinterpret_cast<const int4*>(g.eh + L.sb);
+        }
         int pos = L.sn >> 1;
         if (interp && !(L.flags & F_BISECT)) {
             const int kk = (L.flags & F_KEY_T) ? L.t : L.x;
@@ -1079,10 +1146,8 @@ struct Engine {
             pos = min(max((int)(f * (float)L.sn), 0), max(L.sn - 1, 0));
         }
         const long long bi = (L.sb + pos) & ~7LL;
-        const bool piv = (L.flags & F_PIV) != 0;
+        const bool piv = HUB && (L.flags & F_PIV) != 0;
         L.sd = (int)(bi - L.sb);
-        L.phase = PH_SEARCH;
-        cnt.add(C_PROBES);
         if (piv) cnt.add(C_PIVOT_PROBES);
         return reinterpret_cast<const int4*>((piv ? g.piv : g.dsts) + bi);
     }
@@ -1191,7 +1256,24 @@ struct Engine {
                 probe = true;
             }
         } else if (srch) {
-            if (s_done && !found && (L.flags & F_PIV)) {
+            if (L.flags & F_HASH) {
+                // the pair's bucket: its tag decides; an overflowed bucket
+                // without it sends the test to the sorted rows
+                const unsigned tag = (unsigned)L.vlo;
+                const bool hit = (unsigned)ld.x == tag || (unsigned)ld.y == tag ||
+                                 (unsigned)ld.z == tag || (unsigned)ld.w == tag ||
+                                 (unsigned)ld2.x == tag || (unsigned)ld2.y == tag ||
+                                 (unsigned)ld2.z == tag || (unsigned)ld2.w == tag;
+                if (hit || (unsigned)ld2.w != kHashOverflow) {
+                    if ((L.flags & (hit ? F_ACC_IN : F_ACC_OUT)) != 0) take = true;
+                    else L.k++;
+                } else {
+                    const int4 a = parked_entry()[0];
+                    begin_list_search(L, (long long)(((unsigned long long)(unsigned)a.w << 32) |
+                                                     (unsigned)a.z), a.y);
+                    probe = true;
+                }
+            } else if (HUB && s_done && !found && (L.flags & F_PIV)) {
                 // The pivots place the key in one sector of the list: pivots
                 // before position lo (of the narrowed range) are below it.
                 const long long sector = L.sb - 1 + lo;
@@ -1250,7 +1332,7 @@ struct Engine {
         }
         const int4* addr = nullptr;
         if (probe) {
-            if (fresh && L.sn > warp_min && !(L.flags & F_PIV)) {
+            if (HUB && fresh && L.sn > warp_min && !(L.flags & (F_PIV | F_HASH))) {
                 L.flags |= F_WARPQ;          // warp_search issues this lane's first probe
                 L.phase = PH_SEARCH;
             } else {
@@ -1314,9 +1396,10 @@ struct Policy {
     int interp_search;
     int pivot_min;
     int warp_search_min;
+    int edge_hash;
 };
 
-template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, class Feed>
+template <bool WEIGHTED, bool HAS_P, bool HAS_Q, bool COUNT, bool HUB = false, class Feed>
 __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, const Policy& pol) {
     Lane L;
     L.t = -1;
@@ -1334,15 +1417,16 @@ __device__ __forceinline__ void walk_loop(const GraphDev& g, Feed& feed, const P
     cnt.clear();
     int4 ld = make_int4(0, 0, 0, 0);
     int4 ld2 = make_int4(0, 0, 0, 0);
-    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed> eng{g, feed, pol.trial_cap, pol.shorter_min,
+    Engine<WEIGHTED, HAS_P, HAS_Q, COUNT, Feed, HUB> eng{g, feed, pol.trial_cap, pol.shorter_min,
                                                     pol.interp_search != 0, pol.warp_search_min,
-                                                    pol.pivot_min, cnt, ld, ld2};
+                                                    pol.edge_hash != 0, pol.pivot_min, cnt, ld,
+                                                    ld2};
     bool have = false;
     while (true) {
         have = feed.refill(g, L, have, cnt);
         if (!__any_sync(FULL, have)) break;
         if (have) have = eng.step(L);
-        if (pol.warp_search_min != 0x7fffffff) eng.warp_search(L, have);
+        if (HUB && pol.warp_search_min != 0x7fffffff) eng.warp_search(L, have);
     }
     feed.drain();
     flush_counts(g, cnt);

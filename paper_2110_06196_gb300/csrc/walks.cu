@@ -29,12 +29,15 @@ constexpr int kMinBlocksQueue = 4;
 // Per-call walk kernel: the eight specialisations of GRAPE ("Implementation of
 // second-order RWs": p == 1, q == 1, weighted or not) as template arguments.
 // COUNT: the instantiation that also keeps the work counters.
-// SUSS: the approximated walks (GRAPE, Methods, "Approximated RWs"), only with
-// the general p, q specialisation.
-template <bool W, bool P, bool Q, bool COUNT, bool SUSS = false>
+// MODE 1: the approximated walks (GRAPE, Methods, "Approximated RWs"); MODE 2:
+// the exact walks with the optional long-list search schedules (sector pivots,
+// warp-cooperative narrowing); both only with the general p, q specialisation.
+constexpr int kExact = 0, kSuss = 1, kHub = 2;
+
+template <bool W, bool P, bool Q, bool COUNT, int MODE = kExact>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksWalk)
 walk_kernel(GraphDev g, WalkConst wc, RoundKeys rk, SliceSink sink, Policy pol) {
-    GridFeed<SUSS> f;
+    GridFeed<MODE == kSuss> f;
     f.wc = &wc;
     f.rk = &rk;
     f.sink = &sink;
@@ -45,11 +48,12 @@ walk_kernel(GraphDev g, WalkConst wc, RoundKeys rk, SliceSink sink, Policy pol) 
     }
     f.next = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     f.stride = (long long)gridDim.x * blockDim.x;
-    walk_loop<W, P, Q, COUNT>(g, f, pol);
+    walk_loop<W, P, Q, COUNT, MODE == kHub>(g, f, pol);
 }
 
 // Batched / served kernel: persistent grid draining a queue of walk ranges.
-template <bool W, bool COUNT>
+// HUB: with the optional long-list search schedules.
+template <bool W, bool COUNT, bool HUB = false>
 __global__ void __launch_bounds__(kMaxThreads, kMinBlocksQueue)
 queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned long long* ctl,
              unsigned long long ring, long long idle_spins, int* exit_flag,
@@ -70,7 +74,7 @@ queue_kernel(GraphDev g, const WalkConst* reqs, const Chunk* chunks, unsigned lo
     f.idle_polls = 0;
     if ((threadIdx.x & 31) == 0) *warp_ticket() = kNoTicket;
     __syncwarp();
-    walk_loop<W, true, true, COUNT>(g, f, pol);
+    walk_loop<W, true, true, COUNT, HUB>(g, f, pol);
 }
 
 __global__ void philox_kernel(const uint32_t* __restrict__ ck, long long n, uint32_t* __restrict__ out) {
@@ -196,7 +200,7 @@ int occupancy_blocks(K kernel, int threads) {
     return nb;
 }
 
-template <bool W, bool P, bool Q, bool C, bool S = false>
+template <bool W, bool P, bool Q, bool C, int S = kExact>
 cudaError_t launch_walk_c(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
                           const SliceSink& sink, cudaStream_t stream) {
     const int threads = std::min(t.block_threads, kMaxThreads);
@@ -227,15 +231,27 @@ cudaError_t launch_walk(const grape_graph* g, const grape_tuning_t& t, const Wal
 
 constexpr SliceSink kNoSlices = {nullptr, nullptr, 0, 0};
 
+// Does the tuning turn on a long-list search schedule (the HUB kernels)?
+bool hub_schedules(const grape_tuning_t& t) {
+    return t.pivot_min != 0x7fffffff || t.warp_search_min != 0x7fffffff;
+}
+
 cudaError_t dispatch_walk(const grape_graph* g, const grape_tuning_t& t, const WalkConst& wc,
                           bool has_p, bool has_q, cudaStream_t s,
                           const SliceSink& k = kNoSlices) {
     if (wc.suss_k > 0) {
         if (g->weighted)
-            return g->counting ? launch_walk_c<true, true, true, true, true>(g, t, wc, k, s)
-                               : launch_walk_c<true, true, true, false, true>(g, t, wc, k, s);
-        return g->counting ? launch_walk_c<false, true, true, true, true>(g, t, wc, k, s)
-                           : launch_walk_c<false, true, true, false, true>(g, t, wc, k, s);
+            return g->counting ? launch_walk_c<true, true, true, true, kSuss>(g, t, wc, k, s)
+                               : launch_walk_c<true, true, true, false, kSuss>(g, t, wc, k, s);
+        return g->counting ? launch_walk_c<false, true, true, true, kSuss>(g, t, wc, k, s)
+                           : launch_walk_c<false, true, true, false, kSuss>(g, t, wc, k, s);
+    }
+    if (hub_schedules(t)) {
+        if (g->weighted)
+            return g->counting ? launch_walk_c<true, true, true, true, kHub>(g, t, wc, k, s)
+                               : launch_walk_c<true, true, true, false, kHub>(g, t, wc, k, s);
+        return g->counting ? launch_walk_c<false, true, true, true, kHub>(g, t, wc, k, s)
+                           : launch_walk_c<false, true, true, false, kHub>(g, t, wc, k, s);
     }
     if (g->weighted) {
         if (has_p) return has_q ? launch_walk<true, true, true>(g, t, wc, k, s)
@@ -401,11 +417,21 @@ cudaError_t launch_queue_kernel(const grape_graph* g, const grape_tuning_t& t,
     cfg.attrs = attr;
     cfg.numAttrs = (unsigned)walk_launch_attrs(g, t, attr);
     const GraphDev gd = g->dev();
-#define GRAPE_QUEUE_LAUNCH(W, C)                                                              \
-    cudaLaunchKernelEx(&cfg, queue_kernel<W, C>, gd, reqs, chunks, ctl, ring, idle_spins,     \
+#define GRAPE_QUEUE_LAUNCH(W, C, H)                                                           \
+    cudaLaunchKernelEx(&cfg, queue_kernel<W, C, H>, gd, reqs, chunks, ctl, ring, idle_spins,  \
                        exit_flag, done, done_flags, pol)
-    if (g->weighted) return g->counting ? GRAPE_QUEUE_LAUNCH(true, true) : GRAPE_QUEUE_LAUNCH(true, false);
-    return g->counting ? GRAPE_QUEUE_LAUNCH(false, true) : GRAPE_QUEUE_LAUNCH(false, false);
+    if (hub_schedules(t)) {
+        if (g->weighted)
+            return g->counting ? GRAPE_QUEUE_LAUNCH(true, true, true)
+                               : GRAPE_QUEUE_LAUNCH(true, false, true);
+        return g->counting ? GRAPE_QUEUE_LAUNCH(false, true, true)
+                           : GRAPE_QUEUE_LAUNCH(false, false, true);
+    }
+    if (g->weighted)
+        return g->counting ? GRAPE_QUEUE_LAUNCH(true, true, false)
+                           : GRAPE_QUEUE_LAUNCH(true, false, false);
+    return g->counting ? GRAPE_QUEUE_LAUNCH(false, true, false)
+                       : GRAPE_QUEUE_LAUNCH(false, false, false);
 #undef GRAPE_QUEUE_LAUNCH
 }
 

@@ -113,10 +113,12 @@ def test_rmat12_specialisations_and_search_paths(weighted, shorter_min):
         check_parity(csr, None, 24, 2, p, q, seed=99, graph=g)
 
 
-HUB_SCHEDULES = [dict(pivot_min=1), dict(pivot_min=32), dict(pivot_min=0x7fffffff),
-                 dict(warp_search_min=0), dict(warp_search_min=32),
-                 dict(warp_search_min=0x7fffffff),
-                 dict(pivot_min=32, warp_search_min=300), dict(pivot_min=1, l2_persist_mb=16)]
+HUB_SCHEDULES = [dict(edge_hash=0, pivot_min=1), dict(edge_hash=0, pivot_min=32),
+                 dict(edge_hash=0, pivot_min=0x7fffffff),
+                 dict(edge_hash=0, warp_search_min=0), dict(edge_hash=0, warp_search_min=32),
+                 dict(edge_hash=0, pivot_min=32, warp_search_min=300),
+                 dict(edge_hash=0, pivot_min=1, l2_persist_mb=16),
+                 dict(edge_hash=1), dict(edge_hash=1, pivot_min=1)]
 
 
 @pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
@@ -135,11 +137,14 @@ def test_rmat12_hub_search_schedules(weighted, schedule, shorter_min):
         check_parity(csr, None, 24, 2, p, q, seed=98, graph=g)
     c = g.counters()
     g.counters(enable=False)
-    if schedule.get("pivot_min", 0x7fffffff) < 0x7fffffff:
-        assert c["pivot_probes"] > 0
+    if schedule.get("edge_hash", 1):
+        # every membership test reads its pair's bucket first
+        assert c["hash_probes"] == c["searches"] > 0
+    elif schedule.get("pivot_min", 0x7fffffff) < 0x7fffffff:
+        assert c["pivot_probes"] > 0 and c["hash_probes"] == 0
     else:
-        assert c["pivot_probes"] == 0
-    assert c["pivot_probes"] <= c["probes"]
+        assert c["pivot_probes"] == 0 and c["hash_probes"] == 0
+    assert c["pivot_probes"] + c["hash_probes"] <= c["probes"]
 
 
 def test_hub_search_schedules_on_a_hub_graph():
@@ -149,12 +154,67 @@ def test_hub_search_schedules_on_a_hub_graph():
     edges = [(0, i) for i in range(1, hub + 1)] + [(i, i + 1) for i in range(1, hub)] + \
             [(i, i + 7) for i in range(1, hub - 7, 3)]
     csr = csr_from_np(*_law.csr_from_edges(hub + 1, edges))
-    for sched in ({}, dict(pivot_min=1), dict(warp_search_min=0),
-                  dict(pivot_min=64, warp_search_min=1000)):
+    for sched in ({}, dict(edge_hash=0), dict(edge_hash=0, pivot_min=1),
+                  dict(edge_hash=0, warp_search_min=0),
+                  dict(edge_hash=0, pivot_min=64, warp_search_min=1000)):
         g = Graph.from_csr(csr)
         g.set_tuning(shorter_min=0x7fffffff, **sched)
         for (p, q) in [(1.0, 0.25), (2.0, 0.5)]:
             check_parity(csr, None, 30, 3, p, q, seed=11, graph=g)
+
+
+def _edge_hash_bucket(a, b, n, pairs):
+    """The bucket the library's edge hash gives the pair {a, b} (the table's
+    layout rule, restated for the test: k bits per id, about 3.5 pairs per
+    8-slot bucket, the mixing bijection of 2k-bit keys)."""
+    k = 1
+    while k < 31 and (1 << k) < n:
+        k += 1
+    K = 2 * k
+    bb = 0
+    while bb < K and (1 << bb) * 3.5 < pairs:
+        bb += 1
+    bb = max(bb, K - 31)
+    mask = (1 << K) - 1
+    x = ((min(a, b) << k) | max(a, b)) & mask
+    x ^= x >> (K // 2 + 1)
+    x = (x * 0x9E3779B97F4A7C15) & mask
+    x ^= x >> (K // 3 + 1)
+    x = (x * 0xD6E8FEB86659FD93) & mask
+    x ^= x >> (K // 2 + 1)
+    return x >> (K - bb)
+
+
+def test_edge_hash_overflowed_bucket_falls_back_to_the_rows():
+    """14 pairs that share one 8-slot bucket of the edge hash, among 180 other
+    pairs: tests on pairs the bucket could not hold read the sorted rows, and
+    every row equals the oracle's."""
+    n, total = 64, 190
+    from itertools import combinations
+    allp = [(a, b) for a, b in combinations(range(n), 2)]
+    by = {}
+    for a, b in allp:
+        by.setdefault(_edge_hash_bucket(a, b, n, total), []).append((a, b))
+    crowd = max(by.values(), key=len)[:14]
+    assert len(crowd) == 14
+    rng = np.random.default_rng(3)
+    rest = [allp[i] for i in rng.permutation(len(allp))]
+    edges = list(crowd)
+    for pr in rest:
+        if len(edges) == total:
+            break
+        if pr not in crowd:
+            edges.append(pr)
+    csr = csr_from_np(*_law.csr_from_edges(n, edges))
+    g = Graph.from_csr(csr)
+    assert g.info()["edge_hash_bytes"] > 0
+    g.counters(enable=True)
+    for (p, q) in [(1.0, 0.25), (0.5, 2.0), (4.0, 0.25)]:
+        check_parity(csr, None, 40, 20, p, q, seed=17, graph=g)
+    c = g.counters()
+    g.counters(enable=False)
+    assert c["hash_probes"] == c["searches"] > 0
+    assert c["probes"] > c["hash_probes"]          # some tests went on to the rows
 
 
 @pytest.mark.parametrize("cap", [0, 2])
