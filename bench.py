@@ -484,7 +484,8 @@ def counters_view(cnt):
             "filtered_per_step": cnt["filtered"] / st,
             "searches_per_step": cnt["searches"] / st,
             "probes_per_search": cnt["probes"] / max(1, cnt["searches"]),
-            "probes_per_step": cnt["probes"] / st, "fallbacks": cnt["fallbacks"]}
+            "probes_per_step": cnt["probes"] / st,
+            "hash_probes_per_step": cnt.get("hash_probes", 0) / st, "fallbacks": cnt["fallbacks"]}
 
 
 def run_ours(args, dist):
@@ -598,21 +599,25 @@ def config_of(workload, job, rows, steps_per_launch, num_entries, world):
 
 def bench_hub_schedules(g, job, n, rows, out, dev, plain_ms, reps=3):
     """The headline job under each membership-search schedule (the graph's
-    tuning knobs): sector pivots from a list length on, the same with an L2
-    persisting window over the pivots, and warp-cooperative narrowing of long
-    lists.  Launch time (CUDA events), probes per step (counting launch), and
-    the rows' signature against the plain schedule's."""
+    tuning knobs): the edge hash (default); the sorted-row search alone; with
+    sector pivots from a list length on, with an L2 persisting window over the
+    pivots, and with warp-cooperative narrowing of long lists.  Launch time
+    (CUDA events), probes per step (counting launch), and the rows' signature
+    against the default schedule's."""
     INT = 0x7fffffff
     base = g.get_tuning().as_dict()
     stream = torch.cuda.current_stream(dev)
     ref = row_signature(out)
-    res = [{"schedule": "per-lane interpolation (default)", "ms_per_launch": plain_ms}]
-    variants = [("sector pivots, lists >= 512", dict(pivot_min=512)),
-                ("sector pivots, lists >= 128", dict(pivot_min=128)),
-                ("sector pivots >= 128 + 96 MB L2 persisting window on them",
-                 dict(pivot_min=128, l2_persist_mb=96)),
-                ("warp-cooperative narrowing, lists > 8192", dict(warp_search_min=8192)),
-                ("warp-cooperative narrowing, lists > 1024", dict(warp_search_min=1024))]
+    res = [{"schedule": "edge hash, one bucket per membership test (default)",
+            "ms_per_launch": plain_ms}]
+    variants = [("sorted-row search, per-lane interpolation", dict(edge_hash=0)),
+                ("sorted rows + sector pivots, lists >= 512", dict(edge_hash=0, pivot_min=512)),
+                ("sorted rows + sector pivots >= 128 + 96 MB L2 persisting window on them",
+                 dict(edge_hash=0, pivot_min=128, l2_persist_mb=96)),
+                ("sorted rows + warp-cooperative narrowing, lists > 8192",
+                 dict(edge_hash=0, warp_search_min=8192)),
+                ("sorted rows + warp-cooperative narrowing, lists > 1024",
+                 dict(edge_hash=0, warp_search_min=1024))]
     for name, kw in variants:
         t = dict(base)
         t.update(kw)
@@ -634,7 +639,8 @@ def bench_hub_schedules(g, job, n, rows, out, dev, plain_ms, reps=3):
         st = max(1, c["steps"])
         res.append({"schedule": name, "tuning": kw, "ms_per_launch": e0.elapsed_time(e1) / reps,
                     "rows_equal_default": same, "probes_per_step": c["probes"] / st,
-                    "pivot_probes_per_step": c["pivot_probes"] / st})
+                    "pivot_probes_per_step": c["pivot_probes"] / st,
+                    "hash_probes_per_step": c["hash_probes"] / st})
     base.update(l2_persist_mb=0)
     g.set_tuning(**base)
     return res
@@ -864,6 +870,19 @@ def bench_cumsum(g, job, n, dev, walks_n=1 << 20, reps=3):
             ms = e0.elapsed_time(e1) / reps
             steps = count_steps(out)
             entry[name] = {"ms_per_launch": ms, "steps_per_s": steps / ms * 1e3}
+        # the cumulative-sum sampler with its membership tests on the sorted rows
+        t0 = g.get_tuning().edge_hash
+        g.set_tuning(edge_hash=0)
+        walks_cumsum(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        walks_cumsum(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        g.set_tuning(edge_hash=t0)
+        ms = e0.elapsed_time(e1)
+        entry["cumsum_sorted_row_membership"] = {"ms_per_launch": ms,
+                                                 "steps_per_s": count_steps(out) / ms * 1e3}
         res.append(entry)
     del out
     torch.cuda.empty_cache()

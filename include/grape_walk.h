@@ -662,16 +662,20 @@ grape_status_t grape_philox4x32_10(const uint32_t* ctr_key, int64_t n, uint32_t*
  * (seed, thread, read).  The launch shape is swept by the caller:
  *   mode: the load's cache path: 0 read-only through L1 (ld.global.nc),
  *       1 L2 only (ld.global.cg), 2 streaming (ld.global.cs);
- *   load_bytes: 4, 16 or 32 (a 32-, 128- or 256-bit load at the sector start);
+ *   load_bytes: 4, 16 or 32 (a 32-, 128- or 256-bit load at the sector start),
+ *       or 64 (both sectors of a random aligned 64-byte block, two 256-bit
+ *       loads; a read then counts as two sectors);
  *   loads_in_flight: independent reads each thread issues before it waits:
  *       8/16/32/64 for 4-byte loads, 8/16/32 for 16-byte loads, 4/8/16 for
- *       32-byte loads; other pairs return GRAPE_ERR_INVALID_ARG;
+ *       32-byte loads, 4/8 for 64-byte reads; other pairs return
+ *       GRAPE_ERR_INVALID_ARG;
  *   blocks_per_sm: resident 256-thread blocks per SM, capped at what the
  *       kernel's registers allow (0: that maximum).
  * n_reads is rounded up to whole rounds of the grid.  The XOR of what was read
  * lands in *sink (device uint32) so nothing is optimised away.
- * *resident_blocks_per_sm and *reads_done (host, either may be NULL) receive
- * the blocks per SM launched and the number of reads enqueued.
+ * buf_bytes >= 64.  *resident_blocks_per_sm and *reads_done (host, either may
+ * be NULL) receive the blocks per SM launched and the number of 32-byte
+ * sectors the launch reads.
  */
 grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_reads,
                                   uint64_t seed, int32_t mode, int32_t load_bytes,

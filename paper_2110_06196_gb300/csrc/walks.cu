@@ -19,7 +19,10 @@ constexpr int kMaxThreads = 256;
 // Resident blocks per SM the register allocation is held to: more warps keep
 // more independent gathers in flight, which is what this latency-bound loop
 // needs (4 x 256 threads -> at most 64 registers per thread).
-constexpr int kMinBlocksWalk = 4;
+#ifndef GRAPE_MIN_BLOCKS_WALK
+#define GRAPE_MIN_BLOCKS_WALK 4
+#endif
+constexpr int kMinBlocksWalk = GRAPE_MIN_BLOCKS_WALK;
 constexpr int kMinBlocksQueue = 4;
 
 // ---------------------------------------------------------------------------
@@ -137,21 +140,30 @@ __device__ __forceinline__ void probe_load(const char* p, unsigned* w) {
     }
 }
 
+// WIDTH 64: both 32-byte sectors of a random aligned 64-byte block (two
+// 256-bit loads), to see what the second sector of a DRAM burst costs.
 template <int LOADS, int WIDTH, int MODE>
 __global__ void __launch_bounds__(256)
 sector_probe_kernel(const char* __restrict__ buf, unsigned long long nsec, long long rounds,
                     unsigned long long seed, uint32_t* sink) {
     constexpr int WORDS = WIDTH / 4;
+    constexpr int STRIDE = WIDTH == 64 ? 64 : 32;
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
     unsigned long long ctr = probe_mix(seed ^ (tid * 0x9E3779B97F4A7C15ull));
+    const unsigned long long nblk = WIDTH == 64 ? nsec / 2 : nsec;
     unsigned acc = 0;
     for (long long j = 0; j < rounds; ++j) {
         unsigned v[LOADS * WORDS];
 #pragma unroll
         for (int u = 0; u < LOADS; ++u) {
             ctr += 0x9E3779B97F4A7C15ull;
-            const unsigned long long idx = __umul64hi(probe_mix(ctr), nsec);
-            probe_load<WIDTH, MODE>(buf + 32 * idx, v + u * WORDS);
+            const unsigned long long idx = __umul64hi(probe_mix(ctr), nblk);
+            if (WIDTH == 64) {
+                probe_load<32, MODE>(buf + STRIDE * idx, v + u * WORDS);
+                probe_load<32, MODE>(buf + STRIDE * idx + 32, v + u * WORDS + 8);
+            } else {
+                probe_load<WIDTH, MODE>(buf + STRIDE * idx, v + u * WORDS);
+            }
         }
         // The fold mixes in a value read after the last load is issued, so no
         // fold can start before every read of the round is in flight.
@@ -180,7 +192,7 @@ cudaError_t launch_probe_lw(int mode, const char* buf, unsigned long long nsec, 
     const long long rounds = std::max<long long>(1, (n_reads + threads * LOADS - 1) / (threads * LOADS));
     k<<<(unsigned)(num_sms * per_sm), 256, 0, st>>>(buf, nsec, rounds, seed, sink);
     if (resident) *resident = per_sm;
-    if (reads_done) *reads_done = rounds * threads * LOADS;
+    if (reads_done) *reads_done = rounds * threads * LOADS * (WIDTH == 64 ? 2 : 1);
     return cudaGetLastError();
 }
 
@@ -271,20 +283,30 @@ bool valid_pq(double x) { return std::isfinite(x) && x > 0.0; }
 constexpr int kHostSlices = 64;
 constexpr size_t kHostSliceBytes = 64u << 20;
 
-// One non-blocking stream per device for grape_walks_host's copies out.
-cudaError_t host_copy_stream(cudaStream_t* out) {
+// Non-blocking streams per device for grape_walks_host's copies out; slices
+// go round-robin over them.  While the walks run, the copies compete with the
+// walk kernel's random reads for the memory system; on the R-MAT scale-24 job
+// two streams measured 380-425 ms a call against 690-750 ms for one or four.
+#ifndef GRAPE_COPY_STREAMS
+#define GRAPE_COPY_STREAMS 2
+#endif
+constexpr int kCopyStreams = GRAPE_COPY_STREAMS;
+
+cudaError_t host_copy_streams(cudaStream_t* out) {
     static std::mutex mu;
-    static cudaStream_t streams[64] = {};
+    static cudaStream_t streams[64][kCopyStreams] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
-    if (!streams[dev]) {
-        e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
-        if (e != cudaSuccess) return e;
+    for (int i = 0; i < kCopyStreams; ++i) {
+        if (!streams[dev][i]) {
+            e = cudaStreamCreateWithFlags(&streams[dev][i], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+        }
+        out[i] = streams[dev][i];
     }
-    *out = streams[dev];
     return cudaSuccess;
 }
 
@@ -583,8 +605,8 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
     int dev = 0;
     GRAPE_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return GRAPE_ERR_CUDA;
-    cudaStream_t copy = nullptr;
-    GRAPE_CUDA_TRY(host_copy_stream(&copy));
+    cudaStream_t copy[kCopyStreams] = {};
+    GRAPE_CUDA_TRY(host_copy_streams(copy));
     const int64_t nw = wc.num_walks;
     const size_t row_bytes = sizeof(int32_t) * (size_t)walk_len;
     const size_t out_bytes = row_bytes * (size_t)nw;
@@ -615,9 +637,10 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
     int32_t* d_starts = nullptr;
     int32_t* d_out = nullptr;
     unsigned long long* d_done = nullptr;
-    cudaEvent_t walked = nullptr, copied = nullptr;
+    cudaEvent_t walked = nullptr, copied[kCopyStreams] = {};
     cudaError_t e = cudaEventCreateWithFlags(&walked, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
+    for (int i = 0; i < kCopyStreams && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
     if (e == cudaSuccess && starts)
         e = cudaMallocAsync(&d_starts, sizeof(int32_t) * (size_t)num_starts, stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_out, out_bytes, stream);
@@ -649,14 +672,15 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
             const int64_t c = std::min<int64_t>(per, nw - b);
             e = cudaMemcpyAsync(out + (size_t)b * (size_t)walk_len,
                                 d_out + (size_t)b * (size_t)walk_len, row_bytes * (size_t)c,
-                                cudaMemcpyDeviceToHost, copy);
+                                cudaMemcpyDeviceToHost, copy[next % kCopyStreams]);
             ++next;
             continue;
         }
         const cudaError_t qe = cudaEventQuery(walked);
         if (qe == cudaSuccess) {
             after_launch = true;
-            e = cudaStreamWaitEvent(copy, walked, 0);
+            for (int i = 0; i < kCopyStreams && e == cudaSuccess; ++i)
+                e = cudaStreamWaitEvent(copy[i], walked, 0);
         } else if (qe != cudaErrorNotReady) {
             e = qe;
         } else {
@@ -664,15 +688,22 @@ grape_status_t grape_walks_host(const grape_graph_t* g, const int32_t* starts, i
         }
     }
     // the scratch is freed on `stream` after the copies that read it
-    cudaError_t e2 = cudaEventRecord(copied, copy);
-    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(stream, copied, 0);
-    if (e2 != cudaSuccess) cudaStreamSynchronize(copy);
+    cudaError_t e2 = cudaSuccess;
+    for (int i = 0; i < kCopyStreams; ++i) {
+        cudaError_t ei = copied[i] ? cudaEventRecord(copied[i], copy[i]) : cudaErrorInvalidValue;
+        if (ei == cudaSuccess) ei = cudaStreamWaitEvent(stream, copied[i], 0);
+        if (ei != cudaSuccess) {
+            cudaStreamSynchronize(copy[i]);
+            e2 = ei;
+        }
+    }
     if (d_starts) cudaFreeAsync(d_starts, stream);
     if (d_out) cudaFreeAsync(d_out, stream);
     if (d_done) cudaFreeAsync(d_done, stream);
     const cudaError_t e3 = cudaStreamSynchronize(stream);
     if (walked) cudaEventDestroy(walked);
-    if (copied) cudaEventDestroy(copied);
+    for (int i = 0; i < kCopyStreams; ++i)
+        if (copied[i]) cudaEventDestroy(copied[i]);
     // the flags array is free once the launch that writes it has finished
     if (e3 == cudaSuccess) give_slice_flags(dev, flags);
     if (e == cudaSuccess) e = e2;
@@ -817,7 +848,7 @@ grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_
                                   int32_t loads_in_flight, int32_t blocks_per_sm, uint32_t* sink,
                                   int32_t* resident_blocks_per_sm, int64_t* reads_done,
                                   grape_stream_t stream) {
-    if (!buf || !sink || buf_bytes < 32 || n_reads < 1 || mode < 0 || mode > 2 ||
+    if (!buf || !sink || buf_bytes < 64 || n_reads < 1 || mode < 0 || mode > 2 ||
         blocks_per_sm < 0 || (reinterpret_cast<uintptr_t>(buf) & 31u))
         return GRAPE_ERR_INVALID_ARG;
     const bool ok_shape = (load_bytes == 4 && (loads_in_flight == 8 || loads_in_flight == 16 ||
@@ -825,7 +856,8 @@ grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_
                           (load_bytes == 16 && (loads_in_flight == 8 || loads_in_flight == 16 ||
                                                 loads_in_flight == 32)) ||
                           (load_bytes == 32 && (loads_in_flight == 4 || loads_in_flight == 8 ||
-                                                loads_in_flight == 16));
+                                                loads_in_flight == 16)) ||
+                          (load_bytes == 64 && (loads_in_flight == 4 || loads_in_flight == 8));
     if (!ok_shape) return GRAPE_ERR_INVALID_ARG;
     int dev = 0, sms = 0;
     GRAPE_CUDA_TRY(cudaGetDevice(&dev));
@@ -847,10 +879,13 @@ grape_status_t grape_sector_probe(const void* buf, int64_t buf_bytes, int64_t n_
         if (loads_in_flight == 8) GRAPE_PROBE(8, 16);
         else if (loads_in_flight == 16) GRAPE_PROBE(16, 16);
         else GRAPE_PROBE(32, 16);
-    } else {
+    } else if (load_bytes == 32) {
         if (loads_in_flight == 4) GRAPE_PROBE(4, 32);
         else if (loads_in_flight == 8) GRAPE_PROBE(8, 32);
         else GRAPE_PROBE(16, 32);
+    } else {
+        if (loads_in_flight == 4) GRAPE_PROBE(4, 64);
+        else GRAPE_PROBE(8, 64);
     }
 #undef GRAPE_PROBE
     if (resident_blocks_per_sm) *resident_blocks_per_sm = res;

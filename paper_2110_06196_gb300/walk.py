@@ -422,9 +422,9 @@ def philox4x32_10(ctr_key: torch.Tensor, stream=None) -> torch.Tensor:
 def sector_probe(buf: torch.Tensor, n_reads: int, seed: int, mode: int = 0, load_bytes: int = 32,
                  loads_in_flight: int = 8, blocks_per_sm: int = 0, stream=None) -> tuple:
     """grape_sector_probe: random 32-byte-sector reads over `buf` (mode: 0
-    ld.global.nc, 1 .cg, 2 .cs; load_bytes 4/16/32; loads_in_flight per thread;
-    blocks_per_sm 0 = occupancy maximum).  Returns (reads issued, resident
-    256-thread blocks per SM)."""
+    ld.global.nc, 1 .cg, 2 .cs; load_bytes 4/16/32, or 64 for both sectors of a
+    64-byte block; loads_in_flight per thread; blocks_per_sm 0 = occupancy
+    maximum).  Returns (32-byte sectors read, resident 256-thread blocks per SM)."""
     lib = _lib.load()
     sink = torch.zeros(1, dtype=torch.int32, device=buf.device)
     res = ctypes.c_int32()
