@@ -870,19 +870,6 @@ def bench_cumsum(g, job, n, dev, walks_n=1 << 20, reps=3):
             ms = e0.elapsed_time(e1) / reps
             steps = count_steps(out)
             entry[name] = {"ms_per_launch": ms, "steps_per_s": steps / ms * 1e3}
-        # the cumulative-sum sampler with its membership tests on the sorted rows
-        t0 = g.get_tuning().edge_hash
-        g.set_tuning(edge_hash=0)
-        walks_cumsum(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        walks_cumsum(g, None, job.walk_len, 1, p, q, job.seed, num_starts=ns, out=out)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        g.set_tuning(edge_hash=t0)
-        ms = e0.elapsed_time(e1)
-        entry["cumsum_sorted_row_membership"] = {"ms_per_launch": ms,
-                                                 "steps_per_s": count_steps(out) / ms * 1e3}
         res.append(entry)
     del out
     torch.cuda.empty_cache()

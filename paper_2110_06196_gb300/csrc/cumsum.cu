@@ -15,8 +15,7 @@
 // (p, q, weight) settings that reject most proposals.
 //
 // One warp owns one walk.  The lanes read 32 consecutive entries of N(v) at a
-// time (coalesced) and each tests its own x in N(t), by one edge-hash bucket
-// (the graph's tuning edge_hash) or else by binary search, so
+// time (coalesced) and each tests its own x in N(t) by binary search, so
 // the in-out bias, which the paper names as the bottleneck, runs 32 wide; the
 // second pass takes the products of the first 256 entries from shared memory
 // and the membership of the first 1024 from per-lane bit masks.  Step 4
@@ -67,25 +66,12 @@ __device__ __forceinline__ bool in_sorted(const int* __restrict__ a, long long n
     return lo < n && __ldg(a + lo) == key;
 }
 
-// Is x in N(t)?  One edge-hash bucket when the graph has the table and the
-// launch uses it (use_hash), else (or when the bucket overflowed) the binary
-// search of the row.
-__device__ __forceinline__ bool in_row(const GraphDev& g, bool use_hash, int t, int x,
-                                       long long off_t, long long deg_t) {
-    if (use_hash) {
-        const int f = edge_hash_find(g, t, x);
-        if (f >= 0) return f == 1;
-    }
-    return in_sorted(g.dsts + off_t, deg_t, x);
-}
-
 // alpha(t, x) of entry j of row v: a_ret, 1 or a_out (1 on the first step).
-__device__ __forceinline__ double alpha_of(const GraphDev& g, bool use_hash, int x, int t,
-                                           long long off_t, long long deg_t, double a_ret,
-                                           double a_out) {
+__device__ __forceinline__ double alpha_of(const GraphDev& g, int x, int t, long long off_t,
+                                           long long deg_t, double a_ret, double a_out) {
     if (t < 0) return 1.0;
     if (x == t) return a_ret;
-    return in_row(g, use_hash, t, x, off_t, deg_t) ? 1.0 : a_out;
+    return in_sorted(g.dsts + off_t, deg_t, x) ? 1.0 : a_out;
 }
 
 template <bool WEIGHTED>
@@ -95,13 +81,12 @@ __device__ __forceinline__ double weight_of(const GraphDev& g, long long e) {
 
 // pi of entry j of row v: alpha(t, x) * w, rounded once.
 template <bool WEIGHTED>
-__device__ __forceinline__ double product(const GraphDev& g, bool use_hash, long long off_v,
-                                          long long j, int t, long long off_t, long long deg_t,
-                                          double a_ret, double a_out) {
+__device__ __forceinline__ double product(const GraphDev& g, long long off_v, long long j, int t,
+                                          long long off_t, long long deg_t, double a_ret,
+                                          double a_out) {
     const long long e = off_v + j;
     const int x = __ldg(g.dsts + e);
-    return __dmul_rn(alpha_of(g, use_hash, x, t, off_t, deg_t, a_ret, a_out),
-                     weight_of<WEIGHTED>(g, e));
+    return __dmul_rn(alpha_of(g, x, t, off_t, deg_t, a_ret, a_out), weight_of<WEIGHTED>(g, e));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -112,8 +97,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kCsThreads)
-cumsum_walk_kernel(GraphDev g, WalkConst wc, int use_hash_) {
-    const bool use_hash = use_hash_ != 0 && g.eh != nullptr;
+cumsum_walk_kernel(GraphDev g, WalkConst wc) {
     __shared__ double cache[kCsWarps][kCsCache];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -147,8 +131,7 @@ cumsum_walk_kernel(GraphDev g, WalkConst wc, int use_hash_) {
             auto again = [&](long long j) -> double {
                 if (j < kCsCache) return pc[j];
                 if (j >= kCsMaskRows)
-                    return product<WEIGHTED>(g, use_hash, rv.off, j, t, off_t, deg_t, wc.a_ret,
-                                             wc.a_out);
+                    return product<WEIGHTED>(g, rv.off, j, t, off_t, deg_t, wc.a_ret, wc.a_out);
                 const long long e = rv.off + j;
                 const int x = __ldg(g.dsts + e);
                 const double a = t < 0 ? 1.0
@@ -166,7 +149,7 @@ cumsum_walk_kernel(GraphDev g, WalkConst wc, int use_hash_) {
                         if (x == t) {
                             a = wc.a_ret;
                         } else {
-                            const bool in = in_row(g, use_hash, t, x, off_t, deg_t);
+                            const bool in = in_sorted(g.dsts + off_t, deg_t, x);
                             if (in && j < kCsMaskRows) inmask |= 1u << (j >> 5);
                             a = in ? 1.0 : wc.a_out;
                         }
@@ -247,8 +230,7 @@ cumsum_walk_kernel(GraphDev g, WalkConst wc, int use_hash_) {
 }
 
 template <bool W>
-cudaError_t launch_cumsum(const grape_graph* g, const WalkConst& wc, int use_hash,
-                          cudaStream_t stream) {
+cudaError_t launch_cumsum(const grape_graph* g, const WalkConst& wc, cudaStream_t stream) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cumsum_walk_kernel<W>,
                                                                   kCsThreads, 0);
@@ -256,7 +238,7 @@ cudaError_t launch_cumsum(const grape_graph* g, const WalkConst& wc, int use_has
     per_sm = std::max(per_sm, 1);
     const long long need = (wc.num_walks + kCsWarps - 1) / kCsWarps;
     const int blocks = (int)std::max(1LL, std::min(need, (long long)g->num_sms * per_sm));
-    cumsum_walk_kernel<W><<<blocks, kCsThreads, 0, stream>>>(g->dev(), wc, use_hash);
+    cumsum_walk_kernel<W><<<blocks, kCsThreads, 0, stream>>>(g->dev(), wc);
     return cudaGetLastError();
 }
 
@@ -272,9 +254,7 @@ extern "C" grape_status_t grape_walks_cumsum(const grape_graph_t* g, const int32
                                         seed, out, &wc);
     if (st != GRAPE_OK) return st;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    grape_tuning_t t;
-    grape_graph_get_tuning(g, &t);
-    const cudaError_t e = g->weighted ? launch_cumsum<true>(g, wc, t.edge_hash, stream)
-                                      : launch_cumsum<false>(g, wc, t.edge_hash, stream);
+    const cudaError_t e = g->weighted ? launch_cumsum<true>(g, wc, stream)
+                                      : launch_cumsum<false>(g, wc, stream);
     return cuda_status(e);
 }

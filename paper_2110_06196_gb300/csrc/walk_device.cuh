@@ -224,27 +224,6 @@ __device__ __forceinline__ void ld_sector(const void* p, int4& a, int4& b) {
                  : "l"(p));
 }
 
-// Is the pair (t, x) in the graph's edge hash?  1: yes, 0: no, -1: the pair's
-// bucket overflowed and does not hold it (the caller searches the rows).
-// One 32-byte bucket read.
-__device__ __forceinline__ int edge_hash_find(const GraphDev& g, int t, int x) {
-    unsigned long long a = (unsigned)t, b = (unsigned)x;
-    if (g.undirected && b < a) {
-        const unsigned long long c = a;
-        a = b;
-        b = c;
-    }
-    const int K = 2 * g.eh_k;
-    const unsigned long long h = edge_hash_mix((a << g.eh_k) | b, K);
-    const unsigned tag = (unsigned)(h & ((1ull << (K - g.eh_b)) - 1ull)) + 1u;
-    const uint4* bk = reinterpret_cast<const uint4*>(g.eh + (h >> (K - g.eh_b)) * 8);
-    const uint4 s0 = __ldg(bk), s1 = __ldg(bk + 1);
-    if (s0.x == tag || s0.y == tag || s0.z == tag || s0.w == tag || s1.x == tag ||
-        s1.y == tag || s1.z == tag || s1.w == tag)
-        return 1;
-    return s1.w == kHashOverflow ? -1 : 0;
-}
-
 // Is key in the sorted list a[0, n)?  Lane-local binary search (used by the
 // exact fallback, which runs outside the pipelined state machine).
 __device__ __forceinline__ bool lane_search(const int* __restrict__ a, int n, int key) {

@@ -79,12 +79,10 @@ def rmat12(weighted):
 
 
 @pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
-@pytest.mark.parametrize("edge_hash", [1, 0], ids=["hash", "rows"])
-def test_rmat12_exact_sums(weighted, edge_hash):
+def test_rmat12_exact_sums(weighted):
     csr = rmat12(weighted)
     assert int(np.diff(csr.numpy()[0]).max()) > 256          # rows beyond the product cache
     g = Graph.from_csr(csr)
-    g.set_tuning(edge_hash=edge_hash)                         # membership by bucket or by rows
     for (p, q) in [(1.0, 1.0), (0.5, 2.0), (4.0, 0.25), (0.25, 4.0), (2.0, 0.5)]:
         check(csr, None, 20, 2, p, q, seed=7, g=g)
 
