@@ -219,6 +219,90 @@ __global__ void build_edge_hash_kernel(const int4* __restrict__ rec,
     }
 }
 
+// Is the pair (a, b) in the edge hash?  1 yes, 0 no, -1 its bucket overflowed
+// without holding it (unknown).
+__device__ __forceinline__ int hash_has_pair(const unsigned* __restrict__ table, int k, int b,
+                                             int undirected, long long a_, long long b_) {
+    unsigned long long a = (unsigned long long)a_, c = (unsigned long long)b_;
+    if (undirected && c < a) {
+        const unsigned long long d = a;
+        a = c;
+        c = d;
+    }
+    const int K = 2 * k;
+    const unsigned long long h = grape::edge_hash_mix((a << k) | c, K);
+    const unsigned tag = (unsigned)(h & ((1ull << (K - b)) - 1ull)) + 1u;
+    const uint4* bk = reinterpret_cast<const uint4*>(table + (h >> (K - b)) * 8);
+    const uint4 s0 = __ldg(bk), s1 = __ldg(bk + 1);
+    if (s0.x == tag || s0.y == tag || s0.z == tag || s0.w == tag || s1.x == tag || s1.y == tag ||
+        s1.z == tag || s1.w == tag)
+        return 1;
+    return s1.w == grape::kHashOverflow ? -1 : 0;
+}
+
+// Unweighted undirected graphs: the neighbour filter of entry (v -> x) becomes
+// that of C(v, x) = N(v) n N(x), the common neighbours of the edge's nodes.
+// For a walk at v that came from t (a neighbour of v), x in N(t) holds exactly
+// when x is in C(t, v) and when t is in C(v, x); these sets are much smaller
+// than the rows, so their filters prove far more non-memberships.  One warp
+// per row v takes its entries with x > v in turn; the lanes test the entries of
+// the shorter row against the other node in the edge hash (an overflowed bucket
+// counts as a member), OR their bits, and lane 0 writes the filter into (v -> x)
+// and, through rev, into (x -> v).  Pairs whose shorter row exceeds `cap`
+// entries get an all-ones filter; self-loops keep the row filter (C(v, v) = N(v)).
+__global__ void build_pair_filters_kernel(const int4* __restrict__ rec,
+                                          const int32_t* __restrict__ dsts,
+                                          const unsigned* __restrict__ table, int k, int b,
+                                          long long n, int cap, int4* __restrict__ fat) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+        const int4 rv = rec[v];
+        const long long off_v = (long long)(((unsigned long long)(unsigned)rv.y << 32) | (unsigned)rv.x);
+        for (long long e = off_v; e < off_v + rv.z; ++e) {
+            const long long x = dsts[e];
+            if (x <= v) continue;
+            const int4 rx = rec[x];
+            const long long off_x = (long long)(((unsigned long long)(unsigned)rx.y << 32) | (unsigned)rx.x);
+            const bool v_short = rv.z <= rx.z;
+            const long long so = v_short ? off_v : off_x;
+            const int sn = v_short ? rv.z : rx.z;
+            const long long other = v_short ? x : v;
+            unsigned f[3] = {~0u, ~0u, ~0u};
+            if (sn <= cap) {
+                f[0] = f[1] = f[2] = 0u;
+                for (int j = lane; j < sn; j += 32) {
+                    const int y = dsts[so + j];
+                    if (hash_has_pair(table, k, b, 1, other, y) != 0) {
+                        const int bit = grape::filter_bit(y);
+                        f[bit >> 5] |= 1u << (bit & 31);
+                    }
+                }
+                f[0] = __reduce_or_sync(grape::FULL, f[0]);
+                f[1] = __reduce_or_sync(grape::FULL, f[1]);
+                f[2] = __reduce_or_sync(grape::FULL, f[2]);
+            }
+            if (lane == 0) {
+                int4 w = fat[2 * e + 1];
+                const int rev = w.z;                       // v sits at rev in N(x)
+                w.x = (int)f[0];
+                w.y = (int)f[1];
+                w.w = (int)f[2];
+                fat[2 * e + 1] = w;
+                // (x -> v); an unvalidated graph declared undirected may lack it
+                if (rev >= 0 && rev < rx.z) {
+                    const long long er = off_x + rev;
+                    int4 wr = fat[2 * er + 1];
+                    wr.x = (int)f[0];
+                    wr.y = (int)f[1];
+                    wr.w = (int)f[2];
+                    fat[2 * er + 1] = wr;
+                }
+            }
+        }
+    }
+}
+
 __global__ void mark_edge_hash_overflow_kernel(unsigned* __restrict__ table,
                                                const unsigned* __restrict__ count,
                                                long long buckets) {
@@ -226,6 +310,11 @@ __global__ void mark_edge_hash_overflow_kernel(unsigned* __restrict__ table,
          i += (long long)gridDim.x * blockDim.x)
         if (count[i] > 8) table[8 * i + 7] = grape::kHashOverflow;
 }
+
+// Pairs whose shorter row is longer than this keep an all-ones pair filter:
+// the work of building a filter is one edge-hash read per entry of the shorter
+// row, and a filter of more than about 1,000 common neighbours is saturated.
+constexpr int kPairFilterCap = 1024;
 
 void free_graph(grape_graph* g) {
     if (!g) return;
@@ -414,6 +503,14 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
                 g->eh_b = b;
                 g->eh_bytes = (int64_t)bytes;
                 g->device_bytes += (int64_t)bytes;
+            }
+            // unweighted undirected graphs: filters of common neighbours
+            if (e == cudaSuccess && !weights && g->undirected) {
+                build_pair_filters_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0,
+                                            stream>>>(g->rec, g->dsts, g->eh, k, b, num_nodes,
+                                                      kPairFilterCap, g->fat);
+                e = cudaGetLastError();
+                if (e == cudaSuccess) g->pair_filters = true;
             }
         }
         if (e != cudaSuccess) {

@@ -24,6 +24,7 @@ struct grape_graph {
     unsigned* eh = nullptr;       // edge hash [2^eh_b][8] (see walk_device.cuh), or nullptr
     int eh_k = 0, eh_b = 0;
     int64_t eh_bytes = 0;
+    bool pair_filters = false;    // unweighted entries hold filters of N(v) n N(x), not of N(x)
     int4* fat = nullptr;          // [m] proposal entries (edge-inlined records)
     int* status = nullptr;        // device status word
     unsigned long long* counters = nullptr;  // [grape::C_COUNT]
@@ -41,6 +42,7 @@ struct grape_graph {
         g.eh = eh;
         g.eh_k = eh_k;
         g.eh_b = eh_b;
+        g.pair_filters = pair_filters ? 1 : 0;
         g.n = n;
         g.status = status;
         g.counters = counting ? counters : nullptr;

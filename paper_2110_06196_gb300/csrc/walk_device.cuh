@@ -103,6 +103,9 @@ struct GraphDev {
     // edge hash: [2^eh_b buckets][8] slots, or nullptr; eh_k bits per node id
     const unsigned* eh;
     int eh_k, eh_b;
+    // 1: the filter of an unweighted entry (v -> x) is that of N(v) n N(x)
+    // (undirected graphs with an edge hash); 0: that of N(x)
+    int pair_filters;
     long long n;
     int* status;                // device status word (1 = bad start id)
     unsigned long long* counters;  // [C_COUNT] or nullptr
@@ -1006,12 +1009,17 @@ struct Engine {
         fr->fv[2] = f2;
     }
 
-    // Unweighted: do the filters prove that x is not in N(t)?  The filter of
-    // N(t) tests x; on undirected graphs x in N(t) <=> t in N(x), so the filter
-    // of N(x), which arrived in x's entry (ld2), tests t as well.
+    // Unweighted: do the filters prove that x is not in N(t)?
+    // Row filters: the filter of N(t) tests x; on undirected graphs x in N(t)
+    // <=> t in N(x), so the filter of N(x), which arrived in x's entry (ld2),
+    // tests t as well.
+    // Pair filters (undirected): t is a neighbour of v, so x in N(t) <=> x in
+    // N(t) n N(v), whose filter came with the entry the walk arrived by (fv),
+    // <=> t in N(v) n N(x), whose filter is in x's entry.
     __device__ __forceinline__ bool filters_exclude(const Lane& L, int x) {
         const FRec* fr = frec();
-        if (!filter_has(fr->ft[0], fr->ft[1], fr->ft[2], filter_bit(x))) return true;
+        const unsigned* f = g.pair_filters ? fr->fv : fr->ft;
+        if (!filter_has(f[0], f[1], f[2], filter_bit(x))) return true;
         return g.undirected &&
                !filter_has((unsigned)ld2.x, (unsigned)ld2.y, (unsigned)ld2.w, filter_bit(L.t));
     }
@@ -1322,9 +1330,12 @@ struct Engine {
                     b = make_int4(__float_as_int(L.wr), __float_as_int(tr.wmax_t), tr.jv,
                                   __float_as_int(tr.wj));
                 } else {
-                    // back to t: its filter was the previous node's
+                    // back to t: the filter of the entry (v -> t) is the row
+                    // filter of N(t), held as the previous node's, or the pair
+                    // filter of N(v) n N(t), the one the walk arrived by
                     const FRec* fr = frec();
-                    b = make_int4((int)fr->ft[0], (int)fr->ft[1], tr.jv, (int)fr->ft[2]);
+                    const unsigned* f = g.pair_filters ? fr->fv : fr->ft;
+                    b = make_int4((int)f[0], (int)f[1], tr.jv, (int)f[2]);
                 }
                 jv = L.rt;
             }
