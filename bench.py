@@ -1100,17 +1100,24 @@ def bench_serve(args, dev):
                             len_lo=20, len_hi=120, first_seed=90_000)
     outs = [torch.empty((len(r.starts), r.walk_len), dtype=torch.int32, pin_memory=True)
             for r in mix]
-    srv = Server(g, output_cap_bytes=40 << 30, max_inflight=4096, chunk_walks=0,
-                 max_chunks=1 << 24, idle_exit_us=2000)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(r.starts, r.walk_len, r.p, r.q, r.seed, out=o) for r, o in zip(mix, outs)]
-    lat = []
-    for _ in tickets:
-        _, l, _ = srv.wait_any(timeout_ms=600_000)
-        lat.append(l)
-    t_srv = time.perf_counter() - t0
-    steps = srv.stats()["steps"]
-    srv.close()
+    # three runs (the host link to pinned memory is shared on these hosts and
+    # its rate varies): the median run is reported, and all three
+    runs = []
+    for _ in range(3):
+        srv = Server(g, output_cap_bytes=40 << 30, max_inflight=4096, chunk_walks=0,
+                     max_chunks=1 << 24, idle_exit_us=2000)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(r.starts, r.walk_len, r.p, r.q, r.seed, out=o)
+                   for r, o in zip(mix, outs)]
+        lat = []
+        for _ in tickets:
+            _, l, _ = srv.wait_any(timeout_ms=600_000)
+            lat.append(l)
+        runs.append((time.perf_counter() - t0, lat))
+        steps = srv.stats()["steps"]
+        srv.close()
+    runs.sort(key=lambda r: r[0])
+    t_srv, lat = runs[1]
     seq_outs = [torch.empty_like(o, pin_memory=True) for o in outs]
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -1128,6 +1135,7 @@ def bench_serve(args, dev):
             "rates": results,
             "saturation": {"requests": len(mix), "steps": steps,
                            "served_steps_per_s": steps / t_srv,
+                           "served_s_of_three_runs": [r[0] for r in runs],
                            "sequential_steps_per_s": steps / t_seq,
                            "served_vs_one_launch_per_request": t_seq / t_srv,
                            "p50_ms": float(np.percentile(lat_ms, 50)),

@@ -94,14 +94,20 @@ typedef struct grape_graph grape_graph_t;
  *       caller keeps ownership; they may be freed once `stream` has reached
  *       this call's work (the copies are enqueued on it).
  *   num_nodes in [1, 2^31 - 1]; num_entries in [0, 2^62].  The graph holds
- *   16 * num_nodes + 36.5 * num_entries bytes: node records, sorted rows, their
- *   sector pivots (the first id of every aligned 32-byte sector), and
- *   per CSR entry one 32-byte proposal entry that carries the target's degree,
- *   row offset and largest row weight, the weight, and the position of the
- *   row's node in the target's row (unweighted graphs: a 96-bit filter of the
- *   target's row in place of the weights).  Unweighted graphs need another
- *   16 * num_nodes bytes of scratch from the device's stream-ordered pool
- *   during the call.
+ *   node records (16 bytes per node), the sorted rows and their sector pivots
+ *   (4.5 bytes per entry), one 32-byte proposal entry per CSR entry (the
+ *   target's degree, row offset and largest row weight, the weight, and the
+ *   position of the row's node in the target's row), and an edge hash: every
+ *   pair stored once in 32-byte buckets of eight slots at 2 to 3.5 pairs per
+ *   bucket (8-16 bytes per undirected edge), so that a membership test reads one
+ *   bucket.  The hash is left out when it would exceed twice the sorted rows.
+ *   A proposal entry also carries a filter that proves non-memberships: on
+ *   undirected graphs with the hash, of N(v) n N(x) for the entry (v -> x) (96
+ *   bits unweighted; 32 bits weighted, in place of the reverse weight, which
+ *   the GRAPE_UNDIRECTED flag asserts equal); otherwise, on unweighted graphs,
+ *   of N(x).  Unweighted graphs need another 16 * num_nodes bytes of scratch,
+ *   and the hash 4 bytes per bucket, from the device's stream-ordered pool
+ *   during the call.  grape_graph_info reports the bytes held.
  *   flags: GRAPE_UNDIRECTED | GRAPE_VALIDATE.  With GRAPE_VALIDATE the call
  *       synchronises `stream` and returns GRAPE_ERR_INVALID_GRAPH for:
  *       non-monotone offsets, wrong first or last offset, ids out of range,

@@ -240,8 +240,10 @@ __device__ __forceinline__ int hash_has_pair(const unsigned* __restrict__ table,
     return s1.w == grape::kHashOverflow ? -1 : 0;
 }
 
-// Unweighted undirected graphs: the neighbour filter of entry (v -> x) becomes
-// that of C(v, x) = N(v) n N(x), the common neighbours of the edge's nodes.
+// Undirected graphs: the neighbour filter of entry (v -> x) becomes that of
+// C(v, x) = N(v) n N(x), the common neighbours of the edge's nodes (96 bits in
+// an unweighted entry; 32 bits in the last word of a weighted one, in place of
+// the reverse weight, which equals w_vx on an undirected graph).
 // For a walk at v that came from t (a neighbour of v), x in N(t) holds exactly
 // when x is in C(t, v) and when t is in C(v, x); these sets are much smaller
 // than the rows, so their filters prove far more non-memberships.  One warp
@@ -249,11 +251,13 @@ __device__ __forceinline__ int hash_has_pair(const unsigned* __restrict__ table,
 // the shorter row against the other node in the edge hash (an overflowed bucket
 // counts as a member), OR their bits, and lane 0 writes the filter into (v -> x)
 // and, through rev, into (x -> v).  Pairs whose shorter row exceeds `cap`
-// entries get an all-ones filter; self-loops keep the row filter (C(v, v) = N(v)).
+// entries get an all-ones filter; unweighted self-loops keep the row filter
+// (C(v, v) = N(v)), weighted ones get all ones.
 __global__ void build_pair_filters_kernel(const int4* __restrict__ rec,
                                           const int32_t* __restrict__ dsts,
                                           const unsigned* __restrict__ table, int k, int b,
-                                          long long n, int cap, int4* __restrict__ fat) {
+                                          long long n, int cap, int weighted,
+                                          int4* __restrict__ fat) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
@@ -261,6 +265,7 @@ __global__ void build_pair_filters_kernel(const int4* __restrict__ rec,
         const long long off_v = (long long)(((unsigned long long)(unsigned)rv.y << 32) | (unsigned)rv.x);
         for (long long e = off_v; e < off_v + rv.z; ++e) {
             const long long x = dsts[e];
+            if (x == v && weighted && lane == 0) fat[2 * e + 1].w = -1;   // no filter: all ones
             if (x <= v) continue;
             const int4 rx = rec[x];
             const long long off_x = (long long)(((unsigned long long)(unsigned)rx.y << 32) | (unsigned)rx.x);
@@ -274,7 +279,7 @@ __global__ void build_pair_filters_kernel(const int4* __restrict__ rec,
                 for (int j = lane; j < sn; j += 32) {
                     const int y = dsts[so + j];
                     if (hash_has_pair(table, k, b, 1, other, y) != 0) {
-                        const int bit = grape::filter_bit(y);
+                        const int bit = weighted ? grape::filter_bit32(y) : grape::filter_bit(y);
                         f[bit >> 5] |= 1u << (bit & 31);
                     }
                 }
@@ -283,19 +288,29 @@ __global__ void build_pair_filters_kernel(const int4* __restrict__ rec,
                 f[2] = __reduce_or_sync(grape::FULL, f[2]);
             }
             if (lane == 0) {
+                // unweighted: the three filter words; weighted: the last word
+                // (the reverse weight, equal to w_vx on an undirected graph)
                 int4 w = fat[2 * e + 1];
                 const int rev = w.z;                       // v sits at rev in N(x)
-                w.x = (int)f[0];
-                w.y = (int)f[1];
-                w.w = (int)f[2];
+                if (weighted) {
+                    w.w = (int)f[0];
+                } else {
+                    w.x = (int)f[0];
+                    w.y = (int)f[1];
+                    w.w = (int)f[2];
+                }
                 fat[2 * e + 1] = w;
                 // (x -> v); an unvalidated graph declared undirected may lack it
                 if (rev >= 0 && rev < rx.z) {
                     const long long er = off_x + rev;
                     int4 wr = fat[2 * er + 1];
-                    wr.x = (int)f[0];
-                    wr.y = (int)f[1];
-                    wr.w = (int)f[2];
+                    if (weighted) {
+                        wr.w = (int)f[0];
+                    } else {
+                        wr.x = (int)f[0];
+                        wr.y = (int)f[1];
+                        wr.w = (int)f[2];
+                    }
                     fat[2 * er + 1] = wr;
                 }
             }
@@ -504,11 +519,11 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
                 g->eh_bytes = (int64_t)bytes;
                 g->device_bytes += (int64_t)bytes;
             }
-            // unweighted undirected graphs: filters of common neighbours
-            if (e == cudaSuccess && !weights && g->undirected) {
+            // undirected graphs: filters of common neighbours
+            if (e == cudaSuccess && g->undirected) {
                 build_pair_filters_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0,
                                             stream>>>(g->rec, g->dsts, g->eh, k, b, num_nodes,
-                                                      kPairFilterCap, g->fat);
+                                                      kPairFilterCap, weights ? 1 : 0, g->fat);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) g->pair_filters = true;
             }

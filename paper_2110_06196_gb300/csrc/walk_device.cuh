@@ -60,6 +60,11 @@ __host__ __device__ __forceinline__ int filter_bit(int y) {
     return (int)(((unsigned long long)h * 96ull) >> 32);
 }
 
+// Weighted entries have room for one 32-bit pair filter (undirected graphs).
+__host__ __device__ __forceinline__ int filter_bit32(int y) {
+    return (int)(((unsigned)y * 0x9E3779B1u) >> 27);
+}
+
 __host__ __device__ __forceinline__ bool filter_has(unsigned f0, unsigned f1, unsigned f2, int b) {
     const unsigned word = b < 32 ? f0 : (b < 64 ? f1 : f2);
     return (word >> (b & 31)) & 1u;
@@ -103,8 +108,11 @@ struct GraphDev {
     // edge hash: [2^eh_b buckets][8] slots, or nullptr; eh_k bits per node id
     const unsigned* eh;
     int eh_k, eh_b;
-    // 1: the filter of an unweighted entry (v -> x) is that of N(v) n N(x)
-    // (undirected graphs with an edge hash); 0: that of N(x)
+    // 1 (undirected graphs with an edge hash): an entry (v -> x) holds a filter
+    // of N(v) n N(x), 96 bits in an unweighted entry, 32 bits in the last word
+    // of a weighted one (in place of the reverse weight, equal to w_vx on an
+    // undirected graph); 0: an unweighted entry holds a filter of N(x) and a
+    // weighted one none
     int pair_filters;
     long long n;
     int* status;                // device status word (1 = bad start id)
@@ -993,8 +1001,12 @@ struct Engine {
     // filter (of N(x)) that of N(v).
     __device__ __forceinline__ bool advance_entry(Lane& L, int4 a, int4 b, int idx) {
         if (!WEIGHTED) shift_filters((unsigned)b.x, (unsigned)b.y, (unsigned)b.w);
+        else if (g.pair_filters) frec()->fv[0] = (unsigned)b.w;
         const long long off = (long long)(((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.z);
-        return advance(L, a.x, off, a.y, __int_as_float(b.y), b.z, __int_as_float(b.w), idx,
+        // the weight of (x -> v): the last word, or w_vx itself where that word
+        // holds the pair filter (undirected graphs: equal weights)
+        const int wxv = (WEIGHTED && g.pair_filters) ? b.x : b.w;
+        return advance(L, a.x, off, a.y, __int_as_float(b.y), b.z, __int_as_float(wxv), idx,
                        __int_as_float(b.x));
     }
 
@@ -1018,6 +1030,10 @@ struct Engine {
     // <=> t in N(v) n N(x), whose filter is in x's entry.
     __device__ __forceinline__ bool filters_exclude(const Lane& L, int x) {
         const FRec* fr = frec();
+        if (WEIGHTED) {            // 32-bit pair filters
+            if (!((fr->fv[0] >> filter_bit32(x)) & 1u)) return true;
+            return !(((unsigned)ld2.w >> filter_bit32(L.t)) & 1u);
+        }
         const unsigned* f = g.pair_filters ? fr->fv : fr->ft;
         if (!filter_has(f[0], f[1], f[2], filter_bit(x))) return true;
         return g.undirected &&
@@ -1254,7 +1270,7 @@ struct Engine {
             if (A.acc_a == A.acc_b || !HAS_Q) {
                 if (A.acc_a) take = true;
                 else L.k++;
-            } else if (!WEIGHTED && filters_exclude(L, A.x)) {
+            } else if ((!WEIGHTED || g.pair_filters) && filters_exclude(L, A.x)) {
                 cnt.add(C_FILTERED);            // x is not in N(t): the out class decides
                 if (A.acc_b) take = true;
                 else L.k++;
@@ -1327,8 +1343,10 @@ struct Engine {
                 a = make_int4(L.t, tr.deg_t, (int)(unsigned)tr.off_t,
                               (int)(unsigned)((unsigned long long)tr.off_t >> 32));
                 if (WEIGHTED) {
-                    b = make_int4(__float_as_int(L.wr), __float_as_int(tr.wmax_t), tr.jv,
-                                  __float_as_int(tr.wj));
+                    // the last word: t's weight towards v, or with pair filters
+                    // the filter of N(v) n N(t), the one the walk arrived by
+                    const int last = g.pair_filters ? (int)frec()->fv[0] : __float_as_int(tr.wj);
+                    b = make_int4(__float_as_int(L.wr), __float_as_int(tr.wmax_t), tr.jv, last);
                 } else {
                     // back to t: the filter of the entry (v -> t) is the row
                     // filter of N(t), held as the previous node's, or the pair
