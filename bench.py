@@ -979,8 +979,9 @@ class PinnedArena:
     first-fit into per-request slices and given back once a request's rows
     are counted.  Should the arena be full, a request gets a buffer of its own."""
 
-    def __init__(self, elems):
-        self.buf = torch.empty(elems, dtype=torch.int32, pin_memory=True)
+    def __init__(self, elems, pin=True):
+        self.pin = pin
+        self.buf = torch.empty(elems, dtype=torch.int32, pin_memory=pin)
         self.free = [(0, elems)]                 # sorted (offset, length)
         self.extra = 0
 
@@ -991,7 +992,7 @@ class PinnedArena:
                 self.free[i:i + 1] = [(o + elems, n - elems)] if n > elems else []
                 return ("arena", o, elems), self.buf[o:o + elems]
         self.extra += 1
-        t = torch.empty(elems, dtype=torch.int32, pin_memory=True)
+        t = torch.empty(elems, dtype=torch.int32, pin_memory=self.pin)
         return ("own", 0, elems), t
 
     def give(self, key):

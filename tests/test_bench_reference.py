@@ -48,3 +48,50 @@ def test_step_count_and_row_signature():
         assert bench.row_signature(other) != sig
     swapped = rows[[1, 0, 2, 3]].contiguous()
     assert bench.row_signature(swapped) != sig
+
+
+def test_pinned_arena_carves_and_coalesces():
+    """The served rows' host arena: first-fit slices rounded to 64 entries,
+    given back and merged with their neighbours, a buffer of its own when full."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.PinnedArena(1024, pin=False)
+    k1, b1 = a.take(100)               # 128 entries
+    k2, b2 = a.take(300)               # 320
+    k3, b3 = a.take(64)
+    assert (k1[1], k1[2]) == (0, 128) and (k2[1], k2[2]) == (128, 320) and k3[1] == 448
+    assert b1.data_ptr() == a.buf.data_ptr() and b2.numel() == 320
+    a.give(k2)
+    k4, _ = a.take(200)                # fits the hole at 128
+    assert k4[1] == 128
+    a.give(k1)
+    a.give(k4)
+    a.give(k3)
+    assert a.free == [(0, 1024)]       # everything merged back
+    k5, b5 = a.take(2000)              # larger than the arena: its own buffer
+    assert k5[0] == "own" and b5.numel() >= 2000 and a.extra == 1
+    a.give(k5)
+    assert a.free == [(0, 1024)]
+
+
+def test_job_steps_and_byte_models():
+    """Steps of a whole-graph job on an undirected graph (a walk from a
+    non-isolated start takes walk_len - 1 transitions), and the per-step byte
+    model and sector counts the roofline is built from."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Job:
+        walk_len, walks_per_node = 5, 3
+
+    deg = torch.tensor([2, 0, 1, 4], dtype=torch.int64)
+    assert bench.job_steps(deg, Job) == 3 * 3 * 4
+    c = {"steps": 10, "trials": 30, "gathers": 12, "searches": 4, "probes": 5, "walks": 2}
+    assert bench.model_bytes(c, weighted=False) == 36 * 10 + 32 * 30 + 32 * 5
+    assert bench.model_bytes(c, weighted=True) == 36 * 10 + 64 * 30 + 32 * 5
+    assert bench.sector_minimal_bytes(c, rows=2, walk_len=6) == 32 * (12 + 4 + 2) + 4 * 12
+    assert bench.random_sectors(c) == 12 + 5 + 2
+    r = bench.roofline(dict(c, filtered=0, fallbacks=0), 2, 6, False, 1000.0, 100.0, "measured",
+                       None, 1e9)
+    assert abs(r["achieved"] - bench.model_bytes(c, False) / 1e9) < 1e-9
+    assert abs(r["frac_of_random_sector_peak"] - 19 / 1e9) < 1e-15
