@@ -415,19 +415,27 @@ def time_launches(g, job, n, b, rows, wpn_total, dev, steps, warmup, dist=None, 
     return ms, steps_per_launch, cnt, clk, out
 
 
-def e2e_rate(g, job, n, steps_per_job, dist, k):
+def e2e_buffers(n, job):
+    """Pinned host starts (0..n-1) and rows for the end-to-end calls,
+    allocated before the device timing, as a user allocates them once and
+    reuses them."""
+    rows = n * job.walks_per_node
+    starts_h = host_rows(n)
+    starts_h.copy_(torch.arange(n, dtype=torch.int32))
+    return starts_h, host_rows(rows * job.walk_len).view(rows, job.walk_len)
+
+
+def e2e_rate(g, job, n, steps_per_job, dist, k, bufs=None):
     """The same job end to end through grape_walks_host, the call a user with
     host buffers makes: the starts go in from pinned host memory and the rows
-    come back into pinned host memory inside every timed call.  One untimed
-    call, then k timed ones.  Returns (steps/s, H2D bytes, D2H bytes per call)."""
+    come back into pinned host memory inside every timed call.  Two untimed calls, then k timed ones.  Returns
+    (steps/s, H2D bytes, D2H bytes per call)."""
     from paper_2110_06196_gb300 import _lib
     lib = g._lib
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
     rows = n * job.walks_per_node
-    starts_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    starts_h.copy_(torch.arange(n, dtype=torch.int32))
-    out_h = torch.empty((rows, job.walk_len), dtype=torch.int32, pin_memory=True)
+    starts_h, out_h = bufs if bufs is not None else e2e_buffers(n, job)
     st_ptr = ctypes.c_void_p(starts_h.data_ptr())
     oh_ptr = ctypes.c_void_p(out_h.data_ptr())
 
@@ -437,13 +445,14 @@ def e2e_rate(g, job, n, steps_per_job, dist, k):
         _lib.check(code, "grape_walks_host")
 
     call()
+    call()
     dist.barrier()
     t0 = time.perf_counter()
     for _ in range(k):
         call()
     dt = dist.max(time.perf_counter() - t0)
     h2d, d2h = 4 * n, 4 * rows * job.walk_len
-    del starts_h, out_h
+    del starts_h, out_h, bufs
     from paper_2110_06196_gb300 import walk as W
     W.trim_scratch(0)                        # the call's pooled device scratch goes back
     return steps_per_job * k * dist.world / dt, h2d, d2h
@@ -505,6 +514,7 @@ def run_ours(args, dist):
     num_entries = csr.num_entries
     degrees = csr.degrees()
     log("graph resident; timing walks")
+    e2e_bufs = e2e_buffers(n, job)
     want_cpu = not args.no_cpu_baseline and solo
     csr_host = csr.numpy() if want_cpu else None
     # the library holds its own copy of the graph
@@ -537,7 +547,9 @@ def run_ours(args, dist):
     if spec["kind"] != "er" and dist.world == 1:
         assert steps_per_launch == job_steps(degrees, job), "rows do not have the job's steps"
     log(f"walks {launch_ms:.1f} ms per launch; end to end")
-    e2e_value, h2d, d2h = e2e_rate(g, job, n, steps_per_launch, dist, max(1, min(args.steps, 5)))
+    e2e_value, h2d, d2h = e2e_rate(g, job, n, steps_per_launch, dist, max(1, min(args.steps, 5)),
+                                   e2e_bufs)
+    del e2e_bufs
     log(f"end to end {e2e_value / 1e9:.2f} G steps/s; random-sector probe")
     peak, peak_kind = measured_peaks()
     rs, rs_best, rs_sweep = (None, None, None)
@@ -973,15 +985,21 @@ def bench_batched(g, csr, dev):
 # ---------------------------------------------------------------------------
 # serving
 # ---------------------------------------------------------------------------
+def host_rows(elems, pin=True):
+    """int32 host buffer: page-locked (pinned) when pin, so that the copy
+    engines write it directly; pageable otherwise."""
+    return torch.empty(elems, dtype=torch.int32, pin_memory=pin)
+
+
 class PinnedArena:
-    """Served rows land in one pinned host arena allocated before the arrivals
-    start (a pinned allocation during the run can stall the device), carved
+    """Served rows land in one page-locked host arena allocated before the
+    arrivals start (page-locking during the run can stall the device), carved
     first-fit into per-request slices and given back once a request's rows
     are counted.  Should the arena be full, a request gets a buffer of its own."""
 
     def __init__(self, elems, pin=True):
         self.pin = pin
-        self.buf = torch.empty(elems, dtype=torch.int32, pin_memory=pin)
+        self.buf = host_rows(elems, pin)
         self.free = [(0, elems)]                 # sorted (offset, length)
         self.extra = 0
 
@@ -992,8 +1010,7 @@ class PinnedArena:
                 self.free[i:i + 1] = [(o + elems, n - elems)] if n > elems else []
                 return ("arena", o, elems), self.buf[o:o + elems]
         self.extra += 1
-        t = torch.empty(elems, dtype=torch.int32, pin_memory=self.pin)
-        return ("own", 0, elems), t
+        return ("own", 0, elems), host_rows(elems, self.pin)
 
     def give(self, key):
         kind, o, n = key
@@ -1019,13 +1036,20 @@ def bench_serve(args, dev):
     the same requests as one grape_walks_host launch each, rows compared."""
     import threading
     from paper_2110_06196_gb300 import Graph, Server, synth, walks_host
+    # host buffers first: page-locked once, reused by every run
+    pool = PinnedArena(args.serve_host_gib << 28)   # GiB of int32
     csr = synth.workload_graph(args.serve_graph, device=dev)
     g = Graph.from_csr(csr, validate=False, device=dev)
     n = g.num_nodes
     deg = csr.degrees().cpu().numpy()
     del csr
     torch.cuda.empty_cache()
-    pool = PinnedArena(args.serve_host_gib << 28)   # GiB of int32
+    sat_mix = synth.request_mix(n, args.serve_saturation, gen_seed=99, max_starts=1_000_000,
+                                len_lo=20, len_hi=120, first_seed=90_000)
+    sizes = [len(r.starts) * r.walk_len for r in sat_mix]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    sat_buf = host_rows(int(offs[-1]))
+    seq_buf = host_rows(int(offs[-1]))
     results = []
     rates = [float(x) for x in args.serve_rates.split(",")]
     # (rate index, idle exit): every rate with the default 2 ms idle exit, and
@@ -1097,14 +1121,12 @@ def bench_serve(args, dev):
                         "requests_step_mismatch": checked[1]})
     # Saturation: every request of one mix at once through the server, then the
     # same requests as one grape_walks_host launch each, one after another.
-    mix = synth.request_mix(n, args.serve_saturation, gen_seed=99, max_starts=1_000_000,
-                            len_lo=20, len_hi=120, first_seed=90_000)
-    outs = [torch.empty((len(r.starts), r.walk_len), dtype=torch.int32, pin_memory=True)
-            for r in mix]
-    # three runs (the host link to pinned memory is shared on these hosts and
-    # its rate varies): the median run is reported, and all three
+    mix = sat_mix
+    outs = [sat_buf[int(offs[j]):int(offs[j + 1])].view(len(r.starts), r.walk_len)
+            for j, r in enumerate(mix)]
+    # five runs through fresh servers: the median run is reported, and all five
     runs = []
-    for _ in range(3):
+    for _ in range(5):
         srv = Server(g, output_cap_bytes=40 << 30, max_inflight=4096, chunk_walks=0,
                      max_chunks=1 << 24, idle_exit_us=2000)
         t0 = time.perf_counter()
@@ -1118,17 +1140,21 @@ def bench_serve(args, dev):
         steps = srv.stats()["steps"]
         srv.close()
     runs.sort(key=lambda r: r[0])
-    t_srv, lat = runs[1]
-    seq_outs = [torch.empty_like(o, pin_memory=True) for o in outs]
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for r, o in zip(mix, seq_outs):
-        walks_host(g, r.starts, r.walk_len, 1, r.p, r.q, r.seed, out=o)
-    t_seq = time.perf_counter() - t0
+    t_srv, lat = runs[len(runs) // 2]
+    seq_outs = [seq_buf[int(offs[j]):int(offs[j + 1])].view(len(r.starts), r.walk_len)
+                for j, r in enumerate(mix)]
+    seq_runs = []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for r, o in zip(mix, seq_outs):
+            walks_host(g, r.starts, r.walk_len, 1, r.p, r.q, r.seed, out=o)
+        seq_runs.append(time.perf_counter() - t0)
+    t_seq = statistics.median(seq_runs)
     same = all(torch.equal(a, b) for a, b in zip(outs, seq_outs))
     lat_ms = np.array(lat) * 1e3
     g.close()
-    del g, outs, seq_outs, pool
+    del g, outs, seq_outs, pool, sat_buf, seq_buf
     torch.cuda.empty_cache()
     return {"graph": f"{args.serve_graph}: " + workload_graph_desc(args.serve_graph),
             "mix": "starts log-uniform [1, 1e6] (uniform ids), len U[20, 120], p, q in "
@@ -1136,7 +1162,8 @@ def bench_serve(args, dev):
             "rates": results,
             "saturation": {"requests": len(mix), "steps": steps,
                            "served_steps_per_s": steps / t_srv,
-                           "served_s_of_three_runs": [r[0] for r in runs],
+                           "served_s_of_five_runs": [r[0] for r in runs],
+                           "sequential_s_of_three_runs": seq_runs,
                            "sequential_steps_per_s": steps / t_seq,
                            "served_vs_one_launch_per_request": t_seq / t_srv,
                            "p50_ms": float(np.percentile(lat_ms, 50)),

@@ -249,14 +249,15 @@ grape_status_t grape_walks_cumsum(const grape_graph_t* graph, const int32_t* sta
 
 /*
  * The same walks as grape_walks, with `starts` and `out` in HOST memory
- * (pageable or pinned).  The call copies the starts in, runs the walks and
- * copies the rows out, and returns once `out` holds them (it synchronises
- * `stream`).  Rows above 64 MB are walked in up to 16 slices of walk ids, and
- * each slice is copied out on a per-device copy stream of the library while
- * the later slices are walked.  Device scratch for the starts and rows is
- * taken from, and given back to, the device's default stream-ordered memory
- * pool inside the call.  Pinned host buffers let the copies run at full link
- * speed.
+ * (pageable or page-locked).  The call copies the starts in, walks the whole
+ * job in one launch and copies the rows out, and returns once `out` holds them
+ * (it synchronises `stream`).  The rows are cut into up to 64 slices of walk
+ * ids (64 MB or more each); the walk that completes a slice raises the slice's
+ * flag in mapped host memory, and the calling thread then copies that slice
+ * out on one of the library's per-device copy streams while the launch goes
+ * on.  Device scratch for the starts and rows is taken from, and given back to,
+ * the device's default stream-ordered memory pool inside the call.
+ * Page-locked host buffers let the copies run at the host link's rate.
  */
 grape_status_t grape_walks_host(const grape_graph_t* graph, const int32_t* starts,
                                 int64_t num_starts, int32_t walk_len, int32_t walks_per_node,

@@ -116,6 +116,10 @@ struct Req {
 
 // Queue entries staged in pinned host memory per copy (4 MiB).
 constexpr int64_t kChunkStage = 1 << 18;
+// Pinned staging of requests' start ids, in bytes.  An upload straight from
+// pageable memory would be staged by the driver, synchronously, and while such
+// uploads run the copy stream's transfers of finished rows slow to a few GB/s.
+constexpr size_t kStartsStage = (size_t)32 << 20;
 
 struct grape_server {
     const grape_graph* g = nullptr;
@@ -136,10 +140,12 @@ struct grape_server {
     unsigned* d_flags = nullptr;           // its device address
     WalkConst* h_wc = nullptr;             // pinned staging of request descriptors, per slot
     unsigned long long* h_tail = nullptr;  // pinned queue-tail values, per slot
-    unsigned long long* h_misc = nullptr;  // pinned: [0] head at launch, [1] heartbeat
+    unsigned long long* h_misc = nullptr;  // pinned: [0] head at launch, [1] heartbeat,
+                                           // [2] the exit word (driver thread), [3] shutdown
     uint64_t pub_tail = 0;                 // queue entries published to the device
     Chunk* h_chunks = nullptr;             // pinned staging of queue entries (driver thread)
     size_t h_chunks_cap = 0;               // min(max_chunks, kChunkStage)
+    char* h_starts = nullptr;              // pinned staging of start ids (kStartsStage bytes)
     cudaStream_t compute = nullptr, copy = nullptr, ctl = nullptr;
     cudaEvent_t kernel_done = nullptr;
     bool kernel_launched = false;
@@ -229,16 +235,18 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
     // Per request: its descriptor, starts and queue entries, then the tail
     // that covers them, all on one stream, so a worker that sees a tail also
     // sees what it covers, and the resident kernel starts on the first request
-    // while later ones are still being copied.  Descriptors, entries and tail
-    // values are staged in pinned memory allocated with the server (no
+    // while later ones are still being copied.  Descriptors, start ids, entries
+    // and tail values are staged in pinned memory allocated with the server (no
     // allocation here: freeing or allocating pinned memory may synchronise the
     // device, and the resident kernel may be waiting for exactly this work).
-    // A full entry stage is waited for on the control stream before reuse.
+    // A full entry or start-id stage is waited for on the control stream before
+    // reuse.
     if (reqs.empty()) return GRAPE_OK;
     const uint64_t ring = (uint64_t)cfg.max_chunks;
     uint64_t pos = reqs.front()->first_chunk;     // ring position of the first staged entry
     size_t nstaged = 0;       // entries in the stage
     size_t ncopied = 0;       // of which already enqueued for copy
+    size_t starts_used = 0;   // bytes of the start-id stage in use
     cudaError_t e = cudaSuccess;
     auto copy_staged = [&]() -> cudaError_t {
         while (ncopied < nstaged) {
@@ -257,9 +265,25 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
         int32_t* d_starts = nullptr;
         if (!q->starts.empty()) {
             d_starts = reinterpret_cast<int32_t*>(base + Arena::round(q->out_bytes));
-            e = cudaMemcpyAsync(d_starts, q->starts.data(), (size_t)q->starts_bytes,
-                                cudaMemcpyHostToDevice, ctl);
-            if (e != cudaSuccess) return cuda_status(e);
+            const char* src = reinterpret_cast<const char*>(q->starts.data());
+            const size_t total = (size_t)q->starts_bytes;
+            for (size_t done = 0; done < total;) {
+                if (starts_used == kStartsStage) {
+                    // every earlier entry is already enqueued (each request's
+                    // are, before the next request's starts)
+                    e = cudaStreamSynchronize(ctl);
+                    if (e != cudaSuccess) return cuda_status(e);
+                    starts_used = 0;
+                    nstaged = ncopied = 0;
+                }
+                const size_t n = std::min(total - done, kStartsStage - starts_used);
+                std::memcpy(h_starts + starts_used, src + done, n);
+                e = cudaMemcpyAsync(reinterpret_cast<char*>(d_starts) + done, h_starts + starts_used,
+                                    n, cudaMemcpyHostToDevice, ctl);
+                if (e != cudaSuccess) return cuda_status(e);
+                starts_used += n;
+                done += n;
+            }
         }
         WalkConst* wc = h_wc + q->slot;
         grape_status_t st = make_walk_const(g, d_starts, q->r.num_starts, q->r.walk_len,
@@ -277,6 +301,7 @@ grape_status_t grape_server::publish(const std::vector<std::shared_ptr<Req>>& re
                 if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
                 if (e != cudaSuccess) return cuda_status(e);
                 nstaged = ncopied = 0;
+                starts_used = 0;
             }
             Chunk& ch = h_chunks[nstaged++];
             ch.walk_lo = (long long)(c * (uint64_t)q->chunk);
@@ -354,9 +379,9 @@ void grape_server::run() {
     // the heartbeat comes several times within one wait bound
     const int64_t beat_ns = std::min<int64_t>(100000000, wait_ms * 1000000 / 4);
     auto set_exit = [&](int v) {
-        static thread_local int word;
-        word = v;
-        cudaError_t e = cudaMemcpyAsync(d_exit, &word, sizeof(int), cudaMemcpyHostToDevice, ctl);
+        int* word = reinterpret_cast<int*>(h_misc + 2);   // pinned: the copy is a plain DMA
+        *word = v;
+        cudaError_t e = cudaMemcpyAsync(d_exit, word, sizeof(int), cudaMemcpyHostToDevice, ctl);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctl);
         return e;
     };
@@ -589,8 +614,9 @@ grape_status_t grape_walk_server_create(const grape_graph_t* g, const grape_serv
     if (e == cudaSuccess)
         e = cudaHostAlloc(&s->h_tail, sizeof(unsigned long long) * (size_t)slots,
                           cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_misc, sizeof(unsigned long long) * 2, 0);
-    if (e == cudaSuccess) std::memset(s->h_misc, 0, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_misc, sizeof(unsigned long long) * 4, 0);
+    if (e == cudaSuccess) std::memset(s->h_misc, 0, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_starts, kStartsStage, cudaHostAllocDefault);
     if (e == cudaSuccess) {
         s->h_chunks_cap = (size_t)std::min<int64_t>(cfg->max_chunks, kChunkStage);
         e = cudaHostAlloc(&s->h_chunks, sizeof(Chunk) * s->h_chunks_cap, cudaHostAllocDefault);
@@ -744,8 +770,9 @@ void grape_walk_server_destroy(grape_server_t* s) {
             s->stop = true;
             s->cv.notify_all();
         }
-        int one = 1;
-        cudaMemcpyAsync(s->d_exit, &one, sizeof(int), cudaMemcpyHostToDevice, s->ctl);
+        int* one = reinterpret_cast<int*>(s->h_misc + 3);
+        *one = 1;
+        cudaMemcpyAsync(s->d_exit, one, sizeof(int), cudaMemcpyHostToDevice, s->ctl);
         cudaStreamSynchronize(s->ctl);
         s->driver.join();
     }
@@ -763,6 +790,7 @@ void grape_walk_server_destroy(grape_server_t* s) {
     if (s->h_tail) cudaFreeHost(s->h_tail);
     if (s->h_misc) cudaFreeHost(s->h_misc);
     if (s->h_chunks) cudaFreeHost(s->h_chunks);
+    if (s->h_starts) cudaFreeHost(s->h_starts);
     cudaFree(s->arena_base);
     cudaFree(s->d_reqs);
     cudaFree(s->d_done);
