@@ -1237,36 +1237,13 @@ struct Engine {
     // is one 32-byte sector: the next proposal's entry or the next probe sector.
     __device__ __forceinline__ bool step(Lane& L) {
         const int phase = L.phase;
-        const Prop A = eval(L, L.r2);
-        // ---- probe view of the arrived sector (phase SEARCH) ----
         const bool srch = HAS_Q && phase == PH_SEARCH;
-        const int key = (L.flags & F_KEY_T) ? L.t : L.x;
-        int lo = 0, hi = L.sn;
-        int vlo = L.vlo, vhi = L.vhi;
-        bool found = false;
-        {
-            const int vals[8] = {ld.x, ld.y, ld.z, ld.w, ld2.x, ld2.y, ld2.z, ld2.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int dj = L.sd + j;
-                const bool in = (unsigned)dj < (unsigned)L.sn;
-                found |= in && vals[j] == key;
-                if (in && vals[j] < key && dj + 1 > lo) {
-                    lo = dj + 1;
-                    vlo = vals[j];
-                }
-                if (in && vals[j] > key && dj < hi) {
-                    hi = dj;
-                    vhi = vals[j];
-                }
-            }
-        }
-        const bool s_done = srch && (found || hi <= lo);
         // ---- outcome ----
         bool take = false;           // the walk moves to A (or to the searched proposal)
         bool probe = false;
         bool fresh = false;          // a search began in this iteration
         if (phase == PH_CAND) {
+            const Prop A = eval(L, L.r2);
             if (A.acc_a == A.acc_b || !HAS_Q) {
                 if (A.acc_a) take = true;
                 else L.k++;
@@ -1297,35 +1274,60 @@ struct Engine {
                                                      (unsigned)a.z), a.y);
                     probe = true;
                 }
-            } else if (HUB && s_done && !found && (L.flags & F_PIV)) {
-                // The pivots place the key in one sector of the list: pivots
-                // before position lo (of the narrowed range) are below it.
-                const long long sector = L.sb - 1 + lo;
-                long long rb;
-                int rn;
-                list_bounds(L, rb, rn);
-                const long long a = rb > 8 * sector ? rb : 8 * sector;
-                const long long b = (rb + rn) < (8 * sector + 8) ? (rb + rn) : (8 * sector + 8);
-                L.flags &= ~(F_PIV | F_BISECT);
-                L.sb = a;
-                L.sn = (int)(b - a);
-                L.vlo = vlo;
-                L.vhi = vhi;
-                probe = true;
-            } else if (s_done) {
-                if ((L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0) take = true;
-                else L.k++;
             } else {
-                // an interpolated probe that did not halve the range is followed
-                // by a bisecting one, so a search takes O(log deg) probes at worst
-                const bool slow = 2 * (hi - lo) > L.sn;
-                L.flags = ((L.flags & F_BISECT) || !slow) ? (L.flags & ~F_BISECT)
-                                                          : (L.flags | F_BISECT);
-                L.sb += lo;
-                L.sn = hi - lo;
-                L.vlo = vlo;
-                L.vhi = vhi;
-                probe = true;
+                // ---- probe view of the arrived sector of a sorted list ----
+                const int key = (L.flags & F_KEY_T) ? L.t : L.x;
+                int lo = 0, hi = L.sn;
+                int vlo = L.vlo, vhi = L.vhi;
+                bool found = false;
+                {
+                    const int vals[8] = {ld.x, ld.y, ld.z, ld.w, ld2.x, ld2.y, ld2.z, ld2.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int dj = L.sd + j;
+                        const bool in = (unsigned)dj < (unsigned)L.sn;
+                        found |= in && vals[j] == key;
+                        if (in && vals[j] < key && dj + 1 > lo) {
+                            lo = dj + 1;
+                            vlo = vals[j];
+                        }
+                        if (in && vals[j] > key && dj < hi) {
+                            hi = dj;
+                            vhi = vals[j];
+                        }
+                    }
+                }
+                const bool s_done = found || hi <= lo;
+                if (HUB && s_done && !found && (L.flags & F_PIV)) {
+                    // The pivots place the key in one sector of the list: pivots
+                    // before position lo (of the narrowed range) are below it.
+                    const long long sector = L.sb - 1 + lo;
+                    long long rb;
+                    int rn;
+                    list_bounds(L, rb, rn);
+                    const long long a = rb > 8 * sector ? rb : 8 * sector;
+                    const long long b = (rb + rn) < (8 * sector + 8) ? (rb + rn) : (8 * sector + 8);
+                    L.flags &= ~(F_PIV | F_BISECT);
+                    L.sb = a;
+                    L.sn = (int)(b - a);
+                    L.vlo = vlo;
+                    L.vhi = vhi;
+                    probe = true;
+                } else if (s_done) {
+                    if ((L.flags & (found ? F_ACC_IN : F_ACC_OUT)) != 0) take = true;
+                    else L.k++;
+                } else {
+                    // an interpolated probe that did not halve the range is followed
+                    // by a bisecting one, so a search takes O(log deg) probes at worst
+                    const bool slow = 2 * (hi - lo) > L.sn;
+                    L.flags = ((L.flags & F_BISECT) || !slow) ? (L.flags & ~F_BISECT)
+                                                              : (L.flags | F_BISECT);
+                    L.sb += lo;
+                    L.sn = hi - lo;
+                    L.vlo = vlo;
+                    L.vhi = vhi;
+                    probe = true;
+                }
             }
         }
         take = take || phase == PH_RET;
