@@ -246,72 +246,143 @@ __device__ __forceinline__ int hash_has_pair(const unsigned* __restrict__ table,
 // the reverse weight, which equals w_vx on an undirected graph).
 // For a walk at v that came from t (a neighbour of v), x in N(t) holds exactly
 // when x is in C(t, v) and when t is in C(v, x); these sets are much smaller
-// than the rows, so their filters prove far more non-memberships.  One warp
-// per row v takes its entries with x > v in turn; the lanes test the entries of
-// the shorter row against the other node in the edge hash (an overflowed bucket
-// counts as a member), OR their bits, and lane 0 writes the filter into (v -> x)
-// and, through rev, into (x -> v).  Pairs whose shorter row exceeds `cap`
-// entries get an all-ones filter; unweighted self-loops keep the row filter
+// than the rows, so their filters prove far more non-memberships.
+//
+// Work is cut into chunks of kPairChunk consecutive entries of the whole entry
+// array, one warp per chunk (grid stride), so the rows of hubs spread over many
+// warps.  The warp finds the row of the chunk's first entry by a 32-ary search
+// of the row offsets, loads 32 targets and their records at a time, and takes
+// the entries with x > v in turn: the lanes test the entries of the shorter row
+// against the other node in the edge hash (an overflowed bucket counts as a
+// member), OR their bits, and lane 0 writes the filter into (v -> x) and,
+// through rev, into (x -> v).  Pairs whose shorter row exceeds `cap` entries
+// get an all-ones filter; unweighted self-loops keep the row filter
 // (C(v, v) = N(v)), weighted ones get all ones.
+constexpr int kPairChunk = 512;
+
+__device__ __forceinline__ long long rec_off(int4 r) {
+    return (long long)(((unsigned long long)(unsigned)r.y << 32) | (unsigned)r.x);
+}
+
+// Warp-collective: the last row v with off_v <= e (the row holding entry e,
+// for 0 <= e < m: that row is not empty), by a 32-ary search over the offsets.
+__device__ long long row_of_entry(const int4* __restrict__ rec, long long n, long long e) {
+    const int lane = threadIdx.x & 31;
+    long long lo = 0, hi = n;                  // off_lo <= e; the row lies in [lo, hi)
+    while (hi - lo > 32) {
+        const long long step = (hi - lo + 31) / 32;
+        const long long q = lo + lane * step;
+        const bool ok = q < hi && rec_off(rec[q]) <= e;
+        const int j = 31 - __clz((int)__ballot_sync(grape::FULL, ok));   // lane 0: q = lo
+        const long long top = lo + (long long)(j + 1) * step;
+        lo += (long long)j * step;
+        if (top < hi) hi = top;
+    }
+    const long long q = lo + lane;
+    const bool ok = q < hi && rec_off(rec[q]) <= e;
+    return lo + (31 - __clz((int)__ballot_sync(grape::FULL, ok)));
+}
+
 __global__ void build_pair_filters_kernel(const int4* __restrict__ rec,
                                           const int32_t* __restrict__ dsts,
                                           const unsigned* __restrict__ table, int k, int b,
-                                          long long n, int cap, int weighted,
+                                          long long n, long long m, int cap, int weighted,
                                           int4* __restrict__ fat) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    for (long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
-        const int4 rv = rec[v];
-        const long long off_v = (long long)(((unsigned long long)(unsigned)rv.y << 32) | (unsigned)rv.x);
-        for (long long e = off_v; e < off_v + rv.z; ++e) {
-            const long long x = dsts[e];
-            if (x == v && weighted && lane == 0) fat[2 * e + 1].w = -1;   // no filter: all ones
-            if (x <= v) continue;
-            const int4 rx = rec[x];
-            const long long off_x = (long long)(((unsigned long long)(unsigned)rx.y << 32) | (unsigned)rx.x);
-            const bool v_short = rv.z <= rx.z;
-            const long long so = v_short ? off_v : off_x;
-            const int sn = v_short ? rv.z : rx.z;
-            const long long other = v_short ? x : v;
-            unsigned f[3] = {~0u, ~0u, ~0u};
-            if (sn <= cap) {
-                f[0] = f[1] = f[2] = 0u;
-                for (int j = lane; j < sn; j += 32) {
-                    const int y = dsts[so + j];
-                    if (hash_has_pair(table, k, b, 1, other, y) != 0) {
-                        const int bit = weighted ? grape::filter_bit32(y) : grape::filter_bit(y);
-                        f[bit >> 5] |= 1u << (bit & 31);
-                    }
-                }
-                f[0] = __reduce_or_sync(grape::FULL, f[0]);
-                f[1] = __reduce_or_sync(grape::FULL, f[1]);
-                f[2] = __reduce_or_sync(grape::FULL, f[2]);
+    const long long chunks = (m + kPairChunk - 1) / kPairChunk;
+    for (long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32; c < chunks;
+         c += warps) {
+        const long long e0 = c * kPairChunk;
+        const long long e1 = e0 + kPairChunk < m ? e0 + kPairChunk : m;
+        long long v = row_of_entry(rec, n, e0);
+        int4 rv = rec[v];
+        long long off_v = rec_off(rv);
+        long long end_v = off_v + rv.z;
+        for (long long base = e0; base < e1; base += 32) {
+            // 32 targets and their records at once
+            const long long el = base + lane;
+            int xl = -1;
+            int4 rxl = make_int4(0, 0, 0, 0);
+            if (el < e1) {
+                xl = dsts[el];
+                if ((unsigned long long)(long long)xl < (unsigned long long)n) rxl = rec[xl];
+                else xl = -1;                 // out of range (unvalidated graph): no filter
             }
-            if (lane == 0) {
-                // unweighted: the three filter words; weighted: the last word
-                // (the reverse weight, equal to w_vx on an undirected graph)
-                int4 w = fat[2 * e + 1];
-                const int rev = w.z;                       // v sits at rev in N(x)
-                if (weighted) {
-                    w.w = (int)f[0];
-                } else {
-                    w.x = (int)f[0];
-                    w.y = (int)f[1];
-                    w.w = (int)f[2];
+            const int cnt = (int)(e1 - base < 32 ? e1 - base : 32);
+            for (int j = 0; j < cnt; ++j) {
+                const long long e = base + j;
+                while (e >= end_v && v + 1 < n) {     // the next non-empty row
+                    ++v;
+                    rv = rec[v];
+                    off_v = rec_off(rv);
+                    end_v = off_v + rv.z;
                 }
-                fat[2 * e + 1] = w;
-                // (x -> v); an unvalidated graph declared undirected may lack it
-                if (rev >= 0 && rev < rx.z) {
-                    const long long er = off_x + rev;
-                    int4 wr = fat[2 * er + 1];
-                    if (weighted) {
-                        wr.w = (int)f[0];
-                    } else {
-                        wr.x = (int)f[0];
-                        wr.y = (int)f[1];
-                        wr.w = (int)f[2];
+                if (e < off_v || e >= end_v) continue;    // inconsistent offsets: no filter
+                const int x = __shfl_sync(grape::FULL, xl, j);
+                if (x == v && weighted && lane == 0) fat[2 * e + 1].w = -1;   // no filter: all ones
+                if (x < 0 || x <= v) continue;
+                int4 rx;
+                rx.x = __shfl_sync(grape::FULL, rxl.x, j);
+                rx.y = __shfl_sync(grape::FULL, rxl.y, j);
+                rx.z = __shfl_sync(grape::FULL, rxl.z, j);
+                const long long off_x = rec_off(rx);
+                const bool v_short = rv.z <= rx.z;
+                const long long so = v_short ? off_v : off_x;
+                const int sn = v_short ? rv.z : rx.z;
+                const long long other = v_short ? x : v;
+                unsigned f[3] = {~0u, ~0u, ~0u};
+                if (sn <= cap) {
+                    f[0] = f[1] = f[2] = 0u;
+                    // four entries per lane per round, so their row and hash
+                    // reads are in flight together
+                    for (int i0 = lane; i0 < sn; i0 += 128) {
+                        int y[4];
+                        bool in[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            in[u] = i0 + 32 * u < sn;
+                            y[u] = in[u] ? dsts[so + i0 + 32 * u] : 0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (in[u] && hash_has_pair(table, k, b, 1, other, y[u]) != 0) {
+                                const int bit = weighted ? grape::filter_bit32(y[u])
+                                                         : grape::filter_bit(y[u]);
+                                f[bit >> 5] |= 1u << (bit & 31);
+                            }
+                        }
                     }
-                    fat[2 * er + 1] = wr;
+                    f[0] = __reduce_or_sync(grape::FULL, f[0]);
+                    f[1] = __reduce_or_sync(grape::FULL, f[1]);
+                    f[2] = __reduce_or_sync(grape::FULL, f[2]);
+                }
+                if (lane == 0) {
+                    // unweighted: the three filter words; weighted: the last word
+                    // (the reverse weight, equal to w_vx on an undirected graph)
+                    int4 w = fat[2 * e + 1];
+                    const int rev = w.z;                       // v sits at rev in N(x)
+                    if (weighted) {
+                        w.w = (int)f[0];
+                    } else {
+                        w.x = (int)f[0];
+                        w.y = (int)f[1];
+                        w.w = (int)f[2];
+                    }
+                    fat[2 * e + 1] = w;
+                    // (x -> v); an unvalidated graph declared undirected may lack it
+                    if (rev >= 0 && rev < rx.z) {
+                        const long long er = off_x + rev;
+                        int4 wr = fat[2 * er + 1];
+                        if (weighted) {
+                            wr.w = (int)f[0];
+                        } else {
+                            wr.x = (int)f[0];
+                            wr.y = (int)f[1];
+                            wr.w = (int)f[2];
+                        }
+                        fat[2 * er + 1] = wr;
+                    }
                 }
             }
         }
@@ -521,9 +592,11 @@ grape_status_t grape_graph_create(const int64_t* offsets, const int32_t* dsts,
             }
             // undirected graphs: filters of common neighbours
             if (e == cudaSuccess && g->undirected) {
-                build_pair_filters_kernel<<<grid_for(g->num_sms, num_nodes * 32, 256), 256, 0,
+                const long long chunks = (num_entries + kPairChunk - 1) / kPairChunk;
+                build_pair_filters_kernel<<<grid_for(g->num_sms, chunks * 32, 256), 256, 0,
                                             stream>>>(g->rec, g->dsts, g->eh, k, b, num_nodes,
-                                                      kPairFilterCap, weights ? 1 : 0, g->fat);
+                                                      num_entries, kPairFilterCap,
+                                                      weights ? 1 : 0, g->fat);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) g->pair_filters = true;
             }
