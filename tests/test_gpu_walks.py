@@ -147,6 +147,47 @@ def test_rmat12_hub_search_schedules(weighted, schedule, shorter_min):
     assert c["pivot_probes"] + c["hash_probes"] <= c["probes"]
 
 
+def _chunk_straddling_graph(weighted):
+    """Undirected graph for the common-neighbour filter build, which cuts the
+    entry array into chunks of 512 entries: ten hubs of about 700 neighbours
+    (rows that straddle chunk boundaries), runs of isolated nodes between
+    non-empty rows, self-loops on hubs and leaves, a 61-node clique (pairs with
+    many common neighbours) and random edges (triangles)."""
+    rng = np.random.default_rng(2024)
+    n = 2400
+    live = np.array([v for v in range(n) if v % 7 != 3 and not 1500 <= v < 1540])
+    edges = set()
+    for h in range(10):
+        for x in rng.choice(live[live >= 10], size=700, replace=False):
+            edges.add((h, int(x)))
+        for h2 in range(h + 1, 10):
+            edges.add((h, h2))
+    for a in range(100, 161):
+        for b in range(a + 1, 161):
+            if a % 7 != 3 and b % 7 != 3:
+                edges.add((a, b))
+    for _ in range(5000):
+        a, b = (int(v) for v in rng.choice(live, size=2, replace=False))
+        edges.add((min(a, b), max(a, b)))
+    for v in (0, 1, 17, 250, 2399):
+        edges.add((v, v))
+    edges = sorted(edges)
+    wts = rng.uniform(0.1, 1.0, size=len(edges)).astype(np.float32) if weighted else None
+    return csr_from_np(*_law.csr_from_edges(n, edges, wts, True))
+
+
+@pytest.mark.parametrize("weighted", [False, True], ids=["unweighted", "weighted"])
+def test_filters_built_over_chunks_straddling_rows(weighted):
+    """Rows equal the oracle's on a graph whose hub rows cross the filter
+    build's chunk boundaries, with isolated runs and self-loops, for (p, q)
+    where membership decides acceptance."""
+    csr = _chunk_straddling_graph(weighted)
+    assert csr.num_entries > 20 * 512
+    g = Graph.from_csr(csr)
+    for p, q in ((1.0, 0.25), (0.5, 4.0), (2.0, 0.5)):
+        check_parity(csr, None, 40, 3, p, q, seed=int(p * 100 + q * 10), graph=g)
+
+
 def test_hub_search_schedules_on_a_hub_graph():
     """A hub of degree 6,000 joined to a ring: every search meets long lists,
     pivot and warp schedules both run many rounds; rows equal the oracle's."""
