@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-hub-ab", action="store_true",
                     help="skip the membership-search schedule comparison")
+    ap.add_argument("--probe-buffer-sweep", action="store_true",
+                    help="run only the random-sector probe over buffers of 32 MB to 64 GB "
+                         "and print its table")
     ap.add_argument("--no-probe-sweep", action="store_true",
                     help="time only the probe's default shape instead of sweeping it")
     ap.add_argument("--no-contexts", action="store_true")
@@ -312,6 +315,35 @@ def random_sector_peak(dev, gib=16, reads=1 << 29, sweep=True):
     torch.cuda.empty_cache()
     best = max(rows, key=lambda r: r["sectors_per_s"])
     return best["sectors_per_s"], best, rows
+
+
+def probe_buffer_sweep(dev, reads=1 << 29):
+    """The random-sector probe (grape_sector_probe) over buffers from 32 MB to
+    64 GB, for three shapes: 32-byte loads 8 in flight (.nc), 4-byte loads 32
+    in flight (.cs), and both sectors of a random 64-byte block 4 in flight
+    (.nc; counted as two sectors).  Where the rate stops falling with the
+    buffer size is where L2 stops helping.  Returns sectors/s per size and shape."""
+    from paper_2110_06196_gb300 import walk as W
+    shapes = (("32B x8 nc", 0, 32, 8), ("4B x32 cs", 2, 4, 32), ("64B block x4 nc", 0, 64, 4))
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for mb in (32, 96, 256, 1024, 4096, 16384, 65536):
+        buf = torch.empty(mb << 18, dtype=torch.int32, device=dev)     # mb MiB
+        buf.fill_(1)
+        row = {"buffer_mib": mb}
+        for name, mode, w, l in shapes:
+            W.sector_probe(buf, reads // 8, seed=1, mode=mode, load_bytes=w, loads_in_flight=l)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            n, _ = W.sector_probe(buf, reads, seed=2, mode=mode, load_bytes=w, loads_in_flight=l)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            row[name] = n / e0.elapsed_time(e1) * 1e3
+        rows.append(row)
+        del buf
+        torch.cuda.empty_cache()
+    return {"probe_buffer_sweep": rows, "unit": "32-byte sectors/s", "reads_per_shape": reads}
 
 
 def workload_desc(name, job):
@@ -1228,7 +1260,10 @@ def main():
     args = parse()
     dist = Dist(args.gpus)
     try:
-        if args.impl == "reference":
+        if args.probe_buffer_sweep:
+            torch.cuda.set_device(dist.local)
+            res = probe_buffer_sweep(torch.device("cuda", dist.local)) if dist.rank == 0 else None
+        elif args.impl == "reference":
             res = run_reference(args, dist)
         else:
             res = run_ours(args, dist)
